@@ -1,0 +1,178 @@
+"""Seeded synthetic workloads for the PDV Monte Carlo (shared input generators).
+
+This module only describes inputs: cloud, phase-function choice, probe, snapshot
+times and packet counts, in SI units, plus the seeded draws of the batched and
+served workloads. It holds none of the method's arithmetic, so that the CUDA
+path and the FP64 oracle can both be fed from it without sharing code.
+
+The named workloads follow the paper's synthetic Sn clouds (Section II.D and
+Section III.A: exponential velocity law Eq. 20, log-normal sizes Eq. 21,
+lambda = 1550 nm, vacuum, z = v t) at the sizes of the benchmark set:
+
+* ``cfg1`` — monodisperse 2 um, 0.5 mg/cm^2 (tau ~ 1 with Q_ext = 2), beta = 5
+  on [2000, 6000] m/s, HG g = 0.7 and albedo 0.6 on 1801 angles, one snapshot
+  at 1 us, 1e6 packets, 200 bins over 0-6000 m/s.
+* ``cfg2`` — log-normal d_m = 3 um, sigma = 0.5, Mie m = 3 + 9i, 5 mg/cm^2,
+  beta = 5, 50 snapshots 0.5-5 us, 1e8 packets per snapshot, 600 bins 0-8000.
+* ``cfg3`` — heavy multiple scattering: monodisperse 1 um, 20 mg/cm^2, beta = 3,
+  Mie m = 3 + 9i; FP32 and FP64 GPU paths against the oracle.
+* ``cfg4`` — 256 parameter sets drawn from a seed (batched launch).
+* ``cfg5`` — Poisson request stream for the serving loop.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+MG_CM2 = 1.0e-2          # 1 mg/cm^2 in kg/m^2
+UM = 1.0e-6
+NM = 1.0e-9
+MM = 1.0e-3
+US = 1.0e-6
+
+
+@dataclass
+class Phase:
+    """Phase-function choice: Henyey–Greenstein with given albedo and Q_ext,
+    size-averaged Mie for a complex index, or an explicit table."""
+    kind: str = "hg"                  # "hg" | "mie" | "table"
+    g: float = 0.7
+    albedo: float = 0.6
+    q_ext: float = 2.0
+    m: complex = 3.0 + 9.0j
+    n_angle: int = 1801
+    n_size: int = 256
+    theta: Optional[Sequence[float]] = None
+    p: Optional[Sequence[float]] = None
+
+
+@dataclass
+class Workload:
+    # cloud (SI)
+    rho: float = 7290.0
+    m0: float = 0.5 * MG_CM2
+    v_fs: float = 2000.0
+    reflectivity: float = 0.6
+    surface_mode: int = 0             # 0 uniform polar angle, 1 Lambertian, 2 specular
+    profile_kind: str = "exponential"  # or "tabulated"
+    beta: float = 5.0
+    v_max: float = 6000.0             # 0 -> mass-tail rule
+    prof_v: Optional[Sequence[float]] = None
+    prof_f: Optional[Sequence[float]] = None
+    d_m: float = 2.0 * UM
+    sigma_ln: float = 0.0
+    wavelength: float = 1550.0 * NM
+    phase: Phase = field(default_factory=Phase)
+    # probe
+    z_probe: float = 50.0 * MM
+    r_beam: float = 0.5 * MM
+    r_ap: float = 1.0 * MM            # <= 0: unlimited
+    cone_alpha: float = 0.1           # >= pi/2: all upward
+    # snapshots and tally
+    t_snap: Sequence[float] = (1.0 * US,)
+    n_bins: int = 200
+    v_lo: float = 0.0
+    v_hi: float = 6000.0
+    # packets
+    n_packets: int = 1_000_000
+    seed: int = 1
+    stream_id: int = 0
+    max_events: int = 1_000_000
+    precision: str = "fp32"           # "fp32" | "fp64"
+    name: str = "custom"
+
+    def replace(self, **kw) -> "Workload":
+        return dataclasses.replace(self, **kw)
+
+
+def cfg1(**kw) -> Workload:
+    """Plain FP64-accurate transport case (tin, monodisperse 2 um, HG)."""
+    return Workload(name="cfg1").replace(**kw)
+
+
+def cfg2(**kw) -> Workload:
+    """Log-normal 3 um / 0.5, Mie 3+9i at 1550 nm, 5 mg/cm^2, 50 snapshots."""
+    wl = Workload(
+        name="cfg2", m0=5.0 * MG_CM2, beta=5.0, v_max=0.0, d_m=3.0 * UM, sigma_ln=0.5,
+        phase=Phase(kind="mie", m=3.0 + 9.0j, n_angle=1801, n_size=256),
+        t_snap=tuple(np.linspace(0.5, 5.0, 50) * US), n_bins=600, v_lo=0.0, v_hi=8000.0,
+        n_packets=100_000_000, seed=2)
+    return wl.replace(**kw)
+
+
+def cfg3(**kw) -> Workload:
+    """Heavy multiple scattering: 20 mg/cm^2, monodisperse 1 um, beta = 3."""
+    wl = Workload(
+        name="cfg3", m0=20.0 * MG_CM2, beta=3.0, v_max=0.0, d_m=1.0 * UM, sigma_ln=0.0,
+        phase=Phase(kind="mie", m=3.0 + 9.0j, n_angle=1801, n_size=1),
+        t_snap=(1.0 * US,), n_bins=600, v_lo=0.0, v_hi=8000.0, n_packets=1_000_000_000,
+        seed=3)
+    return wl.replace(**kw)
+
+
+def cfg4_sets(n_sets: int = 256, seed: int = 4, n_min: float = 1e5, n_max: float = 1e8,
+              n_bins: int = 400) -> List[Workload]:
+    """256 parameter sets: beta ~ U(2, 10), m0 ~ logU(0.1, 20) mg/cm^2,
+    d ~ logU(0.5, 10) um, v_fs ~ U(1.5, 3) km/s, t ~ U(1, 4) us, packets ~
+    logU(n_min, n_max); monodisperse Mie 3+9i, one snapshot, bins over
+    [0, v_max of the set]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_sets):
+        beta = float(rng.uniform(2.0, 10.0))
+        m0 = float(np.exp(rng.uniform(np.log(0.1), np.log(20.0)))) * MG_CM2
+        d = float(np.exp(rng.uniform(np.log(0.5), np.log(10.0)))) * UM
+        v_fs = float(rng.uniform(1500.0, 3000.0))
+        t = float(rng.uniform(1.0, 4.0)) * US
+        n = int(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        v_top = v_fs * (1.0 + math.log(1.0e6) / beta)   # mass-tail rule of the cloud
+        out.append(Workload(
+            name="cfg4[%d]" % i, m0=m0, beta=beta, v_max=0.0, v_fs=v_fs, d_m=d, sigma_ln=0.0,
+            phase=Phase(kind="mie", m=3.0 + 9.0j, n_angle=1801, n_size=1), t_snap=(t,),
+            n_bins=n_bins, v_lo=0.0, v_hi=v_top, n_packets=n, seed=1000 + i, stream_id=i))
+    return out
+
+
+@dataclass
+class Arrival:
+    t: float              # arrival time, s
+    beta: float
+    m0: float             # kg/m^2
+    d_m: float            # m
+    n_packets: int
+    seed: int
+
+
+def cfg5_arrivals(rate: float = 200.0, duration: float = 60.0, seed: int = 5,
+                  n_min: float = 1e5, n_max: float = 1e7) -> List[Arrival]:
+    """Poisson request stream (rate per second over ``duration`` seconds) of
+    candidate (beta, m0, d) sets around a sweep, packets ~ logU(n_min, n_max)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    i = 0
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= duration:
+            break
+        out.append(Arrival(
+            t=t, beta=float(rng.uniform(3.0, 10.0)),
+            m0=float(np.exp(rng.uniform(np.log(1.0), np.log(10.0)))) * MG_CM2,
+            d_m=float(np.exp(rng.uniform(np.log(1.0), np.log(4.0)))) * UM,
+            n_packets=int(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))),
+            seed=50_000 + i))
+        i += 1
+    return out
+
+
+def cfg5_request(a: Arrival, **kw) -> Workload:
+    """Spectrum request of the serving stream for one arrival (HG phase so that
+    no per-request Mie table is needed; beams and probe as in cfg1)."""
+    wl = Workload(name="cfg5", m0=a.m0, beta=a.beta, v_max=0.0, d_m=a.d_m,
+                  phase=Phase(kind="hg", g=0.7, albedo=0.6, q_ext=2.0), n_bins=400,
+                  v_lo=0.0, v_hi=8000.0, n_packets=a.n_packets, seed=a.seed)
+    return wl.replace(**kw)

@@ -1,0 +1,265 @@
+"""Pins for the oracle's Monte Carlo transport against what the paper and the
+mathematics fix: Beer–Lambert transmission (Eq. 7, Eq. 10), the free-surface
+echo at v_fs (Fig. 4 caption: omega_fs = 2 omega_r v_fs / c), exact
+backscatter from a thin sheet, the single-scattering integral (the Section
+III.B model in its exact, attenuated form; thin limit I ~ tau0 f(v) of
+Eq. 28), self-similarity in time (z = v t), the Doppler sum of Eq. 4 as
+-1/2 dL/dt of the optical path, and exact integer weight conservation."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import oracle as O
+from paper_2012_00963_gb300 import workloads as W
+
+TWO32 = 2**32
+
+
+def _c(res, s=0):
+    return O.counters_dict(res["counters"][s])
+
+
+def _conserved(c):
+    return (c["w_detected"] + c["w_under"] + c["w_over"] + c["w_escaped_undetected"] +
+            c["w_absorbed_particle"] + c["w_absorbed_surface"] + c["w_truncated"]) == \
+        c["launched"] * TWO32
+
+
+@pytest.mark.parametrize("kw", [
+    dict(),
+    dict(surface_mode=1, reflectivity=1.0),
+    dict(surface_mode=2, reflectivity=0.37, cone_alpha=2.0, r_ap=0.0),
+    dict(phase=W.Phase(albedo=1.0), m0=3 * W.MG_CM2),
+    dict(reflectivity=0.0, max_events=3),
+    dict(t_snap=(0.5 * W.US, 1.0 * W.US, 4.0 * W.US), v_lo=2500.0, v_hi=3500.0),
+])
+def test_weight_conservation_and_event_bookkeeping(kw):
+    wl = W.cfg1(n_packets=20000, **kw)
+    r = O.simulate(wl, n_threads=4, packets=True)
+    pk = r["packets"]
+    for s in range(len(wl.t_snap)):
+        c = _c(r, s)
+        assert _conserved(c)
+        assert c["launched"] == wl.n_packets
+    c = _c(r)
+    n_abs = int(np.sum(pk["fate"] == O.FATE_ABS_PARTICLE))
+    assert c["events"] == c["scatters"] + c["surface_hits"] + n_abs
+    assert c["events"] == int(pk["n_events"].sum())
+    assert c["scatters"] == int(pk["n_scatters"].sum())
+    assert c["escapes"] == int(np.sum(pk["fate"] == O.FATE_ESCAPED))
+    assert c["truncated"] == int(np.sum(pk["fate"] == O.FATE_TRUNCATED))
+    if wl.max_events == 3:
+        assert pk["n_events"].max() <= 3 and c["truncated"] > 0
+
+
+def test_threads_do_not_change_results():
+    wl = W.cfg1(n_packets=30000)
+    a = O.simulate(wl, n_threads=1, packets=True)
+    b = O.simulate(wl, n_threads=7, packets=True)
+    assert np.array_equal(a["hist"], b["hist"])
+    assert np.array_equal(a["counters"], b["counters"])
+    assert np.array_equal(a["packets"], b["packets"])
+
+
+@pytest.mark.parametrize("m0_mg", [0.05, 0.5, 1.5])
+def test_beer_lambert_transmission(m0_mg):
+    """Purely absorbing cloud (albedo 0) over an absorbing surface: the
+    fraction of packets reaching the surface is exp(-tau) (Eq. 7, Eq. 10)."""
+    wl = W.cfg1(n_packets=200000, m0=m0_mg * W.MG_CM2, phase=W.Phase(albedo=0.0),
+                reflectivity=0.0)
+    r = O.simulate(wl)
+    c = _c(r)
+    tau = 3 * wl.m0 * 2.0 / (2 * wl.rho * wl.d_m)
+    p = math.exp(-tau)
+    n = wl.n_packets
+    assert abs(c["surface_hits"] - n * p) < 4 * math.sqrt(n * p * (1 - p))
+    assert c["w_absorbed_surface"] == c["surface_hits"] * TWO32
+    assert c["escapes"] == 0 and c["scatters"] == 0
+
+
+def _overlap_area(R1, R2, d):
+    """Area of the intersection of two disks (radii R1, R2, centre distance d)."""
+    if d >= R1 + R2:
+        return 0.0
+    if d <= abs(R1 - R2):
+        return math.pi * min(R1, R2) ** 2
+    a1 = R1 * R1 * math.acos((d * d + R1 * R1 - R2 * R2) / (2 * d * R1))
+    a2 = R2 * R2 * math.acos((d * d + R2 * R2 - R1 * R1) / (2 * d * R2))
+    a3 = 0.5 * math.sqrt((-d + R1 + R2) * (d + R1 - R2) * (d - R1 + R2) * (d + R1 + R2))
+    return a1 + a2 - a3
+
+
+def test_empty_cloud_free_surface_echo():
+    """m0 = 0: the only echo is the free surface. Every detected packet has
+    v_app = (1 + cos theta') v_fs / 2 in [(1 + cos alpha)/2 v_fs, v_fs]
+    (omega_fs = 2 omega_r v_fs / c, Fig. 4 caption), the detected weight is
+    exactly round(R 2^32) per packet, and the detected fraction matches a
+    quadrature over launch radius and reflection angle (circle overlap)."""
+    t = 1.0 * W.US
+    wl = W.cfg1(n_packets=400000, m0=0.0, t_snap=(t,), n_bins=1000, v_lo=1990.0, v_hi=2010.0)
+    r = O.simulate(wl, packets=True)
+    c = _c(r)
+    pk = r["packets"]
+    det = (pk["detect_mask"] & 1).astype(bool)
+    lo = 0.5 * (1 + math.cos(wl.cone_alpha)) * wl.v_fs
+    assert np.all(pk["v_app"][det] >= lo - 1e-9) and np.all(pk["v_app"][det] <= wl.v_fs + 1e-9)
+    Rq = int(math.floor(wl.reflectivity * TWO32 + 0.5))
+    assert c["w_detected"] == Rq * c["detected"]
+    assert np.all(pk["n_events"] == 1) and np.all(pk["n_surface"] == 1)
+    H = wl.z_probe - wl.v_fs * t
+    f = lambda th: _overlap_area(wl.r_beam, wl.r_ap, H * math.tan(th)) / (math.pi * wl.r_beam**2)
+    th_max = min(wl.cone_alpha, math.atan((wl.r_ap + wl.r_beam) / H))
+    P = integrate.quad(f, 0.0, th_max, epsabs=1e-13, limit=200)[0] / (math.pi / 2)
+    n = wl.n_packets
+    assert abs(c["detected"] - n * P) < 4 * math.sqrt(n * P * (1 - P))
+
+
+@pytest.mark.parametrize("mode,expect", [(0, lambda a: a / (math.pi / 2)),
+                                         (1, lambda a: math.sin(a) ** 2),
+                                         (2, lambda a: 1.0)])
+def test_surface_laws_cone_fraction(mode, expect):
+    """Detected fraction with an unlimited aperture: uniform polar angle gives
+    alpha / (pi/2), Lambertian sin^2(alpha), specular all; specular returns
+    exactly v_fs."""
+    wl = W.cfg1(n_packets=200000, m0=0.0, surface_mode=mode, r_ap=0.0, cone_alpha=0.4,
+                reflectivity=1.0, v_lo=0.0, v_hi=4000.0)
+    r = O.simulate(wl, packets=True)
+    c = _c(r)
+    P = expect(wl.cone_alpha)
+    n = wl.n_packets
+    assert abs(c["detected"] - n * P) <= 4 * math.sqrt(n * P * (1 - P)) + 1e-9
+    if mode == 2:
+        assert np.all(r["packets"]["v_app"] == wl.v_fs)
+
+
+def test_exact_backscatter_from_thin_sheet():
+    """A thin sheet of particles at v0 (optically thin, albedo 1, absorbing
+    surface) echoes at v0: detected v_app lies in [(1+cos alpha)/2 v0, v0+dv]."""
+    v0, dv = 3000.0, 0.5
+    wl = W.cfg1(n_packets=400000, profile_kind="tabulated", prof_v=[v0, v0 + dv],
+                prof_f=[1.0, 1.0], m0=0.1 * W.MG_CM2, reflectivity=0.0,
+                phase=W.Phase(albedo=1.0, g=0.0), r_ap=0.0, cone_alpha=0.3,
+                v_lo=0.0, v_hi=6000.0)
+    r = O.simulate(wl, packets=True)
+    pk = r["packets"]
+    det = (pk["detect_mask"] & 1).astype(bool)
+    assert det.sum() > 100
+    lo = 0.5 * (1 + math.cos(wl.cone_alpha)) * v0
+    assert np.all(pk["v_app"][det] >= lo - 1e-6)
+    assert np.all(pk["v_app"][det] <= v0 + dv + 1e-6)
+
+
+def _hg_pdf_cos(c, g):
+    return 0.5 * (1 - g * g) / (1 + g * g - 2 * g * c) ** 1.5
+
+
+def _single_scatter_expectation(wl, tau, n_grid=3000):
+    """Expected order-1 detected counts per bin for a packet entering straight
+    down: first interaction at depth t_d below the top (density exp(-t_d)),
+    scatter with probability albedo into mu = -cos(theta) > 0 (HG), escape
+    with probability exp(-t_d / mu), accepted when mu >= cos(alpha); the
+    apparent velocity is (1 + mu) v / 2 with v the particle velocity at that
+    depth. v(depth) is inverted numerically from the Eq. 20 mass fraction."""
+    g, alb = wl.phase.g, wl.phase.albedo
+    vv = np.linspace(wl.v_fs, wl.v_max, 200001)
+    fv = np.exp(-wl.beta * (vv / wl.v_fs - 1))
+    cum = integrate.cumulative_trapezoid(fv, vv, initial=0.0)
+    cum /= cum[-1]
+    td = (np.arange(n_grid) + 0.5) / n_grid * tau
+    v_of = np.interp((tau - td) / tau, cum, vv)
+    mu_min = math.cos(wl.cone_alpha) if wl.cone_alpha < math.pi / 2 else 0.0
+    mu = mu_min + (np.arange(n_grid) + 0.5) / n_grid * (1 - mu_min)
+    dmu, dtd = (1 - mu_min) / n_grid, tau / n_grid
+    pm = _hg_pdf_cos(-mu, g) * dmu
+    inv_dbin = wl.n_bins / (wl.v_hi - wl.v_lo)
+    out = np.zeros(wl.n_bins)
+    for i in range(n_grid):
+        w = alb * math.exp(-td[i]) * dtd * pm * np.exp(-td[i] / mu)
+        b = np.floor((0.5 * (1 + mu) * v_of[i] - wl.v_lo) * inv_dbin).astype(np.int64)
+        ok = (b >= 0) & (b < wl.n_bins)
+        out += np.bincount(b[ok], weights=w[ok], minlength=wl.n_bins)
+    return out * wl.n_packets
+
+
+@pytest.mark.parametrize("m0_mg,alpha,g,alb,n", [(0.5, 0.35, 0.7, 0.6, 600000),
+                                                 (2.0, 1.2, 0.7, 0.6, 600000),
+                                                 (0.01, 0.35, 0.0, 1.0, 2000000)])
+def test_order1_matches_single_scattering_integral(m0_mg, alpha, g, alb, n):
+    """Per-order tally: order 1 (one particle scattering, surface absorbing)
+    equals the single-scattering integral bin by bin (5 sigma over bins) and
+    in total (4 sigma)."""
+    wl = W.cfg1(n_packets=n, m0=m0_mg * W.MG_CM2, reflectivity=0.0, r_ap=0.0,
+                cone_alpha=alpha, n_bins=60, v_lo=1500.0, v_hi=6500.0,
+                phase=W.Phase(g=g, albedo=alb))
+    r = O.simulate(wl, order=True)
+    obs = r["order"][0, 1].astype(np.float64) / TWO32
+    exp = _single_scatter_expectation(wl, r["tau_tot"])
+    sel = exp > 20
+    assert sel.sum() >= 5
+    z = (obs[sel] - exp[sel]) / np.sqrt(exp[sel])
+    assert np.max(np.abs(z)) < 5.0, z
+    assert abs(obs.sum() - exp.sum()) < 4 * math.sqrt(exp.sum())
+
+
+def test_thin_limit_follows_mass_distribution():
+    """Optically thin limit of the single-scattering model (Eq. 28 with
+    tau0 -> 0: I ~ tau0 f(v)): with a narrow backscatter cone the order-1
+    spectrum is the mass histogram of Eq. 20 (counting noise plus the few
+    per cent of depth attenuation at tau = 0.02)."""
+    wl = W.cfg1(n_packets=8000000, m0=0.01 * W.MG_CM2, reflectivity=0.0, r_ap=0.0, beta=2.0,
+                cone_alpha=0.35, n_bins=12, v_lo=2000.0, v_hi=6800.0,
+                phase=W.Phase(g=0.0, albedo=1.0))
+    r = O.simulate(wl, order=True)
+    obs = r["order"][0, 1].astype(np.float64) / TWO32
+    edges = wl.v_lo + np.arange(wl.n_bins + 1) * (wl.v_hi - wl.v_lo) / wl.n_bins
+    e = np.minimum(edges, wl.v_max)
+    mass = -np.diff(np.exp(-wl.beta * (e / wl.v_fs - 1)))
+    exp = obs.sum() * mass / mass.sum()
+    sel = exp > 100
+    assert sel.sum() >= 4
+    assert np.all(np.abs(obs[sel] - exp[sel]) < 4 * np.sqrt(exp[sel]) + 0.05 * exp[sel])
+
+
+def test_time_invariance_detect_all():
+    """Self-similar cloud (z = v t, Section II.C) with an unlimited aperture and
+    cone: spectra at t and 2t are identical (common random numbers)."""
+    wl = W.cfg1(n_packets=100000, r_ap=0.0, cone_alpha=2.0, m0=2 * W.MG_CM2,
+                t_snap=(1.0 * W.US, 2.0 * W.US))
+    r = O.simulate(wl)
+    assert np.array_equal(r["hist"][0], r["hist"][1])
+    assert np.array_equal(r["counters"][0], r["counters"][1])
+
+
+def test_doppler_is_minus_half_path_rate():
+    """Eq. 4: v_app = 1/2 sum (n_out - n_in).v_k equals -1/2 dL/dt of the
+    optical path (plane wave in from the probe plane, vertices moving with
+    their particle or wall velocity, plane wave out), by central difference."""
+    wl = W.cfg1(n_packets=3000, m0=2 * W.MG_CM2, phase=W.Phase(albedo=0.95), r_ap=0.0,
+                cone_alpha=2.0)
+    r = O.simulate(wl, packets=True, n_trace=3000, max_vertices=128)
+    tr, pk = r["trace"], r["packets"]
+    h = 1e-11
+    checked = 0
+    for i in range(len(pk)):
+        if pk["fate"][i] != O.FATE_ESCAPED:
+            continue
+        vs = tr[i][tr[i]["kind"] >= 0]
+        assert vs["kind"][0] == 0 and vs["kind"][-1] == 3
+        mid = vs[1:-1]
+        out = vs[-1]
+        n_out = np.array([out["ux"], out["uy"], out["uz"]])
+        ref = np.array([out["x"], out["y"], out["z"]])
+
+        def L(dt):
+            P = np.stack([mid["x"], mid["y"], mid["z"] + mid["v"] * dt], axis=1)
+            Lsum = wl.z_probe - P[0, 2]
+            Lsum += np.sum(np.linalg.norm(np.diff(P, axis=0), axis=1))
+            Lsum += float(np.dot(n_out, ref - P[-1]))
+            return Lsum
+
+        fd = -0.5 * (L(h) - L(-h)) / (2 * h)
+        assert fd == pytest.approx(pk["v_app"][i], rel=1e-5, abs=1e-3)
+        checked += 1
+    assert checked > 100
