@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the PDV Monte Carlo hot path on GB300.
+
+Workload (default): the log-normal Mie cloud of the benchmark set — d_m = 3 um,
+sigma = 0.5, m = 3 + 9i at 1550 nm, 5 mg/cm^2 of tin, beta = 5 (mass tail
+1e-6), 50 snapshots at 0.5-5 us, 1e8 packets per snapshot, 600 bins over
+0-8000 m/s, FP32 transport.
+
+One step = one pass of every step of the path: the cloud's mass table (FP64
+kernel), the phase CDF (FP64 kernel), the persistent FP32 transport of all
+packets with detection at all 50 snapshot times, and the normalisation to 50
+spectra. ``value`` is measured with device-resident inputs and device outputs;
+``e2e`` runs the same step through the public API with pinned host inputs and
+host outputs (copies inside the timed region).
+
+Unit: scatter events per second, counted once per packet history (a history
+serves every snapshot time). Also reported: all events/s, spectra/s, the
+plain FP64 GPU path on the same workload, the issue-rate roofline of the
+transport kernel, and the FP64 CPU oracle on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "photon scatter events/s & spectra/s vs plain FP64 path; p50/p99 request latency"
+UNIT = "scatter events/s"
+# Algorithmic thread-instructions of one event (flight + what ends it) on the
+# FP32 path: Philox4x32-10 (~80), free path and fixed-point update (~30),
+# velocity-table inversion (~20), phase-table inversion and theta (~16),
+# sin/cos of theta and phi (~30), rotation and renormalisation (~25), lateral
+# move, albedo test, Doppler sum and bookkeeping (~20): 220.
+ALGO_INST_PER_EVENT = 220.0
+SMS, SCHEDULERS, LANES, F_MAX_HZ = 152, 4, 32, 2.070e9
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--packets", type=float, default=1e8, help="packets per snapshot")
+    ap.add_argument("--snapshots", type=int, default=50)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def workload(args, rank=0):
+    import numpy as np
+    from paper_2012_00963_gb300 import workloads as W
+    t = tuple(np.linspace(0.5, 5.0, args.snapshots) * W.US)
+    return W.cfg2(n_packets=int(args.packets), t_snap=t, seed=2 + 1000 * rank)
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def source_hash():
+    h = hashlib.sha1()
+    for f in ("transport.cu", "pdv_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2012_00963_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def profile_counters():
+    """Per-event DRAM traffic and issued instructions of the transport kernel
+    from the committed ncu summary, if it was taken on the current source."""
+    p = os.path.join(ROOT, "profiles", "transport_f32_counters.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    return d if d.get("source_hash") == source_hash() else None
+
+
+# ----------------------------------------------------------------------- CPU
+def oracle_sample(wl, seconds, threads):
+    """Time the FP64 oracle on a bounded sample of the workload (all snapshot
+    times, a slice of the packets), sized for about `seconds` of wall time."""
+    from oracle import oracle as O
+    table = O.phase_table(wl)
+    n = 200
+    while True:
+        t0 = time.perf_counter()
+        r = O.simulate(wl, n_threads=threads, n_packets=n, table=table)
+        dt = time.perf_counter() - t0
+        if dt >= seconds * 0.5 or n >= wl.n_packets:
+            break
+        n = min(int(n * max(2.0, 0.8 * seconds / max(dt, 1e-3))), wl.n_packets)
+    ns = len(wl.t_snap)
+    scat = int(r["counters"][0][2])          # scatters of the n distinct histories
+    return dict(value=scat / dt, packets=n, seconds=dt, snapshots=ns,
+                spectra_per_s=ns * (n / wl.n_packets) / dt,
+                events_per_s=int(r["counters"][0][1]) / dt)
+
+
+def reference_arm(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = workload(args)
+    threads = os.cpu_count() or 1
+    per_step = max(1.0, min(6.0, 150.0 / max(args.steps + args.warmup, 1)))
+    for _ in range(args.warmup):
+        oracle_sample(wl, per_step * 0.25, threads)
+    vals, sp, tot, pk = [], [], 0.0, 0
+    for _ in range(args.steps):
+        s = oracle_sample(wl, per_step, threads)
+        vals.append(s["value"])
+        sp.append(s["spectra_per_s"])
+        tot += s["seconds"]
+        pk = s["packets"]
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl.name + " (FP64 CPU oracle)",
+                                        "packets_per_snapshot": wl.n_packets,
+                                        "snapshots": len(wl.t_snap), "bins": wl.n_bins},
+        "spectra_per_s": statistics.median(sp),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "%d packets x %d snapshots per step (of %d packets)" % (
+                             pk, len(wl.t_snap), wl.n_packets)},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------- GPU
+def our_arm(args):
+    import numpy as np
+    import torch
+    from paper_2012_00963_gb300 import pdv
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    wl = workload(args, rank)
+    ns, nb = len(wl.t_snap), wl.n_bins
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+
+    ctx = pdv.Context(local, stream=stream.cuda_stream)
+    # prerequisite input: the size-averaged Mie table (FP64 GPU kernel, once)
+    table = pdv.phase_table(ctx, wl)
+    th_pin = torch.from_numpy(np.ascontiguousarray(table[0])).pin_memory()
+    p_pin = torch.from_numpy(np.ascontiguousarray(table[1])).pin_memory()
+    dev_out = {"spectrum": torch.zeros(ns * nb, dtype=torch.float64, device=dev),
+               "counters": torch.zeros(ns * 14, dtype=torch.int64, device=dev)}
+    host_spec = torch.zeros(ns * nb, dtype=torch.float64).pin_memory()
+    host_cnt = torch.zeros(ns * 14, dtype=torch.int64).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    tbl = (th_pin.numpy(), p_pin.numpy(), table[2], table[3])
+
+    def step(precision, device_outputs):
+        cloud = pdv.Cloud(ctx, wl, table=tbl)            # a1-a3 on the device
+        if device_outputs:
+            req = pdv.Request(cloud, wl, precision=precision, device_out=dev_out)
+        else:
+            req = pdv.Request(cloud, wl, precision=precision, raw=False, counters=True)
+            req.spectrum = host_spec.numpy().reshape(ns, nb)
+            req.c.out_spectrum = host_spec.data_ptr()
+        pdv.pdv_simulate_spectrum(ctx.handle, req.c)    # a4-a14
+        ev = ctx.stats()["last_events"]
+        cloud.close()
+        return ev, ctx.stats()["last_transport_ms"]
+
+    def scat_per_step():
+        return int(dev_out["counters"].view(ns, 14)[0, 2].item())
+
+    def timed(precision, device_outputs, steps, warmup):
+        for _ in range(warmup):
+            step(precision, device_outputs)
+        barrier()
+        l0 = ctx.stats()["kernel_launches"]
+        times, kern, events = [], [], 0
+        for _ in range(steps):
+            flush.zero_()                                  # L2 flushed between steps
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ev, kms = step(precision, device_outputs)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            kern.append(kms)
+            events += ev
+        barrier()
+        launches = ctx.stats()["kernel_launches"] - l0
+        return times, kern, events, launches
+
+    clocks = Clocks(local)
+    # ---- device-resident value
+    clocks.start()
+    t_ms, k_ms, events, launches = timed("fp32", True, args.steps, args.warmup)
+    clk = clocks.stop()
+    scat = scat_per_step()
+    total_s = sum(t_ms) / 1e3
+    # ---- end to end through the public API with host buffers
+    e_ms, _, _, _ = timed("fp32", False, max(2, args.steps // 2), 1)
+    # ---- plain FP64 GPU path on the same workload
+    f_ms, fk_ms, f_events, _ = timed("fp64", True, args.fp64_steps, 1)
+    f_scat = scat_per_step()
+
+    vals = torch.tensor([total_s, sum(e_ms) / 1e3, sum(f_ms) / 1e3], dtype=torch.float64,
+                        device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
+    total_s, e_s, f_s = [float(x) for x in vals.cpu()]
+    steps = args.steps
+    value = world * scat * steps / total_s
+    spectra = world * ns * steps / total_s
+    e_steps = max(2, args.steps // 2)
+    e2e_value = world * scat * e_steps / e_s
+    f_value = world * f_scat * args.fp64_steps / f_s
+
+    kern_ms = statistics.mean(k_ms)
+    ev_per_launch = events / steps
+    achieved = ALGO_INST_PER_EVENT * ev_per_launch / (kern_ms / 1e3) / 1e9
+    peak = SMS * SCHEDULERS * LANES * F_MAX_HZ / 1e9
+    prof = profile_counters()
+    traffic = prof["dram_bytes_per_event"] * ev_per_launch if prof else None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded cloud of the paper's workload shape; no dataset)",
+        "config": {
+            "workload": "cfg2: log-normal Mie cloud d_m=3um sigma=0.5 m=3+9i lambda=1550nm, "
+                        "5 mg/cm^2 tin, beta=5, %d snapshots 0.5-5us, %.0e packets per snapshot, "
+                        "%d bins 0-8000 m/s, FP32 transport" % (ns, wl.n_packets, nb),
+            "packets_per_snapshot": wl.n_packets, "snapshots": ns, "bins": nb,
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "flushed between steps (256 MiB write)",
+        },
+        "spectra_per_s": spectra,
+        "events_per_s": world * (events / steps) * steps / total_s,
+        "packet_histories_per_s": world * wl.n_packets * steps / total_s,
+        "fp64_plain": {"value": f_value, "unit": UNIT, "ms_per_step": 1e3 * f_s / args.fp64_steps,
+                       "spectra_per_s": world * ns * args.fp64_steps / f_s,
+                       "kernel_ms": statistics.mean(fk_ms)},
+        "speedup_vs_fp64_plain": value / f_value if f_value else None,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(th_pin.numel() * 8 + p_pin.numel() * 8 + ns * 8),
+                "d2h_bytes_per_step": int(ns * nb * 8 + ns * 112)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Ginst/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_transport_f32", "kernel_ms": kern_ms,
+                     "algo_inst_per_event": ALGO_INST_PER_EVENT,
+                     "peak_basis": "152 SM x 4 schedulers x 32 lanes x 2070 MHz (issue rate)"},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample(wl, args.cpu_seconds, os.cpu_count() or 1)
+        line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": os.cpu_count() or 1,
+                                "kind": "oracle",
+                                "sample": "%d packets x %d snapshots (%.1f s)" % (
+                                    cb["packets"], cb["snapshots"], cb["seconds"]),
+                                "spectra_per_s": cb["spectra_per_s"]}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,244 @@
+/*
+ * pdv.h — C ABI of libpdv: GB300-native Monte Carlo simulation of the photon
+ * Doppler velocimetry (PDV) spectrum of a shock-ejected particle cloud in
+ * vacuum (Shi et al., "Reconstruction and interpretation of photon Doppler
+ * velocimetry spectrum for ejecta particles from shock-loaded sample in
+ * vacuum", arXiv:2012.00963, Section II).
+ *
+ * Conventions
+ *  - Every function returns pdv_status: 0 on success, a negative code on
+ *    error. pdv_last_error() returns a message for the calling thread's last
+ *    error (valid until that thread's next failing call).
+ *  - Host arrays passed in are caller-owned and copied during the call.
+ *  - Device objects (contexts, clouds, tables) are library-owned and are
+ *    released by the matching destroy function.
+ *  - Output buffers are caller-owned: host memory by default, device memory
+ *    when the request sets PDV_OUT_DEVICE.
+ *  - Units at the ABI follow the paper: area mass mg/cm^2, diameter um,
+ *    wavelength nm, probe lengths mm, snapshot times us, velocities m/s.
+ *  - Nothing here needs a particular framework: streams are plain
+ *    cudaStream_t values passed as void*.
+ */
+#ifndef PDV_H
+#define PDV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pdv_ctx pdv_ctx;
+typedef struct pdv_cloud pdv_cloud;
+typedef uint64_t pdv_ticket;
+
+typedef enum {
+  PDV_OK = 0,
+  PDV_EINVAL = -1,       /* invalid argument (message in pdv_last_error)      */
+  PDV_ENOMEM = -2,       /* device or host allocation failed                  */
+  PDV_ECUDA = -3,        /* a CUDA call failed                                 */
+  PDV_EAGAIN = -4,       /* admission refused: not enough device memory/slots */
+  PDV_ENOTREADY = -5,    /* request still running (pdv_poll)                  */
+  PDV_ETIMEOUT = -6,     /* a bounded wait ran out                            */
+  PDV_ECANCELLED = -7    /* request cancelled                                 */
+} pdv_status;
+
+enum { PDV_SURFACE_UNIFORM_THETA = 0, PDV_SURFACE_LAMBERT = 1, PDV_SURFACE_SPECULAR = 2 };
+enum { PDV_PROFILE_EXPONENTIAL = 0, PDV_PROFILE_TABULATED = 1 };
+enum { PDV_PREC_FP32 = 0, PDV_PREC_FP64 = 1 };
+
+/* request flags */
+#define PDV_OUT_DEVICE 0x1u   /* out_* pointers are device pointers            */
+#define PDV_PER_DV     0x2u   /* spectrum divided by the bin width (per m/s)   */
+
+/* Optional device allocator (NULL: cudaMallocAsync/cudaFreeAsync on the
+ * context stream). Both callbacks are called from library threads. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, void* stream, void* user);
+  void* user;
+} pdv_allocator;
+
+/* Particle cloud (Section II.C). Velocity profile: Eq. 20 (exponential law,
+ * truncated at v_max and renormalised) or a tabulated, piecewise-linear
+ * dm/dv > 0 on [prof_v[0], prof_v[n-1]] with prof_v[0] >= v_fs. Particles
+ * fly freely, z = v t. Sizes: number log-normal of Eq. 21 (sigma_ln = 0 for a
+ * single size); only the Sauter mean d_m exp(2.5 sigma^2) enters the optical
+ * depth (Eq. 10). */
+typedef struct {
+  double rho_kg_m3;            /* particle density                       */
+  double area_mass_mg_cm2;     /* total area mass m0 (0 = empty cloud)   */
+  double v_fs;                 /* free-surface velocity, m/s             */
+  double reflectivity;         /* free-surface reflectivity in [0, 1]    */
+  int surface_mode;            /* PDV_SURFACE_*                          */
+  int profile_kind;            /* PDV_PROFILE_*                          */
+  double beta;                 /* Eq. 20 coefficient                     */
+  double v_max;                /* m/s; 0: v_fs (1 + ln(1e6) / beta)      */
+  const double* prof_v;        /* tabulated velocities (host)            */
+  const double* prof_dmdv;     /* tabulated dm/dv (host, any scale)      */
+  int prof_n;
+  double d_median_um;          /* Eq. 21 median diameter                 */
+  double sigma_ln;             /* Eq. 21 width                           */
+  double wavelength_nm;        /* probe laser wavelength                 */
+  int table_nodes;             /* velocity nodes of the mass table (0 = 4096, max 16384) */
+} pdv_cloud_desc;
+
+/* Probe geometry: a collimated beam of radius beam_radius_mm launched along
+ * -z from the plane z = z_probe_mm; detection on the same plane within
+ * aperture_radius_mm (<= 0: unlimited) and within cone_half_angle_rad of +z
+ * (>= pi/2: every upward packet). Eq. 6 boundary conditions. */
+typedef struct {
+  double z_probe_mm;
+  double beam_radius_mm;
+  double aperture_radius_mm;
+  double cone_half_angle_rad;
+} pdv_probe;
+
+/* Per-snapshot tallies. Weights are 2^32 fixed point per launched packet;
+ * w_detected + w_under + w_over + w_escaped_undetected + w_absorbed_particle
+ * + w_absorbed_surface + w_truncated == launched * 2^32 exactly. */
+typedef struct {
+  uint64_t launched, events, scatters, surface_hits, escapes, detected;
+  uint64_t w_detected, w_under, w_over, w_escaped_undetected;
+  uint64_t w_absorbed_particle, w_absorbed_surface, w_truncated, truncated;
+} pdv_counters;
+
+/* Per-packet record (debug / parity dumps; snapshot 0 unless stated). */
+typedef struct {
+  uint32_t n_events, n_scatters, n_surface, fate;  /* fate: 1 escaped, 2 absorbed by a particle, 3 absorbed at the surface, 4 truncated */
+  uint64_t weight;                                 /* final weight, 2^32 fixed point */
+  double v_app;                                    /* apparent velocity, m/s */
+  uint64_t detect_mask;                            /* bit s: detected at snapshot s < 64 */
+} pdv_packet_record;
+
+/* One spectrum request: packets [packet_begin, packet_begin + n_packets)
+ * of the stream (seed, stream_id), tallied at every snapshot time into
+ * n_bins bins over [v_lo, v_hi). Output spectrum[s * n_bins + b] =
+ * sum of detected weights / (2^32 n_packets) (Eq. 19 without the
+ * sqrt(I0/n0) scale). Packet ranges of one stream add up exactly: raw
+ * tallies of [0, k) and [k, N) sum to those of [0, N). */
+typedef struct {
+  const pdv_cloud* cloud;
+  pdv_probe probe;
+  const double* t_snap_us;         /* host array [n_snap], each > 0      */
+  int n_snap;                      /* 1..4096                            */
+  uint64_t n_packets;              /* >= 1, <= 4e9                       */
+  uint64_t packet_begin;
+  uint64_t seed;
+  uint32_t stream_id;
+  uint32_t max_events;             /* per packet; 0 = 1e6                */
+  int n_bins;                      /* 1..65536                           */
+  double v_lo, v_hi;               /* m/s, v_hi > v_lo                   */
+  int precision;                   /* PDV_PREC_FP32 | PDV_PREC_FP64      */
+  uint32_t flags;                  /* PDV_OUT_DEVICE | PDV_PER_DV        */
+  double* out_spectrum;            /* [n_snap * n_bins], required        */
+  uint64_t* out_raw;               /* optional [n_snap * (n_bins + 2)]: under, bins, over */
+  pdv_counters* out_counters;      /* optional [n_snap]                  */
+  pdv_packet_record* out_packets;  /* optional [n_packets] (n_packets <= 2^26) */
+} pdv_request;
+
+/* Launch parameters of the persistent FP32 kernel (pdv_autotune picks them). */
+typedef struct {
+  int block_threads;               /* 128, 256, 512 (0 = 256)            */
+  int blocks_per_sm;               /* 0 = occupancy maximum              */
+  int tile_packets;                /* packets per work tile (0 = auto)   */
+  int hist_mode;                   /* 0 auto, 1 global atomics, 2 shared-memory privatised */
+} pdv_tuning;
+
+typedef struct {
+  double tau_tot;                  /* optical depth of the cloud (Eq. 10) */
+  double v_bot, v_top;             /* velocity span of the cloud, m/s     */
+  double d_sauter_um;              /* d_m exp(2.5 sigma^2)                */
+  double g_table;                  /* mean cosine of the sampled phase law */
+  double q_ext, albedo;
+  int table_nodes;
+  int has_phase;
+} pdv_cloud_info;
+
+typedef struct {
+  uint64_t kernel_launches;        /* kernels this context has launched   */
+  double last_transport_ms;        /* CUDA-event time of the last transport kernel */
+  uint64_t last_events;            /* events of the last synchronous call */
+  int transport_grid, transport_block;
+} pdv_stats;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on `device`. cuda_stream: a cudaStream_t to run on (NULL:
+ * the library creates its own non-blocking stream). alloc: optional device
+ * allocator. On error *out is NULL. */
+pdv_status pdv_ctx_create(int device, void* cuda_stream, const pdv_allocator* alloc,
+                          pdv_ctx** out);
+/* Waits for the context's work, stops the serving thread, frees everything. */
+pdv_status pdv_ctx_destroy(pdv_ctx* ctx);
+const char* pdv_last_error(void);
+pdv_status pdv_get_stats(pdv_ctx* ctx, pdv_stats* out);
+pdv_status pdv_set_tuning(pdv_ctx* ctx, const pdv_tuning* tuning);
+
+/* ---------------------------------------------------------------- cloud */
+
+/* Build the cloud's cumulative mass-fraction table on the device in FP64
+ * (Eq. 20, z = v t). The cloud is usable once a phase table is set.
+ * Errors: PDV_EINVAL (rho <= 0, m0 < 0, d_m <= 0, sigma < 0, R outside [0,1],
+ * v_fs <= 0, v_max <= v_fs, bad tabulated profile), PDV_ENOMEM, PDV_ECUDA. */
+pdv_status pdv_create_cloud(pdv_ctx* ctx, const pdv_cloud_desc* desc, pdv_cloud** out);
+
+/* Set the phase function p(theta) (Eq. 13, unnormalised, >= 0, theta strictly
+ * increasing from 0 to pi, n in 2..65536), the size-averaged extinction
+ * efficiency Q_ext (Eq. 10) and the single-scattering albedo K_sca/K_ext
+ * (Eq. 11). Builds the integer inverse CDF on the device in FP64. */
+pdv_status pdv_set_phase_table(pdv_cloud* cloud, int n, const double* theta_rad,
+                               const double* p, double q_ext_eff, double albedo);
+pdv_status pdv_cloud_get_info(const pdv_cloud* cloud, pdv_cloud_info* out);
+pdv_status pdv_destroy_cloud(pdv_cloud* cloud);
+
+/* Henyey–Greenstein p(theta) on n uniform angles over [0, pi] (host helper). */
+pdv_status pdv_phase_hg(double g, int n, double* theta_rad, double* p);
+
+/* Size-averaged Mie phase table (Eq. 12-14, Eq. 21) computed on the device in
+ * FP64: theta_rad[n_angle] uniform over [0, pi], p[n_angle] proportional to
+ * <|S1|^2 + |S2|^2>, Q_ext = <d^2 Q_ext>/<d^2>, albedo = <C_sca>/<C_ext>,
+ * g = <C_sca g>/<C_sca>. Gauss–Legendre in ln d over ln d_m +- 6 sigma with
+ * n_size nodes (sigma = 0: one size). Outputs are host arrays. Errors:
+ * PDV_EINVAL (m_im < 0, sizes <= 0, n_angle < 2, size parameter > 20000). */
+pdv_status pdv_mie_table(pdv_ctx* ctx, double m_re, double m_im, double wavelength_nm,
+                         double d_median_um, double sigma_ln, int n_size, int n_angle,
+                         double* theta_rad, double* p, double* q_ext_eff, double* albedo,
+                         double* g);
+
+/* ---------------------------------------------------------------- spectra */
+
+/* Run one request to completion (blocking): transport all packets, tally,
+ * normalise and copy the outputs. Errors: PDV_EINVAL (see pdv_request; also
+ * a snapshot with the top of the cloud at or above the probe plane),
+ * PDV_ENOMEM, PDV_ECUDA. */
+pdv_status pdv_simulate_spectrum(pdv_ctx* ctx, const pdv_request* req);
+
+/* Run n requests in one persistent launch (FP32 requests only; FP64 requests
+ * run one after another), replayed from a captured CUDA graph cached per
+ * batch shape. Outputs as for pdv_simulate_spectrum. */
+pdv_status pdv_simulate_batch(pdv_ctx* ctx, const pdv_request* reqs, int n);
+
+/* Time candidate launch parameters on a short version of the batch and keep
+ * the fastest in the context (and in *out if not NULL). */
+pdv_status pdv_autotune(pdv_ctx* ctx, const pdv_request* reqs, int n, pdv_tuning* out);
+
+/* ---------------------------------------------------------------- serving */
+
+/* Admit a request into the context's continuous-batching loop. The request's
+ * cloud and output buffers must stay valid until pdv_poll reports completion.
+ * Returns PDV_EAGAIN when device memory or request slots do not allow it now. */
+pdv_status pdv_submit(pdv_ctx* ctx, const pdv_request* req, pdv_ticket* out);
+
+/* Wait up to timeout_us for a ticket: PDV_OK (done, outputs written, ticket
+ * released), PDV_ENOTREADY (still running), or the request's error. */
+pdv_status pdv_poll(pdv_ctx* ctx, pdv_ticket ticket, uint32_t timeout_us);
+
+/* Cancel a queued or running request; its ticket then polls PDV_ECANCELLED. */
+pdv_status pdv_cancel(pdv_ctx* ctx, pdv_ticket ticket);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDV_H */

@@ -1,0 +1,158 @@
+// pdv_internal.cuh — device-side data layout and helpers of libpdv.
+//
+// The transport follows the Monte Carlo of arXiv:2012.00963 Section II:
+// launch (Eq. 6), Beer–Lambert free path (Eq. 7, Eq. 10), scatter/absorb
+// (Eq. 11), phase-function angle (Eq. 13-15), rotation (Eq. 16-17), Doppler
+// update (Eq. 4, Eq. 18), diffuse free-surface reflection, tally (Eq. 19).
+//
+// Packet state on the optical-depth axis is the cumulative mass fraction
+// S = T / tau_tot of the cloud below the packet (0 at the free surface, 1 at
+// the top). The FP32 path holds S as a 62-bit fixed-point integer and inverts
+// the velocity table with integer compares; the table itself is built in FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pdv.h"
+
+namespace pdv {
+
+constexpr unsigned long long kOneQ = 1ull << 62;     // S = 1 in 2^62 fixed point
+constexpr double kTwo62 = 4611686018427387904.0;
+constexpr double kTwo32 = 4294967296.0;
+constexpr int kMaxTableNodes = 16384;
+constexpr int kMaxPhase = 65536;
+constexpr int kMaxSnap = 4096;
+constexpr int kMaxBins = 65536;
+constexpr int kGuidePhaseLog = 12;                   // 4096 guide cells over the 2^24 CDF
+
+// Snapshot-independent counter slots of one request (device array of u64).
+enum Counter {
+  C_LAUNCHED = 0,
+  C_EVENTS,
+  C_SCATTERS,
+  C_SURFACE_HITS,
+  C_ESCAPES,
+  C_W_ESCAPED,          // total escaped weight (split per snapshot at normalisation)
+  C_W_ABS_PARTICLE,
+  C_W_ABS_SURFACE,
+  C_W_TRUNCATED,
+  C_TRUNCATED,
+  C_NCOUNT
+};
+
+// Per-snapshot histogram row: [under, bin 0 .. bin n-1, over, detected count].
+__host__ __device__ inline int hist_row(int n_bins) { return n_bins + 3; }
+
+// Device tables of one cloud.
+struct CloudTables {
+  // cumulative mass fraction at velocity nodes v_j = v_bot + j dv, j = 0..n_v
+  unsigned long long* Sq = nullptr;   // [n_v + 1] S_j * 2^62 (u64)
+  double* Sd = nullptr;               // [n_v + 1] S_j (FP64 path)
+  float* w = nullptr;                 // [n_v] dv / (Sq_{j+1} - Sq_j)
+  unsigned short* G = nullptr;        // [n_g + 1] guide: largest j <= n_v-1, Sq_j <= k 2^62 / n_g
+  int n_v = 0, n_g = 0, g_shift = 0;
+  // phase function
+  unsigned* Cq = nullptr;             // [n_p] integer CDF, 2^24 scale
+  float* th = nullptr;                // [n_p] theta (f32)
+  float* dthq = nullptr;              // [n_p] (theta_{i+1} - theta_i) / (Cq_{i+1} - Cq_i)
+  double* th_d = nullptr;             // [n_p] theta (FP64 path)
+  unsigned short* Gp = nullptr;       // [n_gp + 1] guide over the 2^24 CDF
+  int n_p = 0;
+};
+
+// Everything the transport needs for one request ("set"), by value.
+struct SetDesc {
+  const unsigned long long* Sq;
+  const double* Sd;
+  const float* w;
+  const unsigned short* G;
+  const unsigned* Cq;
+  const float* th;
+  const float* dthq;
+  const double* th_d;
+  const unsigned short* Gp;
+  const double* t_snap;               // [n_snap] seconds
+  unsigned long long* hist;           // [n_snap][n_bins + 3]
+  unsigned long long* cnt;            // [C_NCOUNT]
+  pdv_packet_record* packets;         // optional [n_packets]
+  int n_v, n_g, g_shift, n_p;
+  int n_snap, n_bins;
+  int surface_mode, cone_all, ap_all, pad0;
+  unsigned omega_q, stream_id, max_events, pad1;
+  unsigned long long R_q, seed, packet_begin, n_packets;
+  unsigned long long norm_packets;    // packets of the whole request (normalisation)
+  double tau_tot, inv_tau, v_bot, dv, v_top, v_fs;
+  double z_probe, r_beam, r_ap2, cos_alpha, v_lo, inv_dbin;
+  float inv_tau_f, v_bot_f, dv_f, v_top_f, v_fs_f, z_probe_f, r_beam_f, r_ap2_f;
+  float cos_alpha_f, v_lo_f, inv_dbin_f, pad2;
+};
+
+// ------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of the 4x32 S-box with the
+// published multipliers and Weyl key increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    if (i) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// Uniform in (0, 1): ((r >> 9) + 1/2) 2^-23, exact in binary32 and binary64.
+__device__ __forceinline__ float u23f(unsigned r) {
+  return fmaf(__uint2float_rn(r >> 9), 1.0f / 8388608.0f, 1.0f / 16777216.0f);
+}
+__device__ __forceinline__ double u23d(unsigned r) {
+  return ((double)(r >> 9) + 0.5) * (1.0 / 8388608.0);
+}
+
+// x * 2^62 truncated towards zero for |x| < 1 (binary32 -> 64-bit integer with
+// integer instructions only).
+__device__ __forceinline__ long long fix62(float x) {
+  const unsigned b = __float_as_uint(x);
+  const int e = (int)((b >> 23) & 0xffu);
+  const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+  const int sh = e - 88;                       // value = m * 2^(e - 150) * 2^62
+  long long v;
+  if (sh >= 0) v = m << sh;
+  else v = (sh > -40) ? (m >> (-sh)) : 0ll;
+  if (e == 0) v = 0;
+  return (b >> 31) ? -v : v;
+}
+
+// unsigned 64-bit integer (< 2^63) to binary32.
+__device__ __forceinline__ float u64_to_f(unsigned long long d) {
+  return fmaf(__uint2float_rn((unsigned)(d >> 32)), 4294967296.0f, __uint2float_rn((unsigned)d));
+}
+
+// Kernel entry points (defined in the .cu files).
+void launch_transport_f32(const SetDesc* d_sets, int n_sets, unsigned long long* d_set_ctr,
+                          int grid, int block, size_t smem, int hist_mode, bool dump,
+                          cudaStream_t st);
+void launch_transport_f64(const SetDesc* d_set, int grid, int block, cudaStream_t st);
+void launch_normalise(const SetDesc* d_sets, int n_sets, double* const* d_spec,
+                      pdv_counters* const* d_cnt_out, unsigned long long* const* d_raw,
+                      const unsigned* flags, int max_snap, cudaStream_t st);
+size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode);
+int transport_f32_max_smem();
+cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, int* blocks);
+
+cudaError_t build_mass_table(int kind, double beta, double v_fs, double v_bot, double v_top,
+                             const double* d_prof_v, const double* d_prof_f, int prof_n,
+                             double* d_prof_cum, int n_v, CloudTables* t, cudaStream_t st);
+cudaError_t build_phase_cdf(const double* d_theta, const double* d_p, int n, double* d_work,
+                            CloudTables* t, double* d_gtab, cudaStream_t st);
+cudaError_t mie_table_device(double m_re, double m_im, double wavelength, double d_m,
+                             double sigma, int n_size, int n_angle, double* d_theta, double* d_p,
+                             double* d_q3, cudaStream_t st, void* (*alloc)(size_t, void*),
+                             void (*dealloc)(void*, void*), void* user);
+
+}  // namespace pdv

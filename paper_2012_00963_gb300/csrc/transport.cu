@@ -1,0 +1,664 @@
+// transport.cu — Monte Carlo photon-packet transport (arXiv:2012.00963,
+// Section II.B steps (1)-(7)) and the tally normalisation (Eq. 19).
+//
+// k_transport_f32: persistent kernel. Blocks walk the list of request sets;
+// for each set with packets left they stage the set's tables in shared
+// memory, then every warp claims chunks of packets from the set's global
+// counter and keeps its 32 lanes busy: a lane whose packet ends (escape,
+// absorption, surface loss, event limit) launches the next packet of the
+// warp's chunk in the same iteration. Packet state: 62-bit fixed-point mass
+// fraction S (optical depth T = tau_tot S above the free surface), binary32
+// direction and lateral displacement, 2^32 fixed-point weight. Tallies are
+// 64-bit integer atomics, so results do not depend on scheduling.
+//
+// k_transport_f64: the plain FP64 path, one packet per thread at a time,
+// tables read from global memory, FP64 throughout.
+//
+// Both kernels transport a packet once and test detection at every snapshot
+// time: the cloud is self-similar (z = v t, Section II.C), so event decisions
+// and the Doppler sum do not depend on t, and the lateral position at time t
+// is x0 + t X with X accumulated in velocity units.
+#include <math.h>
+
+#include "pdv_internal.cuh"
+
+namespace pdv {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned kChunk = 64;          // packets claimed per warp refill
+
+struct SmemTables {
+  const unsigned long long* Sq;
+  const float* w;
+  const unsigned short* G;
+  const unsigned* Cq;
+  const float* th;
+  const float* dthq;
+  const unsigned short* Gp;
+  const float* ts;
+  unsigned long long* hist;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Shared-memory bytes for one set's staged tables (and optional histogram).
+__host__ __device__ inline size_t smem_layout(int n_v, int n_g, int n_p, int n_snap, int n_bins,
+                                              int hist_mode, size_t* off) {
+  size_t o = 0;
+  off[0] = o; o = align16(o + sizeof(unsigned long long) * (size_t)(n_v + 1));   // Sq
+  off[1] = o; o = align16(o + sizeof(float) * (size_t)n_v);                       // w
+  off[2] = o; o = align16(o + sizeof(unsigned short) * (size_t)(n_g + 1));        // G
+  off[3] = o; o = align16(o + sizeof(unsigned) * (size_t)n_p);                    // Cq
+  off[4] = o; o = align16(o + sizeof(float) * (size_t)n_p);                       // th
+  off[5] = o; o = align16(o + sizeof(float) * (size_t)n_p);                       // dthq
+  off[6] = o; o = align16(o + sizeof(unsigned short) * ((1 << kGuidePhaseLog) + 1));  // Gp
+  off[7] = o; o = align16(o + sizeof(float) * (size_t)n_snap);                    // ts
+  off[8] = o;
+  if (hist_mode == 2) o = align16(o + sizeof(unsigned long long) * (size_t)n_snap * hist_row(n_bins));
+  return o;
+}
+
+size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode) {
+  size_t off[9];
+  return smem_layout(n_v, n_g, n_p, n_snap, n_bins, hist_mode, off);
+}
+
+__device__ __forceinline__ int search_mass(const unsigned long long* Sq, const unsigned short* G,
+                                           int g_shift, int n_g, unsigned long long s) {
+  unsigned kg = (unsigned)(s >> g_shift);
+  if (kg > (unsigned)(n_g - 1)) kg = (unsigned)(n_g - 1);
+  int lo = G[kg], hi = G[kg + 1];
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (Sq[mid] <= s) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int search_phase(const unsigned* Cq, const unsigned short* Gp,
+                                            unsigned m) {
+  const unsigned c = m >> (24 - kGuidePhaseLog);
+  int lo = Gp[c], hi = Gp[c + 1];
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (Cq[mid] <= m) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float term) {
+  const float y = term - comp;
+  const float t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <bool DUMP, int HMODE>
+__global__ void __launch_bounds__(256) k_transport_f32(const SetDesc* __restrict__ sets,
+                                                       int n_sets,
+                                                       unsigned long long* __restrict__ set_ctr) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ SetDesc sd;
+  __shared__ unsigned long long s_cnt[C_NCOUNT];
+  __shared__ int s_go;
+
+  const int lane = threadIdx.x & 31;
+  const int start = (int)(((long long)blockIdx.x * n_sets) / gridDim.x);
+
+  for (int step = 0; step < n_sets; ++step) {
+    const int si = (start + step) % n_sets;
+    if (threadIdx.x == 0) {
+      const unsigned long long c = *((volatile unsigned long long*)&set_ctr[si]);
+      s_go = c < sets[si].n_packets;
+    }
+    __syncthreads();
+    const int go = s_go;
+    __syncthreads();
+    if (!go) continue;
+
+    // ---- stage the set descriptor and its tables in shared memory
+    {
+      const int* src = reinterpret_cast<const int*>(&sets[si]);
+      int* dst = reinterpret_cast<int*>(&sd);
+      for (int i = threadIdx.x; i < (int)(sizeof(SetDesc) / sizeof(int)); i += blockDim.x)
+        dst[i] = src[i];
+      if (threadIdx.x < C_NCOUNT) s_cnt[threadIdx.x] = 0ull;
+    }
+    __syncthreads();
+    size_t off[9];
+    smem_layout(sd.n_v, sd.n_g, sd.n_p, sd.n_snap, sd.n_bins, HMODE, off);
+    SmemTables tb;
+    tb.Sq = reinterpret_cast<const unsigned long long*>(smem + off[0]);
+    tb.w = reinterpret_cast<const float*>(smem + off[1]);
+    tb.G = reinterpret_cast<const unsigned short*>(smem + off[2]);
+    tb.Cq = reinterpret_cast<const unsigned*>(smem + off[3]);
+    tb.th = reinterpret_cast<const float*>(smem + off[4]);
+    tb.dthq = reinterpret_cast<const float*>(smem + off[5]);
+    tb.Gp = reinterpret_cast<const unsigned short*>(smem + off[6]);
+    tb.ts = reinterpret_cast<const float*>(smem + off[7]);
+    tb.hist = HMODE == 2 ? reinterpret_cast<unsigned long long*>(smem + off[8]) : sd.hist;
+    {
+      unsigned long long* Sq = reinterpret_cast<unsigned long long*>(smem + off[0]);
+      for (int i = threadIdx.x; i <= sd.n_v; i += blockDim.x) Sq[i] = sd.Sq[i];
+      float* w = reinterpret_cast<float*>(smem + off[1]);
+      for (int i = threadIdx.x; i < sd.n_v; i += blockDim.x) w[i] = sd.w[i];
+      unsigned short* G = reinterpret_cast<unsigned short*>(smem + off[2]);
+      for (int i = threadIdx.x; i <= sd.n_g; i += blockDim.x) G[i] = sd.G[i];
+      unsigned* Cq = reinterpret_cast<unsigned*>(smem + off[3]);
+      float* th = reinterpret_cast<float*>(smem + off[4]);
+      float* dthq = reinterpret_cast<float*>(smem + off[5]);
+      for (int i = threadIdx.x; i < sd.n_p; i += blockDim.x) {
+        Cq[i] = sd.Cq[i];
+        th[i] = sd.th[i];
+        dthq[i] = sd.dthq[i];
+      }
+      unsigned short* Gp = reinterpret_cast<unsigned short*>(smem + off[6]);
+      for (int i = threadIdx.x; i <= (1 << kGuidePhaseLog); i += blockDim.x) Gp[i] = sd.Gp[i];
+      float* ts = reinterpret_cast<float*>(smem + off[7]);
+      for (int i = threadIdx.x; i < sd.n_snap; i += blockDim.x) ts[i] = (float)sd.t_snap[i];
+      if (HMODE == 2) {
+        unsigned long long* h = reinterpret_cast<unsigned long long*>(smem + off[8]);
+        const int nh = sd.n_snap * hist_row(sd.n_bins);
+        for (int i = threadIdx.x; i < nh; i += blockDim.x) h[i] = 0ull;
+      }
+    }
+    __syncthreads();
+
+    // ---- per-set constants in registers
+    const uint2 key = make_uint2((unsigned)sd.seed, (unsigned)(sd.seed >> 32));
+    const unsigned sid = sd.stream_id;
+    const unsigned long long n_pk = sd.n_packets, base_pk = sd.packet_begin;
+    const float inv_tau = sd.inv_tau_f;
+    const int n_bins = sd.n_bins, row = hist_row(sd.n_bins), n_snap = sd.n_snap;
+
+    // ---- warp loop
+    unsigned long long pool_next = 0, pool_end = 0;
+    bool exhausted = false, alive = false;
+    unsigned long long pk = 0, W = 0;
+    long long Sq = 0;
+    unsigned kev = 0, nev = 0, nsca = 0, nsurf = 0;
+    unsigned long long dmask = 0;
+    float vcur = 0.f, ux = 0.f, uy = 0.f, uz = -1.f, iuz = -1.f;
+    float Xx = 0.f, Xy = 0.f, x0 = 0.f, y0 = 0.f, vapp = 0.f, vcomp = 0.f;
+    unsigned st_launch = 0, st_events = 0, st_scat = 0, st_surf = 0;
+
+    for (;;) {
+      // refill dead lanes from the warp's chunk of packets
+      unsigned need = __ballot_sync(kFull, !alive);
+      while (need) {
+        const unsigned long long avail = pool_end - pool_next;
+        if (avail == 0) {
+          if (exhausted) break;
+          unsigned long long b = 0;
+          if (lane == 0) b = atomicAdd(&set_ctr[si], (unsigned long long)kChunk);
+          b = __shfl_sync(kFull, b, 0);
+          if (b >= n_pk) {
+            exhausted = true;
+            break;
+          }
+          pool_next = b;
+          pool_end = b + kChunk < n_pk ? b + kChunk : n_pk;
+          continue;
+        }
+        const unsigned cnt = __popc(need);
+        const unsigned take = (unsigned)(avail < cnt ? avail : cnt);
+        const unsigned rank = __popc(need & lanemask_lt());
+        if (!alive && rank < take) {
+          // Step (1): launch on the beam disk (event 0), moving along -z
+          pk = base_pk + pool_next + rank;
+          const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), 0u, sid), key);
+          const float rad = sd.r_beam_f * sqrtf(u23f(r.x));
+          float sp, cp;
+          sincospif(2.0f * u23f(r.y), &sp, &cp);
+          x0 = rad * cp;
+          y0 = rad * sp;
+          ux = 0.f; uy = 0.f; uz = -1.f; iuz = -1.f;
+          Sq = (long long)kOneQ;
+          vcur = sd.v_top_f;
+          Xx = 0.f; Xy = 0.f; vapp = 0.f; vcomp = 0.f;
+          W = 1ull << 32;
+          kev = 1; nev = 0;
+          if (DUMP) { nsca = 0; nsurf = 0; dmask = 0; }
+          ++st_launch;
+          alive = true;
+        }
+        pool_next += take;
+        need = __ballot_sync(kFull, !alive);
+      }
+      if (!__any_sync(kFull, alive)) break;
+      if (!alive) continue;
+
+      // ---- one flight and what ends it
+      const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), kev, sid), key);
+      ++kev;
+      const float tau = -logf(u23f(r.x));                // Step (3): Beer–Lambert
+      int what;                                          // 0 interact, 1 escape, 2 surface, 3 horizontal
+      long long Sn = Sq;
+      if (fabsf(uz) < 1e-9f) {
+        what = 3;
+      } else {
+        const float dS = tau * uz * inv_tau;
+        if (dS >= 1.0f) what = 1;
+        else if (dS <= -1.0f) what = 2;
+        else {
+          Sn = Sq + fix62(dS);
+          what = (Sn >= (long long)kOneQ) ? 1 : (Sn <= 0 ? 2 : 0);
+        }
+      }
+      unsigned fate = 0;
+      if (what == 1) {
+        // Step (6): out through the top, vacuum flight to the probe plane
+        const float tx = ux * iuz, ty = uy * iuz;
+        Xx = fmaf(tx, sd.v_top_f - vcur, Xx);
+        Xy = fmaf(ty, sd.v_top_f - vcur, Xy);
+        if (sd.cone_all || uz >= sd.cos_alpha_f) {
+          const float ax = fmaf(tx, sd.z_probe_f, x0), ay = fmaf(ty, sd.z_probe_f, y0);
+          const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
+          const float fb = floorf((vapp - vcomp - sd.v_lo_f) * sd.inv_dbin_f);
+          const int idx = fb < 0.0f ? 0 : (fb >= (float)n_bins ? n_bins + 1 : (int)fb + 1);
+          for (int s = 0; s < n_snap; ++s) {
+            const float t = tb.ts[s];
+            const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
+            if (sd.ap_all || fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
+              // Eq. 19: tally the out-photon at its frequency shift
+              atomicAdd(&tb.hist[(size_t)s * row + idx], W);
+              atomicAdd(&tb.hist[(size_t)s * row + n_bins + 2], 1ull);
+              if (DUMP && s < 64) dmask |= 1ull << s;
+            }
+          }
+        }
+        atomicAdd(&s_cnt[C_ESCAPES], 1ull);
+        atomicAdd(&s_cnt[C_W_ESCAPED], W);
+        fate = 1;
+      } else if (what == 2) {
+        // Step (6): reaches the free surface z = v_fs t
+        Xx = fmaf(ux * iuz, sd.v_fs_f - vcur, Xx);
+        Xy = fmaf(uy * iuz, sd.v_fs_f - vcur, Xy);
+        Sq = 0;
+        vcur = sd.v_fs_f;
+        ++nev; ++st_events; ++st_surf;
+        if (DUMP) ++nsurf;
+        const unsigned long long Wn =
+            sd.R_q >= (1ull << 32) ? W : ((W * sd.R_q + (1ull << 31)) >> 32);
+        if (Wn != W) atomicAdd(&s_cnt[C_W_ABS_SURFACE], W - Wn);
+        W = Wn;
+        float nx, ny, nz;
+        if (sd.surface_mode == PDV_SURFACE_SPECULAR) {
+          nx = ux; ny = uy; nz = -uz;
+        } else {
+          float ct, st;
+          if (sd.surface_mode == PDV_SURFACE_LAMBERT) {
+            const float a = u23f(r.y);
+            ct = sqrtf(a);
+            st = sqrtf(1.0f - a);
+          } else {
+            sincospif(0.5f * u23f(r.y), &st, &ct);     // polar angle uniform in [0, pi/2)
+          }
+          float sp, cp;
+          sincospif(2.0f * u23f(r.z), &sp, &cp);
+          nx = st * cp; ny = st * sp; nz = ct;
+        }
+        kahan_add(vapp, vcomp, 0.5f * (nz - uz) * sd.v_fs_f);   // moving wall
+        ux = nx; uy = ny; uz = nz; iuz = __frcp_rn(nz);
+        if (W == 0) fate = 3;
+      } else {
+        float vn = vcur;
+        if (what == 0) {
+          const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sn);
+          const float fd = u64_to_f((unsigned long long)Sn - tb.Sq[j]);
+          vn = fmaf(fd, tb.w[j], fmaf((float)j, sd.dv_f, sd.v_bot_f));
+          Xx = fmaf(ux * iuz, vn - vcur, Xx);
+          Xy = fmaf(uy * iuz, vn - vcur, Xy);
+        } else {
+          // horizontal packet: lateral path tau / mu(z) in velocity units
+          const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sq);
+          const float len = tau * inv_tau * tb.w[j] * 4.611686018427388e18f;
+          Xx = fmaf(ux, len, Xx);
+          Xy = fmaf(uy, len, Xy);
+        }
+        Sq = Sn;
+        vcur = vn;
+        ++nev; ++st_events;
+        if ((r.y >> 8) < sd.omega_q) {
+          // Step (4): scattering, Eq. 13-17
+          const unsigned m2 = r.z >> 8;
+          const int i = search_phase(tb.Cq, tb.Gp, m2);
+          const float th = fmaf((float)(m2 - tb.Cq[i]) + 0.5f, tb.dthq[i], tb.th[i]);
+          float st, ct, sp, cp;
+          sincosf(th, &st, &ct);
+          sincospif(2.0f * u23f(r.w), &sp, &cp);
+          float nx, ny, nz;
+          if (fabsf(uz) > 1.0f - 1e-6f) {
+            nx = st * cp; ny = st * sp; nz = uz >= 0.0f ? ct : -ct;   // Eq. 17: cos(theta) sign(u_z)
+          } else {
+            const float s = sqrtf(fmaf(ux, ux, uy * uy));
+            const float a = st / s;
+            nx = fmaf(a, fmaf(ux * uz, cp, -uy * sp), ux * ct);
+            ny = fmaf(a, fmaf(uy * uz, cp, ux * sp), uy * ct);
+            nz = fmaf(-st * cp, s, uz * ct);
+          }
+          const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+          nx *= inv_n; ny *= inv_n; nz *= inv_n;
+          kahan_add(vapp, vcomp, 0.5f * (nz - uz) * vn);      // Eq. 4 / Eq. 18
+          ux = nx; uy = ny; uz = nz; iuz = __frcp_rn(nz);
+          ++st_scat;
+          if (DUMP) ++nsca;
+        } else {
+          atomicAdd(&s_cnt[C_W_ABS_PARTICLE], W);             // Eq. 11: absorbed
+          fate = 2;
+        }
+      }
+      if (fate == 0 && nev >= sd.max_events) {
+        atomicAdd(&s_cnt[C_W_TRUNCATED], W);
+        atomicAdd(&s_cnt[C_TRUNCATED], 1ull);
+        fate = 4;
+      }
+      if (fate) {
+        if (DUMP && sd.packets) {
+          pdv_packet_record rec;
+          rec.n_events = nev;
+          rec.n_scatters = nsca;
+          rec.n_surface = nsurf;
+          rec.fate = fate;
+          rec.weight = W;
+          rec.v_app = (double)vapp - (double)vcomp;
+          rec.detect_mask = dmask;
+          sd.packets[pk - base_pk] = rec;
+        }
+        alive = false;
+      }
+    }
+
+    // ---- flush this set's tallies
+    {
+      unsigned a = st_launch, b = st_events, c = st_scat, d = st_surf;
+      for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(kFull, a, o);
+        b += __shfl_xor_sync(kFull, b, o);
+        c += __shfl_xor_sync(kFull, c, o);
+        d += __shfl_xor_sync(kFull, d, o);
+      }
+      if (lane == 0) {
+        atomicAdd(&s_cnt[C_LAUNCHED], (unsigned long long)a);
+        atomicAdd(&s_cnt[C_EVENTS], (unsigned long long)b);
+        atomicAdd(&s_cnt[C_SCATTERS], (unsigned long long)c);
+        atomicAdd(&s_cnt[C_SURFACE_HITS], (unsigned long long)d);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < C_NCOUNT && s_cnt[threadIdx.x])
+      atomicAdd(&sd.cnt[threadIdx.x], s_cnt[threadIdx.x]);
+    if (HMODE == 2) {
+      const int nh = n_snap * row;
+      for (int i = threadIdx.x; i < nh; i += blockDim.x) {
+        const unsigned long long v = tb.hist[i];
+        if (v) atomicAdd(&sd.hist[i], v);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+static const void* f32_kernel(int hist_mode, bool dump) {
+  if (dump) return hist_mode == 2 ? (const void*)k_transport_f32<true, 2> : (const void*)k_transport_f32<true, 1>;
+  return hist_mode == 2 ? (const void*)k_transport_f32<false, 2> : (const void*)k_transport_f32<false, 1>;
+}
+
+int transport_f32_max_smem() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v - (int)(sizeof(SetDesc) + sizeof(unsigned long long) * C_NCOUNT + 64);
+}
+
+cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, int* blocks) {
+  const void* k = f32_kernel(hist_mode, dump);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, block, smem);
+}
+
+void launch_transport_f32(const SetDesc* d_sets, int n_sets, unsigned long long* d_set_ctr,
+                          int grid, int block, size_t smem, int hist_mode, bool dump,
+                          cudaStream_t st) {
+  const void* k = f32_kernel(hist_mode, dump);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  void* args[] = {(void*)&d_sets, (void*)&n_sets, (void*)&d_set_ctr};
+  cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, st);
+}
+
+// ------------------------------------------------------------------ FP64
+__device__ int search_mass_d(const double* Sd, int n_v, double s) {
+  int lo = 0, hi = n_v - 1;                      // largest j <= n_v-1 with Sd_j <= s
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (Sd[mid] <= s) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict__ setp) {
+  __shared__ unsigned long long s_cnt[C_NCOUNT];
+  if (threadIdx.x < C_NCOUNT) s_cnt[threadIdx.x] = 0ull;
+  __syncthreads();
+  const SetDesc& sd = *setp;
+  const double pi = 3.14159265358979323846;
+  const uint2 key = make_uint2((unsigned)sd.seed, (unsigned)(sd.seed >> 32));
+  const int n_bins = sd.n_bins, row = hist_row(n_bins);
+  unsigned long long st_launch = 0, st_events = 0, st_scat = 0, st_surf = 0;
+  for (unsigned long long ip = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+       ip < sd.n_packets; ip += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long pk = sd.packet_begin + ip;
+    uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), 0u, sd.stream_id), key);
+    const double rad = sd.r_beam * sqrt(u23d(r.x));
+    const double psi = 2.0 * pi * u23d(r.y);
+    const double x0 = rad * cos(psi), y0 = rad * sin(psi);
+    double ux = 0.0, uy = 0.0, uz = -1.0;
+    double S = 1.0, vcur = sd.v_top, Xx = 0.0, Xy = 0.0, vapp = 0.0;
+    unsigned long long W = 1ull << 32, dmask = 0;
+    unsigned nev = 0, nsca = 0, nsurf = 0, fate = 0;
+    ++st_launch;
+    for (unsigned k = 1; fate == 0; ++k) {
+      r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), k, sd.stream_id), key);
+      const double tau = -log(u23d(r.x));
+      double Sn = S, vn = vcur;
+      int what;
+      if (fabs(uz) < 1e-9) {
+        what = 3;
+        const int j = search_mass_d(sd.Sd, sd.n_v, S);
+        const double dvds = sd.dv / (sd.Sd[j + 1] - sd.Sd[j]);
+        Xx += ux * tau * sd.inv_tau * dvds;
+        Xy += uy * tau * sd.inv_tau * dvds;
+      } else {
+        Sn = S + tau * uz * sd.inv_tau;
+        what = Sn >= 1.0 ? 1 : (Sn <= 0.0 ? 2 : 0);
+      }
+      if (what == 1) {
+        Xx += ux / uz * (sd.v_top - vcur);
+        Xy += uy / uz * (sd.v_top - vcur);
+        if (sd.cone_all || uz >= sd.cos_alpha) {
+          const double ax = x0 + ux / uz * sd.z_probe, ay = y0 + uy / uz * sd.z_probe;
+          const double bx = Xx - ux / uz * sd.v_top, by = Xy - uy / uz * sd.v_top;
+          const double fb = floor((vapp - sd.v_lo) * sd.inv_dbin);
+          const int idx = fb < 0.0 ? 0 : (fb >= (double)n_bins ? n_bins + 1 : (int)fb + 1);
+          for (int s = 0; s < sd.n_snap; ++s) {
+            const double t = sd.t_snap[s];
+            const double dx = ax + t * bx, dy = ay + t * by;
+            if (sd.ap_all || dx * dx + dy * dy <= sd.r_ap2) {
+              atomicAdd(&sd.hist[(size_t)s * row + idx], W);
+              atomicAdd(&sd.hist[(size_t)s * row + n_bins + 2], 1ull);
+              if (s < 64) dmask |= 1ull << s;
+            }
+          }
+        }
+        atomicAdd(&s_cnt[C_ESCAPES], 1ull);
+        atomicAdd(&s_cnt[C_W_ESCAPED], W);
+        fate = 1;
+      } else if (what == 2) {
+        Xx += ux / uz * (sd.v_fs - vcur);
+        Xy += uy / uz * (sd.v_fs - vcur);
+        S = 0.0;
+        vcur = sd.v_fs;
+        ++nev; ++nsurf; ++st_events; ++st_surf;
+        const unsigned long long Wn =
+            sd.R_q >= (1ull << 32) ? W : ((W * sd.R_q + (1ull << 31)) >> 32);
+        if (Wn != W) atomicAdd(&s_cnt[C_W_ABS_SURFACE], W - Wn);
+        W = Wn;
+        const double uz_old = uz;
+        if (sd.surface_mode == PDV_SURFACE_SPECULAR) {
+          uz = -uz;
+        } else {
+          double ct, st;
+          if (sd.surface_mode == PDV_SURFACE_LAMBERT) {
+            const double a = u23d(r.y);
+            ct = sqrt(a);
+            st = sqrt(1.0 - a);
+          } else {
+            const double th = 0.5 * pi * u23d(r.y);
+            ct = cos(th);
+            st = sin(th);
+          }
+          const double ph = 2.0 * pi * u23d(r.z);
+          ux = st * cos(ph);
+          uy = st * sin(ph);
+          uz = ct;
+        }
+        vapp += 0.5 * (uz - uz_old) * sd.v_fs;
+        if (W == 0) fate = 3;
+      } else {
+        if (what == 0) {
+          const int j = search_mass_d(sd.Sd, sd.n_v, Sn);
+          vn = sd.v_bot + j * sd.dv + (Sn - sd.Sd[j]) / (sd.Sd[j + 1] - sd.Sd[j]) * sd.dv;
+          Xx += ux / uz * (vn - vcur);
+          Xy += uy / uz * (vn - vcur);
+        }
+        S = Sn;
+        vcur = vn;
+        ++nev; ++st_events;
+        if ((r.y >> 8) < sd.omega_q) {
+          const unsigned m2 = r.z >> 8;
+          int lo = 0, hi = sd.n_p - 2;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sd.Cq[mid] <= m2) lo = mid; else hi = mid - 1;
+          }
+          const double th = sd.th_d[lo] + ((double)(m2 - sd.Cq[lo]) + 0.5) /
+                                              (double)(sd.Cq[lo + 1] - sd.Cq[lo]) *
+                                              (sd.th_d[lo + 1] - sd.th_d[lo]);
+          const double ph = 2.0 * pi * u23d(r.w);
+          const double ct = cos(th), st = sin(th), cp = cos(ph), sp = sin(ph);
+          double nx, ny, nz;
+          if (fabs(uz) > 1.0 - 1e-6) {
+            nx = st * cp; ny = st * sp; nz = uz >= 0.0 ? ct : -ct;
+          } else {
+            const double s = sqrt(1.0 - uz * uz);
+            nx = st * (ux * uz * cp - uy * sp) / s + ux * ct;
+            ny = st * (uy * uz * cp + ux * sp) / s + uy * ct;
+            nz = -st * cp * s + uz * ct;
+          }
+          const double nn = sqrt(nx * nx + ny * ny + nz * nz);
+          nx /= nn; ny /= nn; nz /= nn;
+          vapp += 0.5 * (nz - uz) * vn;
+          ux = nx; uy = ny; uz = nz;
+          ++nsca; ++st_scat;
+        } else {
+          atomicAdd(&s_cnt[C_W_ABS_PARTICLE], W);
+          fate = 2;
+        }
+      }
+      if (fate == 0 && nev >= sd.max_events) {
+        atomicAdd(&s_cnt[C_W_TRUNCATED], W);
+        atomicAdd(&s_cnt[C_TRUNCATED], 1ull);
+        fate = 4;
+      }
+    }
+    if (sd.packets) {
+      pdv_packet_record rec;
+      rec.n_events = nev;
+      rec.n_scatters = nsca;
+      rec.n_surface = nsurf;
+      rec.fate = fate;
+      rec.weight = W;
+      rec.v_app = vapp;
+      rec.detect_mask = dmask;
+      sd.packets[ip] = rec;
+    }
+  }
+  atomicAdd(&s_cnt[C_LAUNCHED], st_launch);
+  atomicAdd(&s_cnt[C_EVENTS], st_events);
+  atomicAdd(&s_cnt[C_SCATTERS], st_scat);
+  atomicAdd(&s_cnt[C_SURFACE_HITS], st_surf);
+  __syncthreads();
+  if (threadIdx.x < C_NCOUNT && s_cnt[threadIdx.x]) atomicAdd(&sd.cnt[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+void launch_transport_f64(const SetDesc* d_set, int grid, int block, cudaStream_t st) {
+  k_transport_f64<<<grid, block, 0, st>>>(d_set);
+}
+
+// ------------------------------------------------------------------ Eq. 19
+// One block per (snapshot, set): spectrum = weight / (2^32 N) (optionally per
+// m/s), raw tallies and the per-snapshot counters.
+__global__ void k_normalise(const SetDesc* __restrict__ sets, double* const* spec,
+                            pdv_counters* const* cnt_out, unsigned long long* const* raw,
+                            const unsigned* flags) {
+  const SetDesc& sd = sets[blockIdx.y];
+  const int s = blockIdx.x;
+  if (s >= sd.n_snap) return;
+  const int n_bins = sd.n_bins, row = hist_row(n_bins);
+  const unsigned long long* h = sd.hist + (size_t)s * row;
+  double scale = 1.0 / (kTwo32 * (double)sd.norm_packets);
+  if (flags[blockIdx.y] & PDV_PER_DV) scale *= sd.inv_dbin;
+  double* out = spec[blockIdx.y] + (size_t)s * n_bins;
+  unsigned long long* rw = raw[blockIdx.y];
+  unsigned long long part = 0;
+  for (int b = threadIdx.x; b < n_bins; b += blockDim.x) {
+    const unsigned long long v = h[b + 1];
+    out[b] = (double)v * scale;
+    part += v;
+  }
+  if (rw) {
+    for (int b = threadIdx.x; b < n_bins + 2; b += blockDim.x) rw[(size_t)s * (n_bins + 2) + b] = h[b];
+  }
+  __shared__ unsigned long long red[32];
+  for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long wdet = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) wdet += red[i];
+    pdv_counters* co = cnt_out[blockIdx.y];
+    if (co) {
+      pdv_counters c;
+      c.launched = sd.cnt[C_LAUNCHED];
+      c.events = sd.cnt[C_EVENTS];
+      c.scatters = sd.cnt[C_SCATTERS];
+      c.surface_hits = sd.cnt[C_SURFACE_HITS];
+      c.escapes = sd.cnt[C_ESCAPES];
+      c.detected = h[n_bins + 2];
+      c.w_detected = wdet;
+      c.w_under = h[0];
+      c.w_over = h[n_bins + 1];
+      c.w_escaped_undetected = sd.cnt[C_W_ESCAPED] - wdet - h[0] - h[n_bins + 1];
+      c.w_absorbed_particle = sd.cnt[C_W_ABS_PARTICLE];
+      c.w_absorbed_surface = sd.cnt[C_W_ABS_SURFACE];
+      c.w_truncated = sd.cnt[C_W_TRUNCATED];
+      c.truncated = sd.cnt[C_TRUNCATED];
+      co[s] = c;
+    }
+  }
+}
+
+void launch_normalise(const SetDesc* d_sets, int n_sets, double* const* d_spec,
+                      pdv_counters* const* d_cnt_out, unsigned long long* const* d_raw,
+                      const unsigned* flags, int max_snap, cudaStream_t st) {
+  k_normalise<<<dim3(max_snap, n_sets), 256, 0, st>>>(d_sets, d_spec, d_cnt_out, d_raw, flags);
+}
+
+}  // namespace pdv

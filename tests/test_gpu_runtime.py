@@ -1,0 +1,120 @@
+"""Batched launches (captured-graph persistent kernel over many parameter sets),
+the autotuner, and the continuous-batching serving loop: every result equals
+the same request run alone, bit for bit (counter-based RNG keyed by the
+request's own seed and packet index, integer tallies)."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2012_00963_gb300 import pdv
+from paper_2012_00963_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = pdv.Context(0)
+    yield c
+    c.close()
+
+
+def small_sets(n, n_max=3e5):
+    sets = W.cfg4_sets(n_sets=n, seed=44, n_min=2e4, n_max=n_max)
+    # HG phase keeps the set-up cheap; the sets still differ in every cloud parameter
+    return [s.replace(phase=W.Phase(kind="hg", g=0.6 + 0.01 * i, albedo=0.5 + 0.02 * i),
+                      r_ap=2e-3, cone_alpha=0.4) for i, s in enumerate(sets)]
+
+
+def test_batch_equals_individual_requests(ctx):
+    wls = small_sets(12)
+    clouds = [pdv.Cloud(ctx, w) for w in wls]
+    alone = [pdv.simulate_spectrum(ctx, c, w) for c, w in zip(clouds, wls)]
+    for rep in range(2):   # second call replays the cached graph
+        batch = pdv.simulate_batch(ctx, clouds, wls)
+        for a, b in zip(alone, batch):
+            assert np.array_equal(a["raw"], b["raw"])
+            assert np.array_equal(a["counters"], b["counters"])
+    for c in clouds:
+        c.close()
+
+
+def test_batch_with_mixed_precision_and_multi_snapshot(ctx):
+    wls = small_sets(4)
+    wls[1] = wls[1].replace(precision="fp64")
+    wls[2] = wls[2].replace(t_snap=(1e-6, 2e-6, 3e-6))
+    clouds = [pdv.Cloud(ctx, w) for w in wls]
+    alone = [pdv.simulate_spectrum(ctx, c, w) for c, w in zip(clouds, wls)]
+    batch = pdv.simulate_batch(ctx, clouds, wls)
+    for a, b in zip(alone, batch):
+        assert np.array_equal(a["raw"], b["raw"])
+    for c in clouds:
+        c.close()
+
+
+def test_autotune_keeps_results(ctx):
+    wls = small_sets(6)
+    clouds = [pdv.Cloud(ctx, w) for w in wls]
+    before = pdv.simulate_batch(ctx, clouds, wls)
+    reqs = [pdv.Request(c, w) for c, w in zip(clouds, wls)]
+    t = pdv.pdv_autotune(ctx.handle, [r.c for r in reqs])
+    assert t["block_threads"] in (128, 256) and t["hist_mode"] in (1, 2)
+    after = pdv.simulate_batch(ctx, clouds, wls)
+    for a, b in zip(before, after):
+        assert np.array_equal(a["raw"], b["raw"])
+    ctx.set_tuning()   # back to defaults
+    for c in clouds:
+        c.close()
+
+
+def test_serving_results_equal_standalone(ctx):
+    """Requests submitted while others run are admitted into the running batch
+    loop; each one's tallies equal the same request run alone."""
+    arrivals = W.cfg5_arrivals(rate=2000.0, duration=0.01, seed=9, n_min=1e4, n_max=2e6)[:16]
+    wls = [W.cfg5_request(a, r_ap=2e-3, cone_alpha=0.4) for a in arrivals]
+    clouds = [pdv.Cloud(ctx, w) for w in wls]
+    alone = [pdv.simulate_spectrum(ctx, c, w) for c, w in zip(clouds, wls)]
+    reqs, tickets = [], []
+    for c, w in zip(clouds, wls):
+        r = pdv.Request(c, w)
+        reqs.append(r)
+        tickets.append(pdv.pdv_submit(ctx.handle, r.c))
+    t0 = time.time()
+    pending = set(range(len(tickets)))
+    while pending and time.time() - t0 < 120:
+        for i in list(pending):
+            if pdv.pdv_poll(ctx.handle, tickets[i], 1000) == pdv.PDV_OK:
+                pending.discard(i)
+    assert not pending
+    for a, r in zip(alone, reqs):
+        b = r.result()
+        assert np.array_equal(a["raw"], b["raw"])
+        assert np.array_equal(a["counters"], b["counters"])
+    for c in clouds:
+        c.close()
+
+
+def test_serving_cancel_and_unknown_ticket(ctx):
+    wl = W.cfg1(n_packets=50_000_000)
+    cloud = pdv.Cloud(ctx, wl)
+    r = pdv.Request(cloud, wl)
+    t = pdv.pdv_submit(ctx.handle, r.c)
+    pdv.pdv_cancel(ctx.handle, t)
+    with pytest.raises(pdv.PdvError) as e:
+        while pdv.pdv_poll(ctx.handle, t, 100000) == pdv.PDV_ENOTREADY:
+            pass
+    assert e.value.status == pdv.PDV_ECANCELLED
+    with pytest.raises(pdv.PdvError) as e:
+        pdv.pdv_poll(ctx.handle, 987654321, 0)
+    assert e.value.status == pdv.PDV_EINVAL
+    # the context still serves new work afterwards
+    small = wl.replace(n_packets=10000)
+    r2 = pdv.Request(cloud, small)
+    t2 = pdv.pdv_submit(ctx.handle, r2.c)
+    while pdv.pdv_poll(ctx.handle, t2, 100000) == pdv.PDV_ENOTREADY:
+        pass
+    ref = pdv.simulate_spectrum(ctx, cloud, small)
+    assert np.array_equal(ref["raw"], r2.result()["raw"])
+    time.sleep(0.5)
+    cloud.close()
