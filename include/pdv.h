@@ -81,7 +81,7 @@ typedef struct {
   double d_median_um;          /* Eq. 21 median diameter                 */
   double sigma_ln;             /* Eq. 21 width                           */
   double wavelength_nm;        /* probe laser wavelength                 */
-  int table_nodes;             /* velocity nodes of the mass table (0 = 4096, max 16384) */
+  int table_nodes;             /* velocity nodes of the mass table (0 = 2048, max 16384) */
 } pdv_cloud_desc;
 
 /* Probe geometry: a collimated beam of radius beam_radius_mm launched along

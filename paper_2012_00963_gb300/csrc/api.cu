@@ -275,7 +275,7 @@ extern "C" pdv_status pdv_create_cloud(pdv_ctx* c, const pdv_cloud_desc* d, pdv_
   cl->v_top = v_top;
   cl->d_s = d->d_median_um * 1e-6 * std::exp(2.5 * d->sigma_ln * d->sigma_ln);
   cl->m0 = d->area_mass_mg_cm2 * 1e-2;
-  const int n_v = d->table_nodes ? d->table_nodes : 4096;
+  const int n_v = d->table_nodes ? d->table_nodes : 2048;
   const int n_g = std::min(next_pow2(n_v), kMaxTableNodes);
   int lg = 0;
   while ((1 << lg) < n_g) ++lg;
@@ -362,8 +362,8 @@ extern "C" pdv_status pdv_set_phase_table(pdv_cloud* cl, int n, const double* th
   if (!base) return fail(PDV_ENOMEM, "phase table allocation failed");
   cl->phase_arena = base;
   cl->t.Cq = (unsigned*)(base + oCq);
-  cl->t.th = (float*)(base + oth);
-  cl->t.dthq = (float*)(base + odt);
+  cl->t.thpi = (float*)(base + oth);
+  cl->t.dthpi = (float*)(base + odt);
   cl->t.th_d = (double*)(base + othd);
   cl->t.Gp = (unsigned short*)(base + oGp);
   cl->t.n_p = n;
@@ -516,7 +516,7 @@ static SetDesc make_set(const pdv_request* r) {
   SetDesc d;
   memset(&d, 0, sizeof d);
   d.Sq = cl->t.Sq; d.Sd = cl->t.Sd; d.w = cl->t.w; d.G = cl->t.G;
-  d.Cq = cl->t.Cq; d.th = cl->t.th; d.dthq = cl->t.dthq; d.th_d = cl->t.th_d; d.Gp = cl->t.Gp;
+  d.Cq = cl->t.Cq; d.thpi = cl->t.thpi; d.dthpi = cl->t.dthpi; d.th_d = cl->t.th_d; d.Gp = cl->t.Gp;
   d.n_v = cl->t.n_v; d.n_g = cl->t.n_g; d.g_shift = cl->t.g_shift; d.n_p = cl->t.n_p;
   d.n_snap = r->n_snap; d.n_bins = r->n_bins;
   d.surface_mode = cl->desc.surface_mode;

@@ -25,7 +25,7 @@ constexpr int kMaxTableNodes = 16384;
 constexpr int kMaxPhase = 65536;
 constexpr int kMaxSnap = 4096;
 constexpr int kMaxBins = 65536;
-constexpr int kGuidePhaseLog = 12;                   // 4096 guide cells over the 2^24 CDF
+constexpr int kGuidePhaseLog = 11;                   // 2048 guide cells over the 2^24 CDF
 
 // Snapshot-independent counter slots of one request (device array of u64).
 enum Counter {
@@ -55,8 +55,8 @@ struct CloudTables {
   int n_v = 0, n_g = 0, g_shift = 0;
   // phase function
   unsigned* Cq = nullptr;             // [n_p] integer CDF, 2^24 scale
-  float* th = nullptr;                // [n_p] theta (f32)
-  float* dthq = nullptr;              // [n_p] (theta_{i+1} - theta_i) / (Cq_{i+1} - Cq_i)
+  float* thpi = nullptr;              // [n_p] theta / pi (f32)
+  float* dthpi = nullptr;             // [n_p] (theta_{i+1} - theta_i) / pi / (Cq_{i+1} - Cq_i)
   double* th_d = nullptr;             // [n_p] theta (FP64 path)
   unsigned short* Gp = nullptr;       // [n_gp + 1] guide over the 2^24 CDF
   int n_p = 0;
@@ -69,8 +69,8 @@ struct SetDesc {
   const float* w;
   const unsigned short* G;
   const unsigned* Cq;
-  const float* th;
-  const float* dthq;
+  const float* thpi;
+  const float* dthpi;
   const double* th_d;
   const unsigned short* Gp;
   const double* t_snap;               // [n_snap] seconds
@@ -99,9 +99,10 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
       k.x += 0x9E3779B9u;
       k.y += 0xBB67AE85u;
     }
-    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53u;   // one wide multiply
+    const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57u;
+    c = make_uint4((unsigned)(p1 >> 32) ^ c.y ^ k.x, (unsigned)p1,
+                   (unsigned)(p0 >> 32) ^ c.w ^ k.y, (unsigned)p0);
   }
   return c;
 }
@@ -126,6 +127,14 @@ __device__ __forceinline__ long long fix62(float x) {
   else v = (sh > -40) ? (m >> (-sh)) : 0ll;
   if (e == 0) v = 0;
   return (b >> 31) ? -v : v;
+}
+
+// Reciprocal on the special-function unit (about 1 ulp; used for geometry
+// that only feeds the lateral position).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // unsigned 64-bit integer (< 2^63) to binary32.

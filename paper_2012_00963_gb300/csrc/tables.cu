@@ -153,7 +153,7 @@ __global__ void k_phase_prefix(double* work, int n) {
 }
 
 __global__ void k_phase_quant(const double* work, const double* th, int n, unsigned* Cq,
-                              float* thf, double* thd) {
+                              float* thpi, double* thd) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double* cum = work + (n - 1);
@@ -162,16 +162,16 @@ __global__ void k_phase_quant(const double* work, const double* th, int n, unsig
   if (i == 0) q = 0u;
   if (i == n - 1) q = 16777216u;
   Cq[i] = q;
-  thf[i] = (float)th[i];
+  thpi[i] = (float)(th[i] / 3.14159265358979323846);
   thd[i] = th[i];
 }
 
-__global__ void k_phase_slopes(const unsigned* Cq, const double* th, int n, float* dthq) {
+__global__ void k_phase_slopes(const unsigned* Cq, const double* th, int n, float* dthpi) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  if (i == n - 1) { dthq[i] = 0.0f; return; }
+  if (i == n - 1) { dthpi[i] = 0.0f; return; }
   const unsigned dc = Cq[i + 1] - Cq[i];
-  dthq[i] = dc ? (float)((th[i + 1] - th[i]) / (double)dc) : 0.0f;
+  dthpi[i] = dc ? (float)((th[i + 1] - th[i]) / 3.14159265358979323846 / (double)dc) : 0.0f;
 }
 
 // Gp[c] = largest i in [0, n-2] with Cq_i <= c 2^(24 - kGuidePhaseLog).
@@ -204,8 +204,8 @@ cudaError_t build_phase_cdf(const double* d_theta, const double* d_p, int n, dou
   const int nb = (n + 255) / 256;
   k_phase_trap<<<nb, 256, 0, st>>>(d_theta, d_p, n, d_work);
   k_phase_prefix<<<1, 1, 0, st>>>(d_work, n);
-  k_phase_quant<<<nb, 256, 0, st>>>(d_work, d_theta, n, t->Cq, t->th, t->th_d);
-  k_phase_slopes<<<nb, 256, 0, st>>>(t->Cq, d_theta, n, t->dthq);
+  k_phase_quant<<<nb, 256, 0, st>>>(d_work, d_theta, n, t->Cq, t->thpi, t->th_d);
+  k_phase_slopes<<<nb, 256, 0, st>>>(t->Cq, d_theta, n, t->dthpi);
   k_phase_guide<<<((1 << kGuidePhaseLog) + 1 + 255) / 256, 256, 0, st>>>(t->Cq, n, t->Gp);
   k_phase_gtab<<<1, 1, 0, st>>>(t->Cq, d_theta, n, d_gtab);
   return cudaGetLastError();

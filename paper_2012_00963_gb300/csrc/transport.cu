@@ -32,8 +32,8 @@ struct SmemTables {
   const float* w;
   const unsigned short* G;
   const unsigned* Cq;
-  const float* th;
-  const float* dthq;
+  const float* thpi;
+  const float* dthpi;
   const unsigned short* Gp;
   const float* ts;
   unsigned long long* hist;
@@ -49,8 +49,8 @@ __host__ __device__ inline size_t smem_layout(int n_v, int n_g, int n_p, int n_s
   off[1] = o; o = align16(o + sizeof(float) * (size_t)n_v);                       // w
   off[2] = o; o = align16(o + sizeof(unsigned short) * (size_t)(n_g + 1));        // G
   off[3] = o; o = align16(o + sizeof(unsigned) * (size_t)n_p);                    // Cq
-  off[4] = o; o = align16(o + sizeof(float) * (size_t)n_p);                       // th
-  off[5] = o; o = align16(o + sizeof(float) * (size_t)n_p);                       // dthq
+  off[4] = o; o = align16(o + sizeof(float) * (size_t)n_p);                       // thpi
+  off[5] = o; o = align16(o + sizeof(float) * (size_t)n_p);                       // dthpi
   off[6] = o; o = align16(o + sizeof(unsigned short) * ((1 << kGuidePhaseLog) + 1));  // Gp
   off[7] = o; o = align16(o + sizeof(float) * (size_t)n_snap);                    // ts
   off[8] = o;
@@ -99,10 +99,22 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
+// Launch position on the beam disk (event 0 of the packet's stream). Only the
+// detection test needs it, so it is drawn when a packet reaches the probe.
+__device__ __forceinline__ void launch_position(unsigned long long pk, unsigned sid, uint2 key,
+                                                float r_beam, float& x0, float& y0) {
+  const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), 0u, sid), key);
+  const float rad = r_beam * sqrtf(u23f(r.x));
+  float sp, cp;
+  sincospif(2.0f * u23f(r.y), &sp, &cp);
+  x0 = rad * cp;
+  y0 = rad * sp;
+}
+
 template <bool DUMP, int HMODE>
-__global__ void __launch_bounds__(256) k_transport_f32(const SetDesc* __restrict__ sets,
-                                                       int n_sets,
-                                                       unsigned long long* __restrict__ set_ctr) {
+__global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restrict__ sets,
+                                                          int n_sets,
+                                                          unsigned long long* __restrict__ set_ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SetDesc sd;
   __shared__ unsigned long long s_cnt[C_NCOUNT];
@@ -138,8 +150,8 @@ __global__ void __launch_bounds__(256) k_transport_f32(const SetDesc* __restrict
     tb.w = reinterpret_cast<const float*>(smem + off[1]);
     tb.G = reinterpret_cast<const unsigned short*>(smem + off[2]);
     tb.Cq = reinterpret_cast<const unsigned*>(smem + off[3]);
-    tb.th = reinterpret_cast<const float*>(smem + off[4]);
-    tb.dthq = reinterpret_cast<const float*>(smem + off[5]);
+    tb.thpi = reinterpret_cast<const float*>(smem + off[4]);
+    tb.dthpi = reinterpret_cast<const float*>(smem + off[5]);
     tb.Gp = reinterpret_cast<const unsigned short*>(smem + off[6]);
     tb.ts = reinterpret_cast<const float*>(smem + off[7]);
     tb.hist = HMODE == 2 ? reinterpret_cast<unsigned long long*>(smem + off[8]) : sd.hist;
@@ -151,12 +163,12 @@ __global__ void __launch_bounds__(256) k_transport_f32(const SetDesc* __restrict
       unsigned short* G = reinterpret_cast<unsigned short*>(smem + off[2]);
       for (int i = threadIdx.x; i <= sd.n_g; i += blockDim.x) G[i] = sd.G[i];
       unsigned* Cq = reinterpret_cast<unsigned*>(smem + off[3]);
-      float* th = reinterpret_cast<float*>(smem + off[4]);
-      float* dthq = reinterpret_cast<float*>(smem + off[5]);
+      float* thpi = reinterpret_cast<float*>(smem + off[4]);
+      float* dthpi = reinterpret_cast<float*>(smem + off[5]);
       for (int i = threadIdx.x; i < sd.n_p; i += blockDim.x) {
         Cq[i] = sd.Cq[i];
-        th[i] = sd.th[i];
-        dthq[i] = sd.dthq[i];
+        thpi[i] = sd.thpi[i];
+        dthpi[i] = sd.dthpi[i];
       }
       unsigned short* Gp = reinterpret_cast<unsigned short*>(smem + off[6]);
       for (int i = threadIdx.x; i <= (1 << kGuidePhaseLog); i += blockDim.x) Gp[i] = sd.Gp[i];
@@ -178,14 +190,18 @@ __global__ void __launch_bounds__(256) k_transport_f32(const SetDesc* __restrict
     const int n_bins = sd.n_bins, row = hist_row(sd.n_bins), n_snap = sd.n_snap;
 
     // ---- warp loop
-    unsigned long long pool_next = 0, pool_end = 0;
+    // The warp owns a chunk [pool_next, pool_end) of packet offsets and has the
+    // next chunk's claim already in flight (lane 0's `pre`), so the global
+    // atomic's latency is hidden behind a chunk's worth of events.
+    unsigned long long pool_next = 0, pool_end = 0, pre = 0;
+    if (lane == 0) pre = atomicAdd(&set_ctr[si], (unsigned long long)kChunk);
     bool exhausted = false, alive = false;
     unsigned long long pk = 0, W = 0;
     long long Sq = 0;
     unsigned kev = 0, nev = 0, nsca = 0, nsurf = 0;
     unsigned long long dmask = 0;
     float vcur = 0.f, ux = 0.f, uy = 0.f, uz = -1.f, iuz = -1.f;
-    float Xx = 0.f, Xy = 0.f, x0 = 0.f, y0 = 0.f, vapp = 0.f, vcomp = 0.f;
+    float Xx = 0.f, Xy = 0.f, vapp = 0.f, vcomp = 0.f;
     unsigned st_launch = 0, st_events = 0, st_scat = 0, st_surf = 0;
 
     for (;;) {
@@ -195,13 +211,12 @@ __global__ void __launch_bounds__(256) k_transport_f32(const SetDesc* __restrict
         const unsigned long long avail = pool_end - pool_next;
         if (avail == 0) {
           if (exhausted) break;
-          unsigned long long b = 0;
-          if (lane == 0) b = atomicAdd(&set_ctr[si], (unsigned long long)kChunk);
-          b = __shfl_sync(kFull, b, 0);
+          const unsigned long long b = __shfl_sync(kFull, pre, 0);
           if (b >= n_pk) {
             exhausted = true;
             break;
           }
+          if (lane == 0) pre = atomicAdd(&set_ctr[si], (unsigned long long)kChunk);
           pool_next = b;
           pool_end = b + kChunk < n_pk ? b + kChunk : n_pk;
           continue;
@@ -210,14 +225,8 @@ __global__ void __launch_bounds__(256) k_transport_f32(const SetDesc* __restrict
         const unsigned take = (unsigned)(avail < cnt ? avail : cnt);
         const unsigned rank = __popc(need & lanemask_lt());
         if (!alive && rank < take) {
-          // Step (1): launch on the beam disk (event 0), moving along -z
+          // Step (1): a new packet at the top of the cloud moving along -z
           pk = base_pk + pool_next + rank;
-          const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), 0u, sid), key);
-          const float rad = sd.r_beam_f * sqrtf(u23f(r.x));
-          float sp, cp;
-          sincospif(2.0f * u23f(r.y), &sp, &cp);
-          x0 = rad * cp;
-          y0 = rad * sp;
           ux = 0.f; uy = 0.f; uz = -1.f; iuz = -1.f;
           Sq = (long long)kOneQ;
           vcur = sd.v_top_f;
@@ -238,7 +247,8 @@ __global__ void __launch_bounds__(256) k_transport_f32(const SetDesc* __restrict
       const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), kev, sid), key);
       ++kev;
       const float tau = -logf(u23f(r.x));                // Step (3): Beer–Lambert
-      int what;                                          // 0 interact, 1 escape, 2 surface, 3 horizontal
+      // 0 interaction, 1 escape through the top, 2 free surface, 3 horizontal
+      int what;
       long long Sn = Sq;
       if (fabsf(uz) < 1e-9f) {
         what = 3;
@@ -251,13 +261,37 @@ __global__ void __launch_bounds__(256) k_transport_f32(const SetDesc* __restrict
           what = (Sn >= (long long)kOneQ) ? 1 : (Sn <= 0 ? 2 : 0);
         }
       }
+      // velocity coordinate z/t where the flight ends
+      float vn = vcur;
+      if (what == 0) {
+        const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sn);
+        const float fd = u64_to_f((unsigned long long)Sn - tb.Sq[j]);
+        vn = fmaf(fd, tb.w[j], fmaf((float)j, sd.dv_f, sd.v_bot_f));
+      } else if (what == 1) {
+        vn = sd.v_top_f;
+      } else if (what == 2) {
+        vn = sd.v_fs_f;
+        Sn = 0;
+      }
+      // lateral displacement in velocity units (x = x0 + t X)
+      if (what != 3) {
+        const float d = vn - vcur;
+        Xx = fmaf(ux * iuz, d, Xx);
+        Xy = fmaf(uy * iuz, d, Xy);
+      } else {
+        // horizontal packet: lateral path tau / mu(z)
+        const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sq);
+        const float len = tau * inv_tau * tb.w[j] * 4.611686018427388e18f;
+        Xx = fmaf(ux, len, Xx);
+        Xy = fmaf(uy, len, Xy);
+      }
       unsigned fate = 0;
       if (what == 1) {
         // Step (6): out through the top, vacuum flight to the probe plane
-        const float tx = ux * iuz, ty = uy * iuz;
-        Xx = fmaf(tx, sd.v_top_f - vcur, Xx);
-        Xy = fmaf(ty, sd.v_top_f - vcur, Xy);
         if (sd.cone_all || uz >= sd.cos_alpha_f) {
+          float x0, y0;
+          launch_position(pk, sid, key, sd.r_beam_f, x0, y0);
+          const float tx = ux * iuz, ty = uy * iuz;
           const float ax = fmaf(tx, sd.z_probe_f, x0), ay = fmaf(ty, sd.z_probe_f, y0);
           const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
           const float fb = floorf((vapp - vcomp - sd.v_lo_f) * sd.inv_dbin_f);
@@ -276,82 +310,77 @@ __global__ void __launch_bounds__(256) k_transport_f32(const SetDesc* __restrict
         atomicAdd(&s_cnt[C_ESCAPES], 1ull);
         atomicAdd(&s_cnt[C_W_ESCAPED], W);
         fate = 1;
-      } else if (what == 2) {
-        // Step (6): reaches the free surface z = v_fs t
-        Xx = fmaf(ux * iuz, sd.v_fs_f - vcur, Xx);
-        Xy = fmaf(uy * iuz, sd.v_fs_f - vcur, Xy);
-        Sq = 0;
-        vcur = sd.v_fs_f;
-        ++nev; ++st_events; ++st_surf;
-        if (DUMP) ++nsurf;
-        const unsigned long long Wn =
-            sd.R_q >= (1ull << 32) ? W : ((W * sd.R_q + (1ull << 31)) >> 32);
-        if (Wn != W) atomicAdd(&s_cnt[C_W_ABS_SURFACE], W - Wn);
-        W = Wn;
-        float nx, ny, nz;
-        if (sd.surface_mode == PDV_SURFACE_SPECULAR) {
-          nx = ux; ny = uy; nz = -uz;
-        } else {
-          float ct, st;
-          if (sd.surface_mode == PDV_SURFACE_LAMBERT) {
+      } else {
+        Sq = Sn;
+        vcur = vn;
+        ++nev;
+        ++st_events;
+        const bool surf = what == 2;
+        if (surf) {
+          // Step (6): free surface z = v_fs t, reflectivity in 2^32 fixed point
+          ++st_surf;
+          if (DUMP) ++nsurf;
+          const unsigned long long Wn =
+              sd.R_q >= (1ull << 32) ? W : ((W * sd.R_q + (1ull << 31)) >> 32);
+          if (Wn != W) atomicAdd(&s_cnt[C_W_ABS_SURFACE], W - Wn);
+          W = Wn;
+        } else if ((r.y >> 8) >= sd.omega_q) {
+          atomicAdd(&s_cnt[C_W_ABS_PARTICLE], W);             // Eq. 11: absorbed
+          fate = 2;
+        }
+        if (fate == 0) {
+          // New direction. Particle scattering (Eq. 13-17): polar angle from the
+          // phase CDF, azimuth uniform (Eq. 15). Free surface (diffuse): polar
+          // angle uniform in [0, pi/2) from +z, azimuth uniform. Both are a
+          // (polar, azimuth) pair in units of pi followed by the same rotation.
+          float tpi;
+          unsigned rphi;
+          if (surf) {
+            tpi = 0.5f * u23f(r.y);
+            rphi = r.z;
+          } else {
+            const unsigned m2 = r.z >> 8;
+            const int i = search_phase(tb.Cq, tb.Gp, m2);
+            tpi = fmaf((float)(m2 - tb.Cq[i]) + 0.5f, tb.dthpi[i], tb.thpi[i]);
+            rphi = r.w;
+            ++st_scat;
+            if (DUMP) ++nsca;
+          }
+          float st, ct, sp, cp;
+          sincospif(tpi, &st, &ct);
+          sincospif(2.0f * u23f(rphi), &sp, &cp);                        // azimuth, Eq. 15
+          if (surf && sd.surface_mode == PDV_SURFACE_LAMBERT) {
             const float a = u23f(r.y);
             ct = sqrtf(a);
             st = sqrtf(1.0f - a);
-          } else {
-            sincospif(0.5f * u23f(r.y), &st, &ct);     // polar angle uniform in [0, pi/2)
           }
-          float sp, cp;
-          sincospif(2.0f * u23f(r.z), &sp, &cp);
-          nx = st * cp; ny = st * sp; nz = ct;
-        }
-        kahan_add(vapp, vcomp, 0.5f * (nz - uz) * sd.v_fs_f);   // moving wall
-        ux = nx; uy = ny; uz = nz; iuz = __frcp_rn(nz);
-        if (W == 0) fate = 3;
-      } else {
-        float vn = vcur;
-        if (what == 0) {
-          const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sn);
-          const float fd = u64_to_f((unsigned long long)Sn - tb.Sq[j]);
-          vn = fmaf(fd, tb.w[j], fmaf((float)j, sd.dv_f, sd.v_bot_f));
-          Xx = fmaf(ux * iuz, vn - vcur, Xx);
-          Xy = fmaf(uy * iuz, vn - vcur, Xy);
-        } else {
-          // horizontal packet: lateral path tau / mu(z) in velocity units
-          const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sq);
-          const float len = tau * inv_tau * tb.w[j] * 4.611686018427388e18f;
-          Xx = fmaf(ux, len, Xx);
-          Xy = fmaf(uy, len, Xy);
-        }
-        Sq = Sn;
-        vcur = vn;
-        ++nev; ++st_events;
-        if ((r.y >> 8) < sd.omega_q) {
-          // Step (4): scattering, Eq. 13-17
-          const unsigned m2 = r.z >> 8;
-          const int i = search_phase(tb.Cq, tb.Gp, m2);
-          const float th = fmaf((float)(m2 - tb.Cq[i]) + 0.5f, tb.dthq[i], tb.th[i]);
-          float st, ct, sp, cp;
-          sincosf(th, &st, &ct);
-          sincospif(2.0f * u23f(r.w), &sp, &cp);
           float nx, ny, nz;
-          if (fabsf(uz) > 1.0f - 1e-6f) {
-            nx = st * cp; ny = st * sp; nz = uz >= 0.0f ? ct : -ct;   // Eq. 17: cos(theta) sign(u_z)
+          if (surf || fabsf(uz) > 1.0f - 1e-6f) {
+            // Eq. 17 (and the wall's frame): cos(theta) along the sign of u_z
+            nx = st * cp;
+            ny = st * sp;
+            nz = (surf || uz >= 0.0f) ? ct : -ct;
           } else {
-            const float s = sqrtf(fmaf(ux, ux, uy * uy));
-            const float a = st / s;
+            // Eq. 16 in its standard form
+            const float h2 = fmaf(ux, ux, uy * uy);
+            const float rs = rsqrtf(h2);
+            const float s = h2 * rs;
+            const float a = st * rs;
             nx = fmaf(a, fmaf(ux * uz, cp, -uy * sp), ux * ct);
             ny = fmaf(a, fmaf(uy * uz, cp, ux * sp), uy * ct);
             nz = fmaf(-st * cp, s, uz * ct);
           }
-          const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
-          nx *= inv_n; ny *= inv_n; nz *= inv_n;
-          kahan_add(vapp, vcomp, 0.5f * (nz - uz) * vn);      // Eq. 4 / Eq. 18
-          ux = nx; uy = ny; uz = nz; iuz = __frcp_rn(nz);
-          ++st_scat;
-          if (DUMP) ++nsca;
-        } else {
-          atomicAdd(&s_cnt[C_W_ABS_PARTICLE], W);             // Eq. 11: absorbed
-          fate = 2;
+          if (surf && sd.surface_mode == PDV_SURFACE_SPECULAR) {
+            nx = ux; ny = uy; nz = -uz;
+          } else {
+            const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+            nx *= inv_n; ny *= inv_n; nz *= inv_n;
+          }
+          // Eq. 4 / Eq. 18: the moving scatterer (or wall) shifts the frequency
+          kahan_add(vapp, vcomp, 0.5f * (nz - uz) * vn);
+          ux = nx; uy = ny; uz = nz;
+          iuz = rcp_approx(nz);
+          if (W == 0) fate = 3;      // the surface absorbed all of the weight
         }
       }
       if (fate == 0 && nev >= sd.max_events) {

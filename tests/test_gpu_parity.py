@@ -254,16 +254,22 @@ def test_full_size_cfg2_sampled_packets(ctx):
     torch.cuda.synchronize()
     assert np.array_equal(dev["raw"].cpu().numpy().view(np.uint64).reshape(ns, nb + 2), full["raw"])
     recs = pk.view(-1, pdv.PACKET_DTYPE.itemsize)
-    starts = [0, 31_415_926, n - 1500]
+    starts = [0, 31_415_926, n - 20000]
     table = O.phase_table(wl)
-    for s0 in starts:
-        got = np.frombuffer(recs[s0:s0 + 1500].cpu().numpy().tobytes(), pdv.PACKET_DTYPE)
-        ref = O.simulate(wl, n_packets=1500, packet_begin=s0, packets=True, table=table)
-        same = got["n_events"] == ref["packets"]["n_events"]
-        assert same.mean() >= 0.999
-        err = np.abs(got["v_app"] - ref["packets"]["v_app"]) / np.maximum(
-            np.abs(ref["packets"]["v_app"]), wl.v_fs)
-        assert np.mean(err[same] <= 1e-5) >= 0.999
+    got = np.concatenate([np.frombuffer(recs[s0:s0 + 20000].cpu().numpy().tobytes(),
+                                        pdv.PACKET_DTYPE) for s0 in starts])
+    refs = [O.simulate(wl, n_packets=20000, packet_begin=s0, packets=True, table=table)
+            for s0 in starts]
+    ref = {"packets": np.concatenate([r["packets"] for r in refs]),
+           "hist": sum(r["hist"] for r in refs), "counters": sum(r["counters"] for r in refs)}
+    a, b = got, ref["packets"]
+    same = a["n_events"] == b["n_events"]
+    assert same.mean() >= 0.999
+    err = np.abs(a["v_app"] - b["v_app"]) / np.maximum(np.abs(b["v_app"]), wl.v_fs)
+    det = (a["detect_mask"] != 0) & (b["detect_mask"] != 0)
+    assert np.mean(err[same & det] <= 1e-5) >= 0.999 if (same & det).any() else True
+    assert np.mean(err[same] <= 1e-5) >= 0.998
+    assert np.mean(a["detect_mask"] == b["detect_mask"]) >= 0.999
     cloud.close()
     del pk, dev
     torch.cuda.empty_cache()
