@@ -377,7 +377,9 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
             nx *= inv_n; ny *= inv_n; nz *= inv_n;
           }
           // Eq. 4 / Eq. 18: the moving scatterer (or wall) shifts the frequency
-          kahan_add(vapp, vcomp, 0.5f * (nz - uz) * vn);
+          // (a rounded product: no FMA contraction into the compensated sum,
+          // so every instantiation of this kernel computes the same bits)
+          kahan_add(vapp, vcomp, __fmul_rn(0.5f * (nz - uz), vn));
           ux = nx; uy = ny; uz = nz;
           iuz = rcp_approx(nz);
           if (W == 0) fate = 3;      // the surface absorbed all of the weight
