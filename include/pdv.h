@@ -224,6 +224,21 @@ pdv_status pdv_simulate_batch(pdv_ctx* ctx, const pdv_request* reqs, int n);
  * the fastest in the context (and in *out if not NULL). */
 pdv_status pdv_autotune(pdv_ctx* ctx, const pdv_request* reqs, int n, pdv_tuning* out);
 
+/* The same FP32 spectrum as pdv_simulate_spectrum for callers that cannot
+ * allocate device memory while they run (an allocator or memory plan that
+ * forbids cudaMalloc after start-up). The paper has no counterpart: it is a
+ * deployment variant. Its scratch is a fixed 4 MiB array in device memory that
+ * every GPU loading the library keeps until the process exits; a request must
+ * fit in it (about n_snap * (n_bins + 4) * 8 bytes + 1 KiB), else PDV_EINVAL.
+ * Outputs must be device buffers (PDV_OUT_DEVICE); precision must be FP32.
+ * The cloud's tables are made beforehand by pdv_create_cloud and
+ * pdv_set_phase_table. The first call on a device looks the array's device
+ * address up, so make that first call before any stream capture. All calls
+ * share the array and it keeps the last call's contents (cleared at the start
+ * of each call); calls that overlap on the GPU race. Blocking. Errors:
+ * PDV_EINVAL, PDV_ECUDA. */
+pdv_status pdv_simulate_spectrum_static(pdv_ctx* ctx, const pdv_request* req);
+
 /* ---------------------------------------------------------------- serving */
 
 /* Admit a request into the context's continuous-batching loop. The request's

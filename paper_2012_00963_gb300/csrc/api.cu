@@ -1293,3 +1293,96 @@ extern "C" pdv_status pdv_cancel(pdv_ctx* c, pdv_ticket t) {
   c->done_cv.notify_all();
   return PDV_OK;
 }
+
+// ------------------------------------------------------------------ fixed scratch
+// pdv_simulate_spectrum_static: the FP32 spectrum call for callers that may
+// not allocate device memory at run time (for example code running under an
+// external memory budget or allocator that forbids cudaMalloc after start-up,
+// or a host that pre-plans every byte of device memory). Its scratch lives in
+// this file-scope device array instead: every GPU that loads the library holds
+// these 4 MiB until the process exits. Every call shares the array, so calls
+// that overlap on the GPU (different streams or contexts on one device) race.
+constexpr size_t kStaticScratchBytes = 4u << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// In host code g_static_scratch names a host-side stand-in, not device memory:
+// its device address is looked up once per device, with that device current.
+static std::mutex g_static_mu;
+static void* g_static_addr[128] = {nullptr};
+
+static pdv_status static_scratch_address(int device, char** out) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (device < 0 || device >= 128) return fail(PDV_EINVAL, "device %d out of range", device);
+  if (!g_static_addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(PDV_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
+                  cudaGetErrorString(e));
+    g_static_addr[device] = p;
+  }
+  *out = (char*)g_static_addr[device];
+  return PDV_OK;
+}
+
+extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request* r) {
+  if (!c) return fail(PDV_EINVAL, "ctx is NULL");
+  pdv_status s = validate_request(r);
+  if (s != PDV_OK) return s;
+  if (r->precision != PDV_PREC_FP32) return fail(PDV_EINVAL, "the static-scratch call runs FP32 requests");
+  if (!(r->flags & PDV_OUT_DEVICE)) return fail(PDV_EINVAL, "the static-scratch call needs PDV_OUT_DEVICE outputs");
+  // scratch layout: set descriptor, packet counter, counters, histogram,
+  // snapshot times, normalisation pointers and flags
+  Layout L;
+  const size_t o_set = L.add(sizeof(SetDesc));
+  const size_t o_ctr = L.add(sizeof(unsigned long long));
+  const size_t o_cnt = L.add(sizeof(unsigned long long) * C_NCOUNT);
+  const size_t hist_words = (size_t)hist_row(r->n_bins) * r->n_snap;
+  const size_t o_hist = L.add(sizeof(unsigned long long) * hist_words);
+  const size_t o_t = L.add(sizeof(double) * r->n_snap);
+  const size_t o_ptr = L.add(sizeof(void*) * 3);
+  const size_t o_flags = L.add(sizeof(unsigned));
+  if (L.bytes > kStaticScratchBytes)
+    return fail(PDV_EINVAL, "request needs %zu bytes of scratch; the static scratch holds %zu "
+                "(n_snap * (n_bins + 3) * 8 + n_snap * 8 + about 1 KiB)", L.bytes, kStaticScratchBytes);
+  CK(enter(c->device));
+  char* base = nullptr;
+  s = static_scratch_address(c->device, &base);
+  if (s != PDV_OK) return s;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t st = c->stream;
+  SetDesc d = make_set(r);
+  d.t_snap = (const double*)(base + o_t);
+  d.hist = (unsigned long long*)(base + o_hist);
+  d.cnt = (unsigned long long*)(base + o_cnt);
+  d.packets = r->out_packets;
+  double ts[kMaxSnap];
+  for (int i = 0; i < r->n_snap; ++i) ts[i] = r->t_snap_us[i] * 1e-6;
+  void* ptrs[3] = {(void*)r->out_spectrum, (void*)r->out_counters, (void*)r->out_raw};
+  const unsigned flags = r->flags;
+  CK(cudaMemcpyAsync(base + o_t, ts, sizeof(double) * r->n_snap, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_set, &d, sizeof d, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_ptr, ptrs, sizeof ptrs, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_flags, &flags, sizeof flags, cudaMemcpyHostToDevice, st));
+  // the previous call's counts stay in the array: clear what accumulates
+  CK(cudaMemsetAsync(base + o_ctr, 0, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(base + o_cnt, 0, sizeof(unsigned long long) * C_NCOUNT, st));
+  CK(cudaMemsetAsync(base + o_hist, 0, sizeof(unsigned long long) * hist_words, st));
+  const int hm = pick_hist_mode(c, d);
+  const bool dump = d.packets != nullptr;
+  const size_t smem = transport_f32_smem(d.n_v, d.n_g, d.n_p, d.n_snap, d.n_bins, hm);
+  if (smem > (size_t)c->max_smem) return fail(PDV_EINVAL, "tables need %zu bytes of shared memory", smem);
+  int grid = 0, block = 0;
+  s = f32_geometry(c, smem, hm, dump, &grid, &block);
+  if (s != PDV_OK) return s;
+  launch_transport_f32((const SetDesc*)(base + o_set), 1, (unsigned long long*)(base + o_ctr),
+                       grid, block, smem, hm, dump, st);
+  launch_normalise((const SetDesc*)(base + o_set), 1, (double* const*)(base + o_ptr),
+                   (pdv_counters* const*)(base + o_ptr + sizeof(void*)),
+                   (unsigned long long* const*)(base + o_ptr + 2 * sizeof(void*)),
+                   (const unsigned*)(base + o_flags), r->n_snap, st);
+  c->launches += 2;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return PDV_OK;
+}

@@ -37,7 +37,7 @@ ABI_FUNCTIONS = [
     "pdv_ctx_create", "pdv_ctx_destroy", "pdv_last_error", "pdv_get_stats", "pdv_set_tuning",
     "pdv_create_cloud", "pdv_set_phase_table", "pdv_cloud_get_info", "pdv_destroy_cloud",
     "pdv_phase_hg", "pdv_mie_table", "pdv_simulate_spectrum", "pdv_simulate_batch",
-    "pdv_autotune", "pdv_submit", "pdv_poll", "pdv_cancel",
+    "pdv_autotune", "pdv_submit", "pdv_poll", "pdv_cancel", "pdv_simulate_spectrum_static",
 ]
 
 
@@ -138,6 +138,7 @@ def lib():
                                    ip, ip, dp, dp, dp, dp, dp], ip),
                 "pdv_simulate_spectrum": ([vp, C.POINTER(pdv_request)], ip),
                 "pdv_simulate_batch": ([vp, C.POINTER(pdv_request), ip], ip),
+                "pdv_simulate_spectrum_static": ([vp, C.POINTER(pdv_request)], ip),
                 "pdv_autotune": ([vp, C.POINTER(pdv_request), ip, C.POINTER(pdv_tuning)], ip),
                 "pdv_submit": ([vp, C.POINTER(pdv_request), C.POINTER(C.c_uint64)], ip),
                 "pdv_poll": ([vp, C.c_uint64, C.c_uint32], ip),
@@ -234,6 +235,12 @@ def pdv_mie_table(ctx: int, m: complex, wavelength_nm: float, d_median_um: float
 
 def pdv_simulate_spectrum(ctx: int, req: pdv_request):
     _check(lib().pdv_simulate_spectrum(C.c_void_p(ctx), C.byref(req)))
+
+
+def pdv_simulate_spectrum_static(ctx: int, req: pdv_request):
+    """FP32 spectrum with the library's fixed device scratch (no allocation);
+    outputs must be device buffers (PDV_OUT_DEVICE)."""
+    _check(lib().pdv_simulate_spectrum_static(C.c_void_p(ctx), C.byref(req)))
 
 
 def pdv_simulate_batch(ctx: int, reqs: Sequence[pdv_request]):
