@@ -56,6 +56,11 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--mode", default="default", choices=["default", "serve", "batch", "precision"])
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--sets", type=int, default=256)
+    ap.add_argument("--autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -326,6 +331,8 @@ def our_arm(args):
                      "peak_basis": "152 SM x 4 schedulers x 32 lanes x 2070 MHz (issue rate)"},
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and args.serve_seconds > 0:
+        line["serving"] = serving_run(ctx, args.serve_seconds, args.rate)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample(wl, args.cpu_seconds, os.cpu_count() or 1)
         line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": os.cpu_count() or 1,
@@ -341,10 +348,149 @@ def our_arm(args):
     return 0
 
 
+# ----------------------------------------------------------------------- modes
+def serving_run(ctx, seconds, rate):
+    """Poisson stream of fit candidates through pdv_submit / pdv_poll against the
+    oracle-generated target spectrum stored in tests/golden/serving_target.npz."""
+    import numpy as np
+    from paper_2012_00963_gb300 import serving
+    from paper_2012_00963_gb300 import workloads as W
+    g = np.load(os.path.join(ROOT, "tests", "golden", "serving_target.npz"))
+    target = g["hist"][0].astype(np.float64) / 2.0**32
+    probe = dict(r_ap=3.0 * W.MM, cone_alpha=0.5)
+    res = serving.run_sweep(ctx, target, int(g["n_packets"]), probe, duration=seconds, rate=rate)
+    hidden = {"beta": 6.0, "m0": 3.0 * W.MG_CM2, "d_m": 2.0 * W.UM, "tau0": float(g["tau_tot"])}
+    return serving.summary(res, hidden)
+
+
+def serve_mode(args):
+    import torch
+    from paper_2012_00963_gb300 import pdv
+    torch.cuda.set_device(0)
+    ctx = pdv.Context(0)
+    clocks = Clocks(0)
+    clocks.start()
+    out = serving_run(ctx, args.serve_seconds, args.rate)
+    clk = clocks.stop()
+    ctx.close()
+    line = {"mode": "serve", "metric": "p50/p99 request latency and spectra/s (served)",
+            "unit": "ms", "rate_per_s": args.rate, "seconds": args.serve_seconds,
+            "config": {"workload": "cfg5: Poisson stream of fit candidates (beta, m0, d), HG "
+                                   "g=0.7 albedo 0.6, 400 bins 0-8000 m/s, 1e5-1e7 packets per "
+                                   "request, aperture 3 mm, cone 0.5 rad"},
+            "clocks": clk}
+    line.update(out)
+    print(json.dumps(line))
+    return 0
+
+
+def batch_mode(args):
+    """Batched launch of many parameter sets (cfg4) from one captured graph."""
+    import numpy as np
+    import torch
+    from paper_2012_00963_gb300 import pdv
+    from paper_2012_00963_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = pdv.Context(0, stream=stream.cuda_stream)
+    sets = W.cfg4_sets(n_sets=args.sets, seed=4)
+    clouds = [pdv.Cloud(ctx, w) for w in sets]
+    reqs = [pdv.Request(c, w) for c, w in zip(clouds, sets)]
+    tuning = pdv.pdv_autotune(ctx.handle, [r.c for r in reqs]) if args.autotune else None
+    for _ in range(max(1, args.warmup)):
+        pdv.pdv_simulate_batch(ctx.handle, [r.c for r in reqs])
+    times, kern, scat, ev = [], [], 0, 0
+    clocks = Clocks(0)
+    clocks.start()
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pdv.pdv_simulate_batch(ctx.handle, [r.c for r in reqs])
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+        kern.append(ctx.stats()["last_transport_ms"])
+        cnt = [r.result()["counters"][0] for r in reqs]
+        scat += sum(int(c[2]) for c in cnt)
+        ev += sum(int(c[1]) for c in cnt)
+    clk = clocks.stop()
+    tot = sum(times) / 1e3
+    n_packets = sum(w.n_packets for w in sets)
+    line = {"mode": "batch", "metric": "batched spectra/s", "value": len(sets) * args.steps / tot,
+            "unit": "spectra/s", "scatter_events_per_s": scat / tot, "events_per_s": ev / tot,
+            "ms_per_launch": 1e3 * tot / args.steps, "kernel_ms": statistics.mean(kern),
+            "packets_per_launch": n_packets, "sets": len(sets), "tuning": tuning,
+            "gpu_launches_per_step": 2,
+            "config": {"workload": "cfg4: %d sets, beta U(2,10), m0 logU(0.1,20) mg/cm^2, d "
+                                   "logU(0.5,10) um Mie 3+9i, v_fs U(1.5,3) km/s, t U(1,4) us, "
+                                   "packets logU(1e5,1e8), 400 bins" % len(sets)},
+            "clocks": clk}
+    for c in clouds:
+        c.close()
+    ctx.close()
+    print(json.dumps(line))
+    return 0
+
+
+def precision_mode(args):
+    """FP32 and FP64 GPU spectra of the heavy multiple-scattering cloud against
+    the FP64 oracle's spectrum stored in tests/golden/precision_cfg3.npz."""
+    import numpy as np
+    import torch
+    from paper_2012_00963_gb300 import pdv
+    from paper_2012_00963_gb300 import workloads as W
+    g = np.load(os.path.join(ROOT, "tests", "golden", "precision_cfg3.npz"))
+    n_ref = int(g["n_packets"])
+    h_ref = g["hist"][0].astype(np.float64) / 2.0**32
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = pdv.Context(0, stream=stream.cuda_stream)
+    n = int(args.packets)
+    wl = W.cfg3(n_packets=n, r_ap=3.0 * W.MM, cone_alpha=0.5)
+    cloud = pdv.Cloud(ctx, wl)
+    out = {}
+    for prec in ("fp32", "fp64"):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = pdv.simulate_spectrum(ctx, cloud, wl, precision=prec)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        h = r["raw"][0, 1:-1].astype(np.float64) / 2.0**32
+        s_g, s_o = h / n, h_ref / n_ref
+        pooled = (h + h_ref) / (n + n_ref)        # per-packet rate under the null
+        var = pooled / n + pooled / n_ref
+        sel = var > 0
+        z = (s_g[sel] - s_o[sel]) / np.sqrt(var[sel])
+        rel = np.abs(s_g - s_o)[sel].sum() / s_o[sel].sum()
+        c = pdv.counters_dict(r["counters"][0])
+        out[prec] = {"ms": ms, "packets_per_s": n / (ms / 1e3),
+                     "scatter_events_per_s": c["scatters"] / (ms / 1e3),
+                     "chi2_per_bin": float(np.mean(z * z)), "max_abs_z": float(np.abs(z).max()),
+                     "l1_rel_error_vs_oracle": float(rel), "bins": int(sel.sum())}
+    cloud.close()
+    ctx.close()
+    line = {"mode": "precision", "metric": "per-bin spectrum error vs the FP64 oracle, and "
+            "throughput at equal error", "packets_gpu": n, "packets_oracle": n_ref,
+            "tau_tot": float(g["tau_tot"]), "fp32": out["fp32"], "fp64": out["fp64"],
+            "throughput_ratio_fp32_over_fp64": out["fp32"]["packets_per_s"] /
+            out["fp64"]["packets_per_s"],
+            "note": "both GPU paths draw the same random numbers, so at equal packet counts "
+                    "their spectra (and errors against the oracle) are equal"}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.mode == "serve":
+        return serve_mode(args)
+    if args.mode == "batch":
+        return batch_mode(args)
+    if args.mode == "precision":
+        return precision_mode(args)
     return our_arm(args)
 
 

@@ -13,7 +13,9 @@
  *  - Device objects (contexts, clouds, tables) are library-owned and are
  *    released by the matching destroy function.
  *  - Output buffers are caller-owned: host memory by default, device memory
- *    when the request sets PDV_OUT_DEVICE.
+ *    when the request sets PDV_OUT_DEVICE. Device outputs are written on the
+ *    context's stream; work that prepares them on another stream (for
+ *    example a zero-fill) must be ordered before the call by the caller.
  *  - Units at the ABI follow the paper: area mass mg/cm^2, diameter um,
  *    wavelength nm, probe lengths mm, snapshot times us, velocities m/s.
  *  - Nothing here needs a particular framework: streams are plain

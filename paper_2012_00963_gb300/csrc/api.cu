@@ -95,7 +95,44 @@ struct pdv_ctx {
   cudaStream_t serve_stream = nullptr;
   int max_slots = 1024;
   unsigned long long quantum = 1ull << 21;   // packets per request per serving launch
+  // pinned staging buffers for served outputs, reused by size class (page-
+  // locking memory per request would cost milliseconds of latency)
+  std::mutex pin_mu;
+  std::map<size_t, std::vector<void*>> pinned_free;
+  size_t mem_free = 0;
+  std::chrono::steady_clock::time_point mem_checked{};
 };
+
+static size_t pin_class(size_t bytes) {
+  size_t c = 4096;
+  while (c < bytes) c <<= 1;
+  return c;
+}
+
+static void* pin_acquire(pdv_ctx* c, size_t bytes, size_t* cls) {
+  *cls = pin_class(bytes);
+  {
+    std::lock_guard<std::mutex> lk(c->pin_mu);
+    auto& v = c->pinned_free[*cls];
+    if (!v.empty()) {
+      void* p = v.back();
+      v.pop_back();
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, *cls) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+static void pin_release(pdv_ctx* c, void* p, size_t cls) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(c->pin_mu);
+  c->pinned_free[cls].push_back(p);
+}
 
 struct pdv_cloud {
   pdv_ctx* ctx = nullptr;
@@ -187,6 +224,8 @@ extern "C" pdv_status pdv_ctx_destroy(pdv_ctx* c) {
     if (g.pinned) cudaFreeHost(g.pinned);
   }
   cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->pinned_free)
+    for (void* p : kv.second) cudaFreeHost(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -1173,7 +1212,7 @@ static void serving_stop(pdv_ctx* c) {
     auto& q = kv.second;
     if (q->arena) ctx_free(c, q->arena, c->serve_stream);
     if (q->fin) cudaEventDestroy(q->fin);
-    if (q->pinned) cudaFreeHost(q->pinned);
+    pin_release(c, q->pinned, q->pinned_bytes);
   }
   c->requests.clear();
   cudaStreamSynchronize(c->serve_stream);
@@ -1201,10 +1240,20 @@ extern "C" pdv_status pdv_submit(pdv_ctx* c, const pdv_request* r, pdv_ticket* o
     if ((int)c->requests.size() >= c->max_slots)
       return fail(PDV_EAGAIN, "all %d request slots are in use", c->max_slots);
   }
-  // admission by free device memory (keep 256 MiB in reserve)
-  size_t fr = 0, tot = 0;
-  CK(cudaMemGetInfo(&fr, &tot));
-  if (fr < q->b.bytes + (256ull << 20)) return fail(PDV_EAGAIN, "not enough free device memory");
+  // admission by free device memory (keep 256 MiB in reserve); the driver is
+  // asked at most every 20 ms and the bytes admitted since are subtracted
+  {
+    std::lock_guard<std::mutex> lk(c->smu);
+    const auto now = std::chrono::steady_clock::now();
+    if (now - c->mem_checked > std::chrono::milliseconds(20)) {
+      size_t fr = 0, tot = 0;
+      CK(cudaMemGetInfo(&fr, &tot));
+      c->mem_free = fr;
+      c->mem_checked = now;
+    }
+    if (c->mem_free < q->b.bytes + (256ull << 20)) return fail(PDV_EAGAIN, "not enough free device memory");
+    c->mem_free -= q->b.bytes;
+  }
   q->arena = (char*)ctx_alloc(c, q->b.bytes, c->serve_stream);
   if (!q->arena) return fail(PDV_EAGAIN, "request allocation failed");
   char* base = q->arena;
@@ -1219,25 +1268,37 @@ extern "C" pdv_status pdv_submit(pdv_ctx* c, const pdv_request* r, pdv_ticket* o
   unsigned long long* raw = r->out_raw ? (dev ? (unsigned long long*)r->out_raw : (unsigned long long*)(base + q->b.o_craw)) : nullptr;
   const unsigned flags = r->flags;
   cudaStream_t st = c->serve_stream;
-  if (!dev) {
-    Layout L;
-    q->o_spec = L.add(sizeof(double) * (size_t)r->n_snap * r->n_bins);
-    q->o_cnt = r->out_counters ? L.add(sizeof(pdv_counters) * r->n_snap) : 0;
-    q->o_raw = r->out_raw ? L.add(sizeof(unsigned long long) * (size_t)r->n_snap * (r->n_bins + 2)) : 0;
-    q->pinned_bytes = L.bytes;
-    CK(cudaMallocHost(&q->pinned, L.bytes));
+  // one pinned buffer per request: the uploads below (copied from pinned
+  // memory, so the driver never has to wait for the serving stream) and,
+  // for host outputs, the staged results
+  Layout L;
+  const size_t o_up_set = L.add(sizeof(SetDesc));
+  const size_t o_up_t = L.add(sizeof(double) * r->n_snap);
+  const size_t o_up_ptr = L.add(sizeof(void*) * 3 + sizeof(unsigned));
+  q->o_spec = dev ? 0 : L.add(sizeof(double) * (size_t)r->n_snap * r->n_bins);
+  q->o_cnt = (!dev && r->out_counters) ? L.add(sizeof(pdv_counters) * r->n_snap) : 0;
+  q->o_raw = (!dev && r->out_raw) ? L.add(sizeof(unsigned long long) * (size_t)r->n_snap * (r->n_bins + 2)) : 0;
+  q->pinned = pin_acquire(c, L.bytes, &q->pinned_bytes);
+  if (!q->pinned) {
+    ctx_free(c, q->arena, c->serve_stream);
+    return fail(PDV_EAGAIN, "pinned staging allocation failed");
   }
+  char* pin = (char*)q->pinned;
+  memcpy(pin + o_up_set, &q->d, sizeof(SetDesc));
+  memcpy(pin + o_up_t, q->ts.data(), sizeof(double) * r->n_snap);
+  void* ptrs[3] = {(void*)spec, (void*)cout, (void*)raw};
+  memcpy(pin + o_up_ptr, ptrs, sizeof ptrs);
+  memcpy(pin + o_up_ptr + sizeof ptrs, &flags, sizeof flags);
   CK(cudaEventCreateWithFlags(&q->fin, cudaEventDisableTiming));
-  CK(cudaMemcpyAsync(base + q->b.o_t, q->ts.data(), sizeof(double) * r->n_snap, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + q->b.o_set, &q->d, sizeof(SetDesc), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + q->b.o_ptr_spec, &spec, sizeof spec, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + q->b.o_ptr_cnt, &cout, sizeof cout, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + q->b.o_ptr_raw, &raw, sizeof raw, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(base + q->b.o_flags, &flags, sizeof flags, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + q->b.o_t, pin + o_up_t, sizeof(double) * r->n_snap, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + q->b.o_set, pin + o_up_set, sizeof(SetDesc), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + q->b.o_ptr_spec, pin + o_up_ptr, sizeof(void*), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + q->b.o_ptr_cnt, pin + o_up_ptr + sizeof(void*), sizeof(void*), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + q->b.o_ptr_raw, pin + o_up_ptr + 2 * sizeof(void*), sizeof(void*), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + q->b.o_flags, pin + o_up_ptr + sizeof ptrs, sizeof flags, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(base + q->b.o_cnt, 0, sizeof(unsigned long long) * C_NCOUNT, st));
   CK(cudaMemsetAsync(base + q->b.o_hist, 0, sizeof(unsigned long long) * hist_row(r->n_bins) * r->n_snap, st));
-  // (pageable host-to-device copies are staged when enqueued; the worker's
-  // launches for this request follow them on the same stream)
+  // (the worker's launches for this request follow these copies on the same stream)
   {
     std::lock_guard<std::mutex> lk(c->smu);
     q->id = c->next_ticket++;
@@ -1269,7 +1330,7 @@ extern "C" pdv_status pdv_poll(pdv_ctx* c, pdv_ticket t, uint32_t timeout_us) {
   const bool in_flight = q->state == 3 && q->next > q->done;
   if (!in_flight) {
     if (q->fin) cudaEventDestroy(q->fin);
-    if (q->pinned) cudaFreeHost(q->pinned);
+    pin_release(c, q->pinned, q->pinned_bytes);
     q->fin = nullptr;
     q->pinned = nullptr;
     c->requests.erase(it);

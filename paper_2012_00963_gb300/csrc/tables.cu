@@ -140,13 +140,32 @@ __global__ void k_phase_trap(const double* th, const double* p, int n, double* w
   work[i] = dmul(dmul(0.5, dadd(a, b)), th[i + 1] - th[i]);
 }
 
-// Sequential prefix (fixed order); work[n-1 + i] receives the cumulative C_i.
-__global__ void k_phase_prefix(double* work, int n) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  double* cum = work + (n - 1);
-  double c = 0.0;
-  cum[0] = 0.0;
-  for (int i = 0; i + 1 < n; ++i) {
+// Prefix sum of the trapezoids by one block in a fixed order (chunk sums,
+// then a sequential scan of the chunk totals): deterministic run to run.
+// work[n-1 + i] receives the cumulative C_i.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_phase_prefix(double* work, int n) {
+  __shared__ double tot[kScanThreads];
+  const int m = n - 1;                                  // number of trapezoids
+  const int chunk = (m + kScanThreads - 1) / kScanThreads;
+  const int b = threadIdx.x * chunk, e = min(b + chunk, m);
+  double s = 0.0;
+  for (int i = b; i < e; ++i) s = dadd(s, work[i]);
+  tot[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double run = 0.0;
+    for (int t = 0; t < kScanThreads; ++t) {
+      const double v = tot[t];
+      tot[t] = run;                                     // exclusive prefix of chunks
+      run = dadd(run, v);
+    }
+  }
+  __syncthreads();
+  double* cum = work + m;
+  double c = tot[threadIdx.x];
+  if (threadIdx.x == 0) cum[0] = 0.0;
+  for (int i = b; i < e; ++i) {
     c = dadd(c, work[i]);
     cum[i + 1] = c;
   }
@@ -188,26 +207,34 @@ __global__ void k_phase_guide(const unsigned* Cq, int n, unsigned short* Gp) {
   Gp[c] = (unsigned short)lo;
 }
 
-// Mean cosine of the sampled law (uniform theta inside each CDF bin).
-__global__ void k_phase_gtab(const unsigned* Cq, const double* th, int n, double* g) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+// Mean cosine of the sampled law (uniform theta inside each CDF bin): terms
+// in parallel, one block, fixed-order tree reduction.
+__global__ void __launch_bounds__(kScanThreads) k_phase_gtab(const unsigned* Cq, const double* th,
+                                                             int n, double* g) {
+  __shared__ double part[kScanThreads];
   double s = 0.0;
-  for (int i = 0; i + 1 < n; ++i) {
+  for (int i = threadIdx.x; i + 1 < n; i += kScanThreads) {
     const double dc = (double)(Cq[i + 1] - Cq[i]) / 16777216.0;
     s += dc * (sin(th[i + 1]) - sin(th[i])) / (th[i + 1] - th[i]);
   }
-  *g = s;
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kScanThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *g = part[0];
 }
 
 cudaError_t build_phase_cdf(const double* d_theta, const double* d_p, int n, double* d_work,
                             CloudTables* t, double* d_gtab, cudaStream_t st) {
   const int nb = (n + 255) / 256;
   k_phase_trap<<<nb, 256, 0, st>>>(d_theta, d_p, n, d_work);
-  k_phase_prefix<<<1, 1, 0, st>>>(d_work, n);
+  k_phase_prefix<<<1, kScanThreads, 0, st>>>(d_work, n);
   k_phase_quant<<<nb, 256, 0, st>>>(d_work, d_theta, n, t->Cq, t->thpi, t->th_d);
   k_phase_slopes<<<nb, 256, 0, st>>>(t->Cq, d_theta, n, t->dthpi);
   k_phase_guide<<<((1 << kGuidePhaseLog) + 1 + 255) / 256, 256, 0, st>>>(t->Cq, n, t->Gp);
-  k_phase_gtab<<<1, 1, 0, st>>>(t->Cq, d_theta, n, d_gtab);
+  k_phase_gtab<<<1, kScanThreads, 0, st>>>(t->Cq, d_theta, n, d_gtab);
   return cudaGetLastError();
 }
 

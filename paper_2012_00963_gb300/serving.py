@@ -1,0 +1,142 @@
+"""Serving-side parameter sweep over the library's continuous-batching loop.
+
+A stream of spectrum requests arrives as a Poisson process. Each request is a
+candidate (beta, m0, d) of a fit to a target spectrum (Section III: the
+spectrum is fixed mainly by beta and the optical depth tau0, so m0 and d are
+degenerate along m0/d). Requests are admitted with pdv_submit while others are
+running and finish through pdv_poll; the driver records every request's
+latency (submit to completion) and keeps the best candidate.
+
+The library does all Monte Carlo work on the GPU; this module only proposes
+parameters, marshals requests and scores finished spectra (a chi-square
+between two histograms on the host).
+"""
+from __future__ import annotations
+
+import math
+import threading
+import time
+from dataclasses import dataclass, field
+from typing import List
+
+import numpy as np
+
+from . import pdv
+from . import workloads as W
+
+
+@dataclass
+class SweepResult:
+    latencies_ms: List[float] = field(default_factory=list)
+    completed: int = 0
+    rejected: int = 0
+    wall_s: float = 0.0
+    best: dict = field(default_factory=dict)
+    submitted: int = 0
+
+
+def chi2(h_c, n_c, h_t, n_t, min_counts=10.0):
+    """Chi-square per bin between a candidate's and the target's weight
+    histograms (packet units) normalised per launched packet, over the bins
+    where the target holds at least `min_counts`; the variance of both sides
+    is taken from the target's rate (the null hypothesis)."""
+    s_c, s_t = h_c / n_c, h_t / n_t
+    sel = h_t >= min_counts
+    var = s_t[sel] * (1.0 / n_c + 1.0 / n_t)
+    return float(np.sum((s_c[sel] - s_t[sel]) ** 2 / var)), int(sel.sum())
+
+
+def run_sweep(ctx: pdv.Context, target_hist, target_packets, probe: dict, duration: float = 60.0,
+              rate: float = 200.0, seed: int = 5, n_min: float = 1e5, n_max: float = 1e7,
+              explore: float = 0.2, poll_us: int = 200,
+              min_best_packets: int = 1_000_000) -> SweepResult:
+    arrivals = W.cfg5_arrivals(rate=rate, duration=duration, seed=seed, n_min=n_min,
+                               n_max=n_max)
+    rng = np.random.default_rng(seed + 1)
+    res = SweepResult()
+    lock = threading.Lock()
+    pending = {}            # ticket -> (request, cloud, t_submit, params)
+    best = {"chi2": math.inf}
+    target = np.asarray(target_hist, np.float64)
+    done_submitting = threading.Event()
+
+    def poller():
+        while True:
+            with lock:
+                items = list(pending.items())
+            if not items:
+                if done_submitting.is_set():
+                    return
+                time.sleep(0.0002)
+                continue
+            for t, (req, cloud, t0, params) in items:
+                st = pdv.pdv_poll(ctx.handle, t, poll_us // max(len(items), 1))
+                if st != pdv.PDV_OK:
+                    continue
+                t1 = time.perf_counter()
+                h = req.raw[0, 1:-1].astype(np.float64) / 2.0**32
+                c2, dof = chi2(h, req.c.n_packets, target, target_packets)
+                with lock:
+                    del pending[t]
+                    res.latencies_ms.append(1e3 * (t1 - t0))
+                    res.completed += 1
+                    # only well-sampled candidates can become the best fit
+                    if dof and req.c.n_packets >= min_best_packets and c2 / dof < best["chi2"]:
+                        best.update(chi2=c2 / dof, tau0=cloud.info()["tau_tot"], **params)
+
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    clouds = []
+    t_start = time.perf_counter()
+    for k, a in enumerate(arrivals):
+        now = time.perf_counter() - t_start
+        if a.t > now:
+            time.sleep(a.t - now)
+        with lock:
+            have_best = math.isfinite(best["chi2"])
+            b = dict(best)
+        if k < explore * len(arrivals) or not have_best:
+            params = dict(beta=a.beta, m0=a.m0, d_m=a.d_m)
+        else:
+            scale = max(0.02, 0.3 * (1.0 - k / len(arrivals)))
+            params = dict(beta=b["beta"] * math.exp(scale * rng.standard_normal()),
+                          m0=b["m0"] * math.exp(scale * rng.standard_normal()),
+                          d_m=b["d_m"] * math.exp(scale * rng.standard_normal()))
+            params["beta"] = min(max(params["beta"], 1.0), 20.0)
+        wl = W.cfg5_request(W.Arrival(t=a.t, n_packets=a.n_packets, seed=a.seed, **params),
+                            **probe)
+        cloud = pdv.Cloud(ctx, wl)
+        clouds.append(cloud)
+        req = pdv.Request(cloud, wl, raw=True, counters=False)
+        t0 = time.perf_counter()
+        while True:
+            try:
+                ticket = pdv.pdv_submit(ctx.handle, req.c)
+                break
+            except pdv.PdvError as e:
+                if e.status != pdv.PDV_EAGAIN:
+                    raise
+                res.rejected += 1
+                time.sleep(0.001)
+        with lock:
+            pending[ticket] = (req, cloud, t0, params)
+        res.submitted += 1
+    done_submitting.set()
+    th.join()
+    res.wall_s = time.perf_counter() - t_start
+    res.best = best
+    for c in clouds:
+        c.close()
+    return res
+
+
+def summary(res: SweepResult, hidden: dict) -> dict:
+    lat = np.asarray(res.latencies_ms)
+    return {
+        "requests": res.submitted, "completed": res.completed, "rejected_retries": res.rejected,
+        "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+        "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+        "spectra_per_s": res.completed / res.wall_s if res.wall_s else None,
+        "recovered": {k: res.best.get(k) for k in ("beta", "m0", "d_m", "tau0", "chi2")},
+        "hidden": hidden,
+    }

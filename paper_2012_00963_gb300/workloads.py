@@ -119,7 +119,8 @@ def cfg4_sets(n_sets: int = 256, seed: int = 4, n_min: float = 1e5, n_max: float
     """256 parameter sets: beta ~ U(2, 10), m0 ~ logU(0.1, 20) mg/cm^2,
     d ~ logU(0.5, 10) um, v_fs ~ U(1.5, 3) km/s, t ~ U(1, 4) us, packets ~
     logU(n_min, n_max); monodisperse Mie 3+9i, one snapshot, bins over
-    [0, v_max of the set]."""
+    [0, v_max of the set]. The probe sits 120 mm above the sample: the fastest
+    clouds of these ranges (beta = 2, v_fs = 3 km/s) reach about 95 mm at 4 us."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n_sets):
@@ -133,7 +134,8 @@ def cfg4_sets(n_sets: int = 256, seed: int = 4, n_min: float = 1e5, n_max: float
         out.append(Workload(
             name="cfg4[%d]" % i, m0=m0, beta=beta, v_max=0.0, v_fs=v_fs, d_m=d, sigma_ln=0.0,
             phase=Phase(kind="mie", m=3.0 + 9.0j, n_angle=1801, n_size=1), t_snap=(t,),
-            n_bins=n_bins, v_lo=0.0, v_hi=v_top, n_packets=n, seed=1000 + i, stream_id=i))
+            n_bins=n_bins, v_lo=0.0, v_hi=v_top, n_packets=n, seed=1000 + i, stream_id=i,
+            z_probe=120.0 * MM))
     return out
 
 

@@ -186,6 +186,7 @@ def test_device_outputs_match_host_outputs(ctx):
     dev = {"spectrum": torch.zeros(ns * nb, dtype=torch.float64, device="cuda"),
            "raw": torch.zeros(ns * (nb + 2), dtype=torch.int64, device="cuda")}
     req = pdv.Request(cloud, wl, per_dv=True, device_out=dev)
+    torch.cuda.synchronize()      # order torch's zero-fills before the context's stream
     pdv.pdv_simulate_spectrum(ctx.handle, req.c)
     torch.cuda.synchronize()
     cloud.close()
@@ -250,6 +251,7 @@ def test_full_size_cfg2_sampled_packets(ctx):
     dev = {"spectrum": torch.zeros(ns * nb, dtype=torch.float64, device="cuda"),
            "raw": torch.zeros(ns * (nb + 2), dtype=torch.int64, device="cuda"), "packets": pk}
     req = pdv.Request(cloud, wl, device_out=dev)
+    torch.cuda.synchronize()      # the zero-fills above run on torch's stream, not the context's
     pdv.pdv_simulate_spectrum(ctx.handle, req.c)
     torch.cuda.synchronize()
     got_raw = dev["raw"].cpu().numpy().view(np.uint64).reshape(ns, nb + 2)

@@ -35,6 +35,7 @@ def _device_outputs(torch, wl):
 def _run(ctx, cloud, wl, torch, static):
     out = _device_outputs(torch, wl)
     req = pdv.Request(cloud, wl, device_out=out)
+    torch.cuda.synchronize()      # the fills run on torch's stream, not the context's
     if static:
         pdv.pdv_simulate_spectrum_static(ctx.handle, req.c)
     else:
