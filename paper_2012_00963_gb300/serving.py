@@ -33,6 +33,7 @@ class SweepResult:
     wall_s: float = 0.0
     best: dict = field(default_factory=dict)
     submitted: int = 0
+    records: List[dict] = field(default_factory=list)
 
 
 def chi2(h_c, n_c, h_t, n_t, min_counts=10.0):
@@ -44,6 +45,30 @@ def chi2(h_c, n_c, h_t, n_t, min_counts=10.0):
     sel = h_t >= min_counts
     var = s_t[sel] * (1.0 / n_c + 1.0 / n_t)
     return float(np.sum((s_c[sel] - s_t[sel]) ** 2 / var)), int(sel.sum())
+
+
+def surrogate_estimate(records, min_packets=1_000_000, keep=0.4, min_points=12):
+    """Vertex of a least-squares quadratic in (log beta, log tau0) fitted to
+    chi^2/dof of the best-scoring well-sampled candidates; None when fewer than
+    `min_points` qualify or the fitted bowl is not convex. Beta and tau0 are the
+    two parameters a single spectrum fixes (Eq. 35)."""
+    r = [x for x in records if x["n"] >= min_packets]
+    if len(r) < min_points:
+        return None
+    r.sort(key=lambda x: x["chi2"])
+    r = r[:max(min_points, int(len(r) * keep))]
+    X = np.log([x["beta"] for x in r])
+    Y = np.log([x["tau0"] for x in r])
+    Z = np.array([x["chi2"] for x in r])
+    A = np.stack([np.ones_like(X), X, Y, X * X, Y * Y, X * Y], axis=1)
+    (a, b, c, d, e, f), *_ = np.linalg.lstsq(A, Z, rcond=None)
+    H = np.array([[2 * d, f], [f, 2 * e]])
+    if np.any(np.linalg.eigvalsh(H) <= 0):
+        return None
+    x0, y0 = np.linalg.solve(H, [-b, -c])
+    if not (X.min() - 1 <= x0 <= X.max() + 1 and Y.min() - 1 <= y0 <= Y.max() + 1):
+        return None
+    return {"beta": float(math.exp(x0)), "tau0": float(math.exp(y0)), "points": len(r)}
 
 
 def run_sweep(ctx: pdv.Context, target_hist, target_packets, probe: dict, duration: float = 60.0,
@@ -59,6 +84,7 @@ def run_sweep(ctx: pdv.Context, target_hist, target_packets, probe: dict, durati
     best = {"chi2": math.inf}
     target = np.asarray(target_hist, np.float64)
     done_submitting = threading.Event()
+    surrogate_center = {}
 
     def poller():
         while True:
@@ -76,13 +102,18 @@ def run_sweep(ctx: pdv.Context, target_hist, target_packets, probe: dict, durati
                 t1 = time.perf_counter()
                 h = req.raw[0, 1:-1].astype(np.float64) / 2.0**32
                 c2, dof = chi2(h, req.c.n_packets, target, target_packets)
+                tau0 = cloud.info()["tau_tot"]
                 with lock:
                     del pending[t]
                     res.latencies_ms.append(1e3 * (t1 - t0))
                     res.completed += 1
+                    if dof:
+                        res.records.append(dict(beta=params["beta"], tau0=tau0, m0=params["m0"],
+                                                d_m=params["d_m"], chi2=c2 / dof,
+                                                n=int(req.c.n_packets)))
                     # only well-sampled candidates can become the best fit
                     if dof and req.c.n_packets >= min_best_packets and c2 / dof < best["chi2"]:
-                        best.update(chi2=c2 / dof, tau0=cloud.info()["tau_tot"], **params)
+                        best.update(chi2=c2 / dof, tau0=tau0, **params)
 
     th = threading.Thread(target=poller, daemon=True)
     th.start()
@@ -95,6 +126,18 @@ def run_sweep(ctx: pdv.Context, target_hist, target_packets, probe: dict, durati
         with lock:
             have_best = math.isfinite(best["chi2"])
             b = dict(best)
+            recs = list(res.records) if k % 50 == 0 else None
+        if recs is not None and have_best:
+            sur = surrogate_estimate(recs)
+            if sur is not None:
+                # move the proposal centre to the surrogate's vertex, keeping m0/d
+                # on the line that gives its tau0 (tau0 is linear in m0/d)
+                center = dict(b)
+                center["beta"] = sur["beta"]
+                center["m0"] = b["m0"] * sur["tau0"] / b["tau0"]
+                surrogate_center.update(center)
+        if surrogate_center:
+            b = dict(b, **surrogate_center)
         if k < explore * len(arrivals) or not have_best:
             params = dict(beta=a.beta, m0=a.m0, d_m=a.d_m)
         else:
@@ -137,6 +180,7 @@ def summary(res: SweepResult, hidden: dict) -> dict:
         "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
         "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
         "spectra_per_s": res.completed / res.wall_s if res.wall_s else None,
-        "recovered": {k: res.best.get(k) for k in ("beta", "m0", "d_m", "tau0", "chi2")},
+        "best_candidate": {k: res.best.get(k) for k in ("beta", "m0", "d_m", "tau0", "chi2")},
+        "recovered": surrogate_estimate(res.records),
         "hidden": hidden,
     }
