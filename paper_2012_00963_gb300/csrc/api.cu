@@ -377,6 +377,9 @@ extern "C" pdv_status pdv_set_phase_table(pdv_cloud* cl, int n, const double* th
     if (i) total += 0.5 * (p[i - 1] * std::sin(theta[i - 1]) + p[i] * std::sin(theta[i])) * (theta[i] - theta[i - 1]);
   }
   if (!(total > 0)) return fail(PDV_EINVAL, "phase function integrates to zero");
+  bool uniform = true;
+  for (int i = 0; i < n && uniform; ++i)
+    uniform = std::fabs(theta[i] - M_PI * (double)i / (double)(n - 1)) <= 1e-12;
   if (!(q_ext >= 0) || !std::isfinite(q_ext)) return fail(PDV_EINVAL, "q_ext must be >= 0");
   if (!(albedo >= 0 && albedo <= 1)) return fail(PDV_EINVAL, "albedo must be in [0,1]");
   pdv_ctx* c = cl->ctx;
@@ -406,6 +409,7 @@ extern "C" pdv_status pdv_set_phase_table(pdv_cloud* cl, int n, const double* th
   cl->t.th_d = (double*)(base + othd);
   cl->t.Gp = (unsigned short*)(base + oGp);
   cl->t.n_p = n;
+  cl->t.phase_uniform = uniform ? 1 : 0;
   double* din = (double*)(base + oin);
   double* dwk = (double*)(base + owk);
   double* dg = (double*)(base + og);
@@ -557,6 +561,8 @@ static SetDesc make_set(const pdv_request* r) {
   d.Sq = cl->t.Sq; d.Sd = cl->t.Sd; d.w = cl->t.w; d.G = cl->t.G;
   d.Cq = cl->t.Cq; d.thpi = cl->t.thpi; d.dthpi = cl->t.dthpi; d.th_d = cl->t.th_d; d.Gp = cl->t.Gp;
   d.n_v = cl->t.n_v; d.n_g = cl->t.n_g; d.g_shift = cl->t.g_shift; d.n_p = cl->t.n_p;
+  d.phase_uniform = cl->t.phase_uniform;
+  d.inv_nm1 = (float)(1.0 / (double)(cl->t.n_p - 1));
   d.n_snap = r->n_snap; d.n_bins = r->n_bins;
   d.surface_mode = cl->desc.surface_mode;
   d.cone_all = r->probe.cone_half_angle_rad >= 0.5 * M_PI;
@@ -589,6 +595,25 @@ static SetDesc make_set(const pdv_request* r) {
   return d;
 }
 
+// Snapshot times as the kernels read them: the times in request order
+// (seconds), the same times ascending, and the request index of each
+// ascending time (as a double). The FP32 kernel walks the ascending list to
+// visit only the times at which an escaping packet is inside the aperture.
+static size_t time_words(int n_snap) { return 3 * (size_t)n_snap; }
+
+static void fill_times(const pdv_request* r, double* out) {
+  const int n = r->n_snap;
+  int idx[kMaxSnap];
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  const double* t = r->t_snap_us;
+  std::sort(idx, idx + n, [t](int a, int b) { return t[a] < t[b] || (t[a] == t[b] && a < b); });
+  for (int i = 0; i < n; ++i) {
+    out[i] = t[i] * 1e-6;
+    out[n + i] = t[idx[i]] * 1e-6;
+    out[2 * n + i] = (double)idx[i];
+  }
+}
+
 // Device buffers of one request: set descriptor, counters, histogram,
 // snapshot times and staged outputs.
 struct ReqBuffers {
@@ -605,7 +630,7 @@ static ReqBuffers plan_request(const pdv_request* r, bool device_out) {
   b.o_ctr = L.add(sizeof(unsigned long long));
   b.o_cnt = L.add(sizeof(unsigned long long) * C_NCOUNT);
   b.o_hist = L.add(sizeof(unsigned long long) * row * r->n_snap);
-  b.o_t = L.add(sizeof(double) * r->n_snap);
+  b.o_t = L.add(sizeof(double) * time_words(r->n_snap));
   b.o_spec = device_out ? 0 : L.add(sizeof(double) * (size_t)r->n_snap * r->n_bins);
   b.o_craw = (!device_out && r->out_raw) ? L.add(sizeof(unsigned long long) * (size_t)r->n_snap * (r->n_bins + 2)) : 0;
   b.o_cout = (!device_out && r->out_counters) ? L.add(sizeof(pdv_counters) * r->n_snap) : 0;
@@ -618,10 +643,14 @@ static ReqBuffers plan_request(const pdv_request* r, bool device_out) {
   return b;
 }
 
+static size_t set_smem(const SetDesc& d, int hm) {
+  return transport_f32_smem(d.n_v, d.n_g, d.n_p, d.n_snap, d.n_bins, hm, d.phase_uniform);
+}
+
 static int pick_hist_mode(const pdv_ctx* c, const SetDesc& d) {
   if (c->tuning.hist_mode == 1) return 1;
-  const size_t tables = transport_f32_smem(d.n_v, d.n_g, d.n_p, d.n_snap, d.n_bins, 1);
-  const size_t priv = transport_f32_smem(d.n_v, d.n_g, d.n_p, d.n_snap, d.n_bins, 2);
+  const size_t tables = set_smem(d, 1);
+  const size_t priv = set_smem(d, 2);
   if (c->tuning.hist_mode == 2) return priv <= (size_t)c->max_smem ? 2 : 1;
   // auto: privatise when the histogram is small next to the tables
   return (priv - tables) <= 16384 && priv <= (size_t)c->max_smem ? 2 : 1;
@@ -649,7 +678,7 @@ static pdv_status enqueue_transport(pdv_ctx* c, const pdv_request* r, const SetD
   if (r->precision == PDV_PREC_FP32) {
     const int hm = pick_hist_mode(c, d);
     const bool dump = d.packets != nullptr;
-    const size_t smem = transport_f32_smem(d.n_v, d.n_g, d.n_p, d.n_snap, d.n_bins, hm);
+    const size_t smem = set_smem(d, hm);
     if (smem > (size_t)c->max_smem) return fail(PDV_EINVAL, "tables need %zu bytes of shared memory (max %d)", smem, c->max_smem);
     int grid = 0, block = 0;
     pdv_status s = f32_geometry(c, smem, hm, dump, &grid, &block);
@@ -692,13 +721,13 @@ extern "C" pdv_status pdv_simulate_spectrum(pdv_ctx* c, const pdv_request* r) {
   d.hist = (unsigned long long*)(base + b.o_hist);
   d.cnt = (unsigned long long*)(base + b.o_cnt);
   d.packets = r->out_packets ? (dev_out ? r->out_packets : (pdv_packet_record*)(base + b.o_pk)) : nullptr;
-  std::vector<double> ts(r->n_snap);
-  for (int i = 0; i < r->n_snap; ++i) ts[i] = r->t_snap_us[i] * 1e-6;
+  std::vector<double> ts(time_words(r->n_snap));
+  fill_times(r, ts.data());
   double* spec = dev_out ? r->out_spectrum : (double*)(base + b.o_spec);
   pdv_counters* cout = r->out_counters ? (dev_out ? r->out_counters : (pdv_counters*)(base + b.o_cout)) : nullptr;
   unsigned long long* raw = r->out_raw ? (dev_out ? (unsigned long long*)r->out_raw : (unsigned long long*)(base + b.o_craw)) : nullptr;
   const unsigned flags = r->flags;
-  CK(cudaMemcpyAsync(base + b.o_t, ts.data(), sizeof(double) * r->n_snap, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + b.o_t, ts.data(), sizeof(double) * ts.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(base + b.o_set, &d, sizeof d, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(base + b.o_ptr_spec, &spec, sizeof spec, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(base + b.o_ptr_cnt, &cout, sizeof cout, cudaMemcpyHostToDevice, st));
@@ -755,7 +784,7 @@ static BatchLayout plan_batch(const pdv_request* rs, int n) {
   B.hist_words = hw;
   B.o_hist = L.add(sizeof(unsigned long long) * hw);
   size_t tw = 0;
-  for (int i = 0; i < n; ++i) tw += rs[i].n_snap;
+  for (int i = 0; i < n; ++i) tw += time_words(rs[i].n_snap);
   B.o_t = L.add(sizeof(double) * tw);
   B.o_pspec = L.add(sizeof(void*) * n);
   B.o_pcnt = L.add(sizeof(void*) * n);
@@ -768,7 +797,7 @@ static BatchLayout plan_batch(const pdv_request* rs, int n) {
     B.o_hist_i.push_back(B.o_hist + sizeof(unsigned long long) * h);
     B.o_t_i.push_back(B.o_t + sizeof(double) * t);
     h += (size_t)hist_row(r.n_bins) * r.n_snap;
-    t += r.n_snap;
+    t += time_words(r.n_snap);
     B.o_spec_i.push_back(dev ? 0 : L.add(sizeof(double) * (size_t)r.n_snap * r.n_bins));
     B.o_raw_i.push_back((!dev && r.out_raw) ? L.add(sizeof(unsigned long long) * (size_t)r.n_snap * (r.n_bins + 2)) : 0);
     B.o_cout_i.push_back((!dev && r.out_counters) ? L.add(sizeof(pdv_counters) * r.n_snap) : 0);
@@ -810,7 +839,7 @@ static pdv_status run_batch_f32(pdv_ctx* c, const pdv_request* rs, int n, bool t
   }
   for (int i = 0; i < n; ++i) {
     const SetDesc& d = sets[i];
-    smem = std::max(smem, transport_f32_smem(d.n_v, d.n_g, d.n_p, d.n_snap, d.n_bins, hm));
+    smem = std::max(smem, set_smem(d, hm));
   }
   if (smem > (size_t)c->max_smem) return fail(PDV_EINVAL, "batch tables need %zu bytes of shared memory", smem);
   int grid = 0, block = 0;
@@ -883,7 +912,9 @@ static pdv_status run_batch_f32(pdv_ctx* c, const pdv_request* rs, int n, bool t
     d.hist = (unsigned long long*)(base + B.o_hist_i[i]);
     d.cnt = (unsigned long long*)(base + B.o_cnt) + (size_t)C_NCOUNT * i;
     d.packets = r.out_packets ? (dev ? r.out_packets : (pdv_packet_record*)(base + B.o_pk_i[i])) : nullptr;
-    for (int k = 0; k < r.n_snap; ++k) ts.push_back(r.t_snap_us[k] * 1e-6);
+    const size_t at = ts.size();
+    ts.resize(at + time_words(r.n_snap));
+    fill_times(&r, ts.data() + at);
     pspec[i] = dev ? (void*)r.out_spectrum : (void*)(base + B.o_spec_i[i]);
     pcnt[i] = r.out_counters ? (dev ? (void*)r.out_counters : (void*)(base + B.o_cout_i[i])) : nullptr;
     praw[i] = r.out_raw ? (dev ? (void*)r.out_raw : (void*)(base + B.o_raw_i[i])) : nullptr;
@@ -1162,7 +1193,7 @@ static void serving_loop(pdv_ctx* c) {
     int hm = 1;
     for (int k = 0; k < n; ++k) {
       const SetDesc& d = s.h_sets[k];
-      smem = std::max(smem, transport_f32_smem(d.n_v, d.n_g, d.n_p, d.n_snap, d.n_bins, 1));
+      smem = std::max(smem, set_smem(d, 1));
     }
     int grid = 0, block = 0;
     if (f32_geometry(c, smem, hm, false, &grid, &block) != PDV_OK) {
@@ -1232,8 +1263,8 @@ extern "C" pdv_status pdv_submit(pdv_ctx* c, const pdv_request* r, pdv_ticket* o
   const bool dev = (r->flags & PDV_OUT_DEVICE) != 0;
   auto q = std::make_shared<Request>();
   q->req = *r;
-  q->ts.assign(r->t_snap_us, r->t_snap_us + r->n_snap);
-  for (auto& t : q->ts) t *= 1e-6;
+  q->ts.resize(time_words(r->n_snap));
+  fill_times(r, q->ts.data());
   q->b = plan_request(r, dev);
   {
     std::lock_guard<std::mutex> lk(c->smu);
@@ -1273,7 +1304,7 @@ extern "C" pdv_status pdv_submit(pdv_ctx* c, const pdv_request* r, pdv_ticket* o
   // for host outputs, the staged results
   Layout L;
   const size_t o_up_set = L.add(sizeof(SetDesc));
-  const size_t o_up_t = L.add(sizeof(double) * r->n_snap);
+  const size_t o_up_t = L.add(sizeof(double) * time_words(r->n_snap));
   const size_t o_up_ptr = L.add(sizeof(void*) * 3 + sizeof(unsigned));
   q->o_spec = dev ? 0 : L.add(sizeof(double) * (size_t)r->n_snap * r->n_bins);
   q->o_cnt = (!dev && r->out_counters) ? L.add(sizeof(pdv_counters) * r->n_snap) : 0;
@@ -1285,12 +1316,12 @@ extern "C" pdv_status pdv_submit(pdv_ctx* c, const pdv_request* r, pdv_ticket* o
   }
   char* pin = (char*)q->pinned;
   memcpy(pin + o_up_set, &q->d, sizeof(SetDesc));
-  memcpy(pin + o_up_t, q->ts.data(), sizeof(double) * r->n_snap);
+  memcpy(pin + o_up_t, q->ts.data(), sizeof(double) * q->ts.size());
   void* ptrs[3] = {(void*)spec, (void*)cout, (void*)raw};
   memcpy(pin + o_up_ptr, ptrs, sizeof ptrs);
   memcpy(pin + o_up_ptr + sizeof ptrs, &flags, sizeof flags);
   CK(cudaEventCreateWithFlags(&q->fin, cudaEventDisableTiming));
-  CK(cudaMemcpyAsync(base + q->b.o_t, pin + o_up_t, sizeof(double) * r->n_snap, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + q->b.o_t, pin + o_up_t, sizeof(double) * q->ts.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(base + q->b.o_set, pin + o_up_set, sizeof(SetDesc), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(base + q->b.o_ptr_spec, pin + o_up_ptr, sizeof(void*), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(base + q->b.o_ptr_cnt, pin + o_up_ptr + sizeof(void*), sizeof(void*), cudaMemcpyHostToDevice, st));
@@ -1400,12 +1431,12 @@ extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request
   const size_t o_cnt = L.add(sizeof(unsigned long long) * C_NCOUNT);
   const size_t hist_words = (size_t)hist_row(r->n_bins) * r->n_snap;
   const size_t o_hist = L.add(sizeof(unsigned long long) * hist_words);
-  const size_t o_t = L.add(sizeof(double) * r->n_snap);
+  const size_t o_t = L.add(sizeof(double) * time_words(r->n_snap));
   const size_t o_ptr = L.add(sizeof(void*) * 3);
   const size_t o_flags = L.add(sizeof(unsigned));
   if (L.bytes > kStaticScratchBytes)
     return fail(PDV_EINVAL, "request needs %zu bytes of scratch; the static scratch holds %zu "
-                "(n_snap * (n_bins + 3) * 8 + n_snap * 8 + about 1 KiB)", L.bytes, kStaticScratchBytes);
+                "(n_snap * (n_bins + 3) * 8 + n_snap * 24 + about 1 KiB)", L.bytes, kStaticScratchBytes);
   CK(enter(c->device));
   char* base = nullptr;
   s = static_scratch_address(c->device, &base);
@@ -1417,11 +1448,11 @@ extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request
   d.hist = (unsigned long long*)(base + o_hist);
   d.cnt = (unsigned long long*)(base + o_cnt);
   d.packets = r->out_packets;
-  double ts[kMaxSnap];
-  for (int i = 0; i < r->n_snap; ++i) ts[i] = r->t_snap_us[i] * 1e-6;
+  double ts[3 * kMaxSnap];          // on the stack: no allocation, heap or TLS
+  fill_times(r, ts);
   void* ptrs[3] = {(void*)r->out_spectrum, (void*)r->out_counters, (void*)r->out_raw};
   const unsigned flags = r->flags;
-  CK(cudaMemcpyAsync(base + o_t, ts, sizeof(double) * r->n_snap, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_t, ts, sizeof(double) * time_words(r->n_snap), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(base + o_set, &d, sizeof d, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(base + o_ptr, ptrs, sizeof ptrs, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(base + o_flags, &flags, sizeof flags, cudaMemcpyHostToDevice, st));
@@ -1431,7 +1462,7 @@ extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request
   CK(cudaMemsetAsync(base + o_hist, 0, sizeof(unsigned long long) * hist_words, st));
   const int hm = pick_hist_mode(c, d);
   const bool dump = d.packets != nullptr;
-  const size_t smem = transport_f32_smem(d.n_v, d.n_g, d.n_p, d.n_snap, d.n_bins, hm);
+  const size_t smem = set_smem(d, hm);
   if (smem > (size_t)c->max_smem) return fail(PDV_EINVAL, "tables need %zu bytes of shared memory", smem);
   int grid = 0, block = 0;
   s = f32_geometry(c, smem, hm, dump, &grid, &block);

@@ -60,6 +60,7 @@ struct CloudTables {
   double* th_d = nullptr;             // [n_p] theta (FP64 path)
   unsigned short* Gp = nullptr;       // [n_gp + 1] guide over the 2^24 CDF
   int n_p = 0;
+  int phase_uniform = 0;              // theta grid uniform over [0, pi]
 };
 
 // Everything the transport needs for one request ("set"), by value.
@@ -73,20 +74,20 @@ struct SetDesc {
   const float* dthpi;
   const double* th_d;
   const unsigned short* Gp;
-  const double* t_snap;               // [n_snap] seconds
+  const double* t_snap;               // [3 n_snap]: seconds in request order, ascending, index
   unsigned long long* hist;           // [n_snap][n_bins + 3]
   unsigned long long* cnt;            // [C_NCOUNT]
   pdv_packet_record* packets;         // optional [n_packets]
   int n_v, n_g, g_shift, n_p;
   int n_snap, n_bins;
-  int surface_mode, cone_all, ap_all, pad0;
+  int surface_mode, cone_all, ap_all, phase_uniform;   // theta_i = pi i / (n_p - 1)
   unsigned omega_q, stream_id, max_events, pad1;
   unsigned long long R_q, seed, packet_begin, n_packets;
   unsigned long long norm_packets;    // packets of the whole request (normalisation)
   double tau_tot, inv_tau, v_bot, dv, v_top, v_fs;
   double z_probe, r_beam, r_ap2, cos_alpha, v_lo, inv_dbin;
   float inv_tau_f, v_bot_f, dv_f, v_top_f, v_fs_f, z_probe_f, r_beam_f, r_ap2_f;
-  float cos_alpha_f, v_lo_f, inv_dbin_f, pad2;
+  float cos_alpha_f, v_lo_f, inv_dbin_f, inv_nm1;      // 1 / (n_p - 1)
 };
 
 // ------------------------------------------------------------- Philox4x32-10
@@ -150,7 +151,8 @@ void launch_transport_f64(const SetDesc* d_set, int grid, int block, cudaStream_
 void launch_normalise(const SetDesc* d_sets, int n_sets, double* const* d_spec,
                       pdv_counters* const* d_cnt_out, unsigned long long* const* d_raw,
                       const unsigned* flags, int max_snap, cudaStream_t st);
-size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode);
+size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode,
+                          int phase_uniform);
 int transport_f32_max_smem();
 cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, int* blocks);
 

@@ -35,32 +35,37 @@ struct SmemTables {
   const float* thpi;
   const float* dthpi;
   const unsigned short* Gp;
-  const float* ts;
+  const float* ts;                    // snapshot times, ascending (seconds)
+  const unsigned short* perm;         // request index of each ascending time
   unsigned long long* hist;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Shared-memory bytes for one set's staged tables (and optional histogram).
+// A uniform theta grid needs no per-node angle arrays.
 __host__ __device__ inline size_t smem_layout(int n_v, int n_g, int n_p, int n_snap, int n_bins,
-                                              int hist_mode, size_t* off) {
+                                              int hist_mode, int phase_uniform, size_t* off) {
+  const size_t n_th = phase_uniform ? 0 : (size_t)n_p;
   size_t o = 0;
   off[0] = o; o = align16(o + sizeof(unsigned long long) * (size_t)(n_v + 1));   // Sq
   off[1] = o; o = align16(o + sizeof(float) * (size_t)n_v);                       // w
   off[2] = o; o = align16(o + sizeof(unsigned short) * (size_t)(n_g + 1));        // G
   off[3] = o; o = align16(o + sizeof(unsigned) * (size_t)n_p);                    // Cq
-  off[4] = o; o = align16(o + sizeof(float) * (size_t)n_p);                       // thpi
-  off[5] = o; o = align16(o + sizeof(float) * (size_t)n_p);                       // dthpi
+  off[4] = o; o = align16(o + sizeof(float) * n_th);                              // thpi
+  off[5] = o; o = align16(o + sizeof(float) * n_th);                              // dthpi
   off[6] = o; o = align16(o + sizeof(unsigned short) * ((1 << kGuidePhaseLog) + 1));  // Gp
   off[7] = o; o = align16(o + sizeof(float) * (size_t)n_snap);                    // ts
-  off[8] = o;
+  off[8] = o; o = align16(o + sizeof(unsigned short) * (size_t)n_snap);           // perm
+  off[9] = o;
   if (hist_mode == 2) o = align16(o + sizeof(unsigned long long) * (size_t)n_snap * hist_row(n_bins));
   return o;
 }
 
-size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode) {
-  size_t off[9];
-  return smem_layout(n_v, n_g, n_p, n_snap, n_bins, hist_mode, off);
+size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode,
+                          int phase_uniform) {
+  size_t off[10];
+  return smem_layout(n_v, n_g, n_p, n_snap, n_bins, hist_mode, phase_uniform, off);
 }
 
 __device__ __forceinline__ int search_mass(const unsigned long long* Sq, const unsigned short* G,
@@ -112,7 +117,7 @@ __device__ __forceinline__ void launch_position(unsigned long long pk, unsigned 
 }
 
 template <bool DUMP, int HMODE>
-__global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restrict__ sets,
+__global__ void __launch_bounds__(256, 5) k_transport_f32(const SetDesc* __restrict__ sets,
                                                           int n_sets,
                                                           unsigned long long* __restrict__ set_ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -143,8 +148,8 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
       if (threadIdx.x < C_NCOUNT) s_cnt[threadIdx.x] = 0ull;
     }
     __syncthreads();
-    size_t off[9];
-    smem_layout(sd.n_v, sd.n_g, sd.n_p, sd.n_snap, sd.n_bins, HMODE, off);
+    size_t off[10];
+    smem_layout(sd.n_v, sd.n_g, sd.n_p, sd.n_snap, sd.n_bins, HMODE, sd.phase_uniform, off);
     SmemTables tb;
     tb.Sq = reinterpret_cast<const unsigned long long*>(smem + off[0]);
     tb.w = reinterpret_cast<const float*>(smem + off[1]);
@@ -154,7 +159,8 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
     tb.dthpi = reinterpret_cast<const float*>(smem + off[5]);
     tb.Gp = reinterpret_cast<const unsigned short*>(smem + off[6]);
     tb.ts = reinterpret_cast<const float*>(smem + off[7]);
-    tb.hist = HMODE == 2 ? reinterpret_cast<unsigned long long*>(smem + off[8]) : sd.hist;
+    tb.perm = reinterpret_cast<const unsigned short*>(smem + off[8]);
+    tb.hist = HMODE == 2 ? reinterpret_cast<unsigned long long*>(smem + off[9]) : sd.hist;
     {
       unsigned long long* Sq = reinterpret_cast<unsigned long long*>(smem + off[0]);
       for (int i = threadIdx.x; i <= sd.n_v; i += blockDim.x) Sq[i] = sd.Sq[i];
@@ -167,15 +173,21 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
       float* dthpi = reinterpret_cast<float*>(smem + off[5]);
       for (int i = threadIdx.x; i < sd.n_p; i += blockDim.x) {
         Cq[i] = sd.Cq[i];
-        thpi[i] = sd.thpi[i];
-        dthpi[i] = sd.dthpi[i];
+        if (!sd.phase_uniform) {
+          thpi[i] = sd.thpi[i];
+          dthpi[i] = sd.dthpi[i];
+        }
       }
       unsigned short* Gp = reinterpret_cast<unsigned short*>(smem + off[6]);
       for (int i = threadIdx.x; i <= (1 << kGuidePhaseLog); i += blockDim.x) Gp[i] = sd.Gp[i];
       float* ts = reinterpret_cast<float*>(smem + off[7]);
-      for (int i = threadIdx.x; i < sd.n_snap; i += blockDim.x) ts[i] = (float)sd.t_snap[i];
+      unsigned short* perm = reinterpret_cast<unsigned short*>(smem + off[8]);
+      for (int i = threadIdx.x; i < sd.n_snap; i += blockDim.x) {
+        ts[i] = (float)sd.t_snap[sd.n_snap + i];
+        perm[i] = (unsigned short)sd.t_snap[2 * sd.n_snap + i];
+      }
       if (HMODE == 2) {
-        unsigned long long* h = reinterpret_cast<unsigned long long*>(smem + off[8]);
+        unsigned long long* h = reinterpret_cast<unsigned long long*>(smem + off[9]);
         const int nh = sd.n_snap * hist_row(sd.n_bins);
         for (int i = threadIdx.x; i < nh; i += blockDim.x) h[i] = 0ull;
       }
@@ -296,14 +308,45 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
           const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
           const float fb = floorf((vapp - vcomp - sd.v_lo_f) * sd.inv_dbin_f);
           const int idx = fb < 0.0f ? 0 : (fb >= (float)n_bins ? n_bins + 1 : (int)fb + 1);
-          for (int s = 0; s < n_snap; ++s) {
+          // |a + t b|^2 <= R^2 holds on one interval of t: visit the ascending
+          // snapshot times inside it, plus one on each side, each re-tested
+          // exactly as below (the interval only narrows the search)
+          int s0 = 0, s1 = n_snap;
+          if (!sd.ap_all) {
+            const float A = fmaf(bx, bx, by * by);
+            const float B = 2.0f * fmaf(ax, bx, ay * by);
+            const float Cc = fmaf(ax, ax, fmaf(ay, ay, -sd.r_ap2_f));
+            const float disc = fmaf(B, B, -4.0f * A * Cc);
+            if (A > 0.0f) {
+              if (disc < 0.0f) {
+                s1 = 0;
+              } else {
+                const float q = sqrtf(disc), ia = 0.5f / A;
+                const float t1 = (-B - q) * ia, t2 = (-B + q) * ia;
+                int lo = 0, hi = n_snap;                   // first time >= t1
+                while (lo < hi) {
+                  const int mid = (lo + hi) >> 1;
+                  if (tb.ts[mid] < t1) lo = mid + 1; else hi = mid;
+                }
+                s0 = lo > 0 ? lo - 1 : 0;
+                hi = n_snap;                               // first time > t2
+                while (lo < hi) {
+                  const int mid = (lo + hi) >> 1;
+                  if (tb.ts[mid] <= t2) lo = mid + 1; else hi = mid;
+                }
+                s1 = lo < n_snap ? lo + 1 : n_snap;
+              }
+            }
+          }
+          for (int s = s0; s < s1; ++s) {
             const float t = tb.ts[s];
             const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
             if (sd.ap_all || fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
               // Eq. 19: tally the out-photon at its frequency shift
-              atomicAdd(&tb.hist[(size_t)s * row + idx], W);
-              atomicAdd(&tb.hist[(size_t)s * row + n_bins + 2], 1ull);
-              if (DUMP && s < 64) dmask |= 1ull << s;
+              const int sr = tb.perm[s];
+              atomicAdd(&tb.hist[(size_t)sr * row + idx], W);
+              atomicAdd(&tb.hist[(size_t)sr * row + n_bins + 2], 1ull);
+              if (DUMP && sr < 64) dmask |= 1ull << sr;
             }
           }
         }
@@ -341,7 +384,14 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
           } else {
             const unsigned m2 = r.z >> 8;
             const int i = search_phase(tb.Cq, tb.Gp, m2);
-            tpi = fmaf((float)(m2 - tb.Cq[i]) + 0.5f, tb.dthpi[i], tb.thpi[i]);
+            const unsigned c0 = tb.Cq[i];
+            if (sd.phase_uniform) {
+              // theta_i / pi = i / (n_p - 1); linear inside the CDF bin
+              const float frac = ((float)(m2 - c0) + 0.5f) * rcp_approx((float)(tb.Cq[i + 1] - c0));
+              tpi = ((float)i + frac) * sd.inv_nm1;
+            } else {
+              tpi = fmaf((float)(m2 - c0) + 0.5f, tb.dthpi[i], tb.thpi[i]);
+            }
             rphi = r.w;
             ++st_scat;
             if (DUMP) ++nsca;
