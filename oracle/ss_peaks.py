@@ -81,19 +81,28 @@ def ss_intensity(v, beta, tau0, v_fs, v_max=math.inf, prefactor=1.0):
 def ss_spectrum_bins(beta, tau0, v_fs, n_bins, v_lo, v_hi, v_max=math.inf, prefactor=1.0,
                      per_dv=False, n_gauss=16):
     """The single-scattering spectrum integrated over each of ``n_bins``
-    uniform bins of [v_lo, v_hi]: Gauss-Legendre quadrature of Eq. 28 on the
-    part of each bin inside the support [v_fs, v_max] (split there, because
-    the integrand jumps at both ends). With ``per_dv`` each bin is divided by
-    its width."""
+    uniform bins of [v_lo, v_hi]: composite Gauss-Legendre quadrature of
+    Eq. 28 on the part of each bin inside the support [v_fs, v_max] (split
+    there, because the integrand jumps at both ends). The integrand varies on
+    the scale v_fs / beta (exp(-tau0 Fbar) changes by O(1) per unit of
+    beta (v / v_fs - 1)), so each piece is cut into panels no wider than
+    v_fs / (8 beta). With ``per_dv`` each bin is divided by its width."""
     xg, wg = np.polynomial.legendre.leggauss(n_gauss)
     edges = v_lo + (v_hi - v_lo) * np.arange(n_bins + 1, dtype=np.float64) / n_bins
+    panel = v_fs / (8.0 * beta)
     out = np.zeros(n_bins)
     for b in range(n_bins):
         a, c = max(edges[b], v_fs), min(edges[b + 1], v_max)
         if c <= a:
             continue
-        v = 0.5 * (c - a) * xg + 0.5 * (c + a)
-        out[b] = 0.5 * (c - a) * np.sum(wg * ss_intensity(v, beta, tau0, v_fs, v_max, prefactor))
+        m = max(1, int(math.ceil((c - a) / panel)))
+        p = a + (c - a) * np.arange(m + 1, dtype=np.float64) / m
+        total = 0.0
+        for i in range(m):
+            v = 0.5 * (p[i + 1] - p[i]) * xg + 0.5 * (p[i + 1] + p[i])
+            total += 0.5 * (p[i + 1] - p[i]) * np.sum(
+                wg * ss_intensity(v, beta, tau0, v_fs, v_max, prefactor))
+        out[b] = total
     if per_dv:
         out /= (v_hi - v_lo) / n_bins
     return out

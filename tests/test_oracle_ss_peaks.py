@@ -61,6 +61,9 @@ def test_ss_bins_integrate_to_one_minus_exp(tau0):
     # untruncated law over a range that holds all but exp(-40) of the mass
     s = O.ss_spectrum_bins(beta, tau0, v_fs, 2000, 0.0, 2000.0 * 9.0, prefactor=1.0)
     assert s.sum() == pytest.approx(-math.expm1(-tau0), rel=1e-12)
+    # one bin holding the whole support (the integrand's peak is resolved)
+    one = O.ss_spectrum_bins(10.0, tau0, v_fs, 1, 0.0, 8000.0, v_max=v_max)
+    assert one[0] == pytest.approx(-math.expm1(-tau0), rel=1e-12)
     # per_dv divides by the bin width
     d = O.ss_spectrum_bins(beta, tau0, v_fs, 2000, 0.0, 18000.0, per_dv=True)
     assert np.allclose(d * 9.0, s, rtol=1e-14, atol=0)
