@@ -53,6 +53,8 @@ enum { PDV_PREC_FP32 = 0, PDV_PREC_FP64 = 1 };
 /* request flags */
 #define PDV_OUT_DEVICE 0x1u   /* out_* pointers are device pointers            */
 #define PDV_PER_DV     0x2u   /* spectrum divided by the bin width (per m/s)   */
+#define PDV_IN_DEVICE  0x4u   /* input arrays are device pointers (pdv_ss_spectrum,
+                                 pdv_extract_peaks)                            */
 
 /* Optional device allocator (NULL: cudaMallocAsync/cudaFreeAsync on the
  * context stream). Both callbacks are called from library threads. */
@@ -163,6 +165,8 @@ typedef struct {
   double last_transport_ms;        /* CUDA-event time of the last transport kernel */
   uint64_t last_events;            /* events of the last synchronous call */
   int transport_grid, transport_block;
+  double last_model_ms;            /* CUDA-event time of the last pdv_ss_spectrum /
+                                      pdv_extract_peaks main kernel      */
 } pdv_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -255,7 +259,81 @@ pdv_status pdv_poll(pdv_ctx* ctx, pdv_ticket ticket, uint32_t timeout_us);
 /* Cancel a queued or running request; its ticket then polls PDV_ECANCELLED. */
 pdv_status pdv_cancel(pdv_ctx* ctx, pdv_ticket ticket);
 
+/* ---------------------------------------------------------------- spectrum model
+ *
+ * Single-scattering spectrum (Section III.B, Eq. 22-28): light scattered once,
+ * straight back, by the particles at velocity v, attenuated on the way in and
+ * out by the mass above them. With f the mass density of Eq. 20 (unit area
+ * mass; renormalised over [v_fs, v_max] when v_max is finite) and Fbar(v) the
+ * mass fraction above v,
+ *     I(v) = prefactor * tau0 * f(v) * exp(-tau0 * Fbar(v)),
+ * which is Eq. 28 for the untruncated law (Fbar = f v_fs / beta). tau0 is the
+ * optical thickness of Eq. 27 (extinction by back-scattering and absorption,
+ * g_back K_ext of Eq. 25); prefactor holds the size factors of Eq. 28. */
+typedef struct {
+  double beta;                     /* velocity coefficient of Eq. 20, > 0            */
+  double tau0;                     /* optical thickness of Eq. 27, >= 0              */
+  double v_fs;                     /* free-surface velocity, m/s, > 0                */
+  double v_max;                    /* cut of the law, m/s; <= v_fs or inf: untruncated */
+  double prefactor;                /* constant factor of Eq. 28 (1 for the shape)    */
+} pdv_ss_set;
+
+/* Integrate the single-scattering spectrum of each set over n_bins uniform
+ * bins of [v_lo, v_hi] (out[set * n_bins + bin], FP64 output computed in FP32
+ * arithmetic from FP64 per-set constants; relative error about 1e-6 of the
+ * spectrum's largest bin). The bin integral is exact through the antiderivative
+ * prefactor * exp(-tau0 Fbar(v)). With PDV_PER_DV each bin is divided by its
+ * width. sets: host array, or device array with PDV_IN_DEVICE (those sets are
+ * checked on the device). out: host array, or device with PDV_OUT_DEVICE.
+ * Errors: PDV_EINVAL (n_sets < 0, n_bins < 1, v_hi <= v_lo, a set with
+ * beta <= 0, tau0 < 0 or v_fs <= 0: its bins are then NaN), PDV_ENOMEM,
+ * PDV_ECUDA. */
+pdv_status pdv_ss_spectrum(pdv_ctx* ctx, const pdv_ss_set* sets, int n_sets, int n_bins,
+                           double v_lo, double v_hi, uint32_t flags, double* out);
+
+/* ---------------------------------------------------------------- peak extraction
+ *
+ * Section III.C and Eq. 29-35: low-pass the binned spectrum with the real DFT
+ * (modes 0..k_c kept), find the largest smoothed value on the bin centres
+ * inside the search window, refine it by up to 8 Newton steps on the
+ * analytic first derivative (each kept within one bin of the grid maximum),
+ * and read off the relative curvature I''/I at the peak in x = v / v_fs:
+ *     beta = sqrt(-I''/I)  (Eq. 34),  tau0 = exp(beta (x_peak - 1))  (Eq. 31). */
+typedef struct {
+  int k_c;                         /* modes kept, 1 <= k_c < n_bins / 2              */
+  int reserved;
+  double x_min, x_max;             /* search window in v / v_fs (bin centres inside
+                                      it); -inf / +inf for the whole range          */
+} pdv_peak_opts;
+
+enum { PDV_PEAK_OK = 0, PDV_PEAK_NO_PEAK = 1, PDV_PEAK_NOT_MAX = 2, PDV_PEAK_EDGE = 3 };
+
+typedef struct {
+  double x_peak;                   /* peak position, v / v_fs                        */
+  double i_peak;                   /* smoothed spectrum at the peak                  */
+  double curvature;                /* I''/I at the peak, per (v / v_fs)^2            */
+  double beta, tau0;               /* Eq. 35; NaN unless status is PDV_PEAK_OK       */
+  int32_t status;                  /* PDV_PEAK_*                                     */
+  int32_t j_max;                   /* bin of the smoothed grid maximum (-1: none)    */
+} pdv_peak;
+
+/* Extract the main peak of n_spectra spectra of n_bins uniform bins over
+ * [v_lo, v_hi] (row-major [n_spectra][n_bins]). Arithmetic is FP32 with an
+ * FP64 twiddle table rounded to FP32; positions and the Eq. 35 inversion are
+ * FP64. Accuracy: about 1e-6 relative in x_peak, I''/I, beta and tau0 while the
+ * cut-off smooths (k_c well below n_bins / 2); as k_c nears n_bins / 2 the
+ * FP32 rounding of the input itself, amplified by up to pi^2 per bin in the
+ * second derivative, dominates the curvature.
+ * spectra: host array, or device with PDV_IN_DEVICE. out: host array,
+ * or device with PDV_OUT_DEVICE. Errors: PDV_EINVAL (n_spectra < 0,
+ * n_bins < 3 or > 8192, k_c outside [1, n_bins / 2), v_hi <= v_lo, v_fs <= 0),
+ * PDV_ENOMEM, PDV_ECUDA. */
+pdv_status pdv_extract_peaks(pdv_ctx* ctx, const double* spectra, int n_spectra, int n_bins,
+                             double v_lo, double v_hi, double v_fs, const pdv_peak_opts* opts,
+                             uint32_t flags, pdv_peak* out);
+
 #ifdef __cplusplus
 }
 #endif
+
 #endif /* PDV_H */

@@ -16,9 +16,12 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpdv.so")
-SOURCES = ["tables.cu", "transport.cu", "api.cu"]
+SOURCES = ["tables.cu", "transport.cu", "spectra.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+# Host code is compiled without FMA contraction (gcc contracts by default on
+# Arm), so host-side floating point gives the same bits on x86 and Arm.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+         "-I" + INCLUDE, "-I" + CSRC]
 
 
 def nvcc() -> str:

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "pdv_internal.cuh"
+#include "spectra.cuh"
 
 using namespace pdv;
 
@@ -70,6 +71,7 @@ struct pdv_ctx {
   std::mutex mu;                      // serialises synchronous calls on the stream
   std::atomic<unsigned long long> launches{0};
   double last_transport_ms = 0.0;
+  double last_model_ms = 0.0;
   unsigned long long last_events = 0;
   int last_grid = 0, last_block = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -240,6 +242,7 @@ extern "C" pdv_status pdv_get_stats(pdv_ctx* c, pdv_stats* out) {
   out->last_events = c->last_events;
   out->transport_grid = c->last_grid;
   out->transport_block = c->last_block;
+  out->last_model_ms = c->last_model_ms;
   return PDV_OK;
 }
 
@@ -1476,5 +1479,122 @@ extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request
   c->launches += 2;
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
+  return PDV_OK;
+}
+
+// ------------------------------------------------------------------ spectrum model
+// Single-scattering spectra (Eq. 22-28) and peak extraction (Eq. 29-35).
+static bool ss_set_valid(const pdv_ss_set& s) {
+  return s.beta > 0.0 && std::isfinite(s.beta) && s.tau0 >= 0.0 && std::isfinite(s.tau0) &&
+         s.v_fs > 0.0 && std::isfinite(s.v_fs) && std::isfinite(s.prefactor) && !std::isnan(s.v_max);
+}
+
+extern "C" pdv_status pdv_ss_spectrum(pdv_ctx* c, const pdv_ss_set* sets, int n_sets, int n_bins,
+                                      double v_lo, double v_hi, uint32_t flags, double* out) {
+  if (!c) return fail(PDV_EINVAL, "ctx is NULL");
+  if (n_sets < 0 || n_bins < 1) return fail(PDV_EINVAL, "n_sets must be >= 0 and n_bins >= 1");
+  if (!(v_hi > v_lo) || !std::isfinite(v_lo) || !std::isfinite(v_hi))
+    return fail(PDV_EINVAL, "need finite v_lo < v_hi");
+  if (flags & ~(PDV_IN_DEVICE | PDV_OUT_DEVICE | PDV_PER_DV)) return fail(PDV_EINVAL, "unknown flags");
+  if ((long long)n_sets * n_bins > (1LL << 36)) return fail(PDV_EINVAL, "n_sets * n_bins too large");
+  if (n_sets == 0) return PDV_OK;
+  if (!sets || !out) return fail(PDV_EINVAL, "sets and out must not be NULL");
+  const bool dev_in = (flags & PDV_IN_DEVICE) != 0, dev_out = (flags & PDV_OUT_DEVICE) != 0;
+  if (!dev_in)
+    for (int i = 0; i < n_sets; ++i)
+      if (!ss_set_valid(sets[i]))
+        return fail(PDV_EINVAL, "set %d: need beta > 0, tau0 >= 0, v_fs > 0, finite values", i);
+  CK(enter(c->device));
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t st = c->stream;
+  const size_t out_bytes = sizeof(double) * (size_t)n_sets * n_bins;
+  Layout L;
+  const size_t o_sets = dev_in ? 0 : L.add(sizeof(pdv_ss_set) * (size_t)n_sets);
+  const size_t o_const = L.add(ss_const_bytes() * (size_t)n_sets);
+  const size_t o_bad = L.add(sizeof(int));
+  const size_t o_out = dev_out ? 0 : L.add(out_bytes);
+  char* base = (char*)ctx_alloc(c, L.bytes, st);
+  if (!base) return fail(PDV_ENOMEM, "model allocation of %zu bytes failed", L.bytes);
+  struct Guard {
+    pdv_ctx* c; char* p; cudaStream_t st;
+    ~Guard() { ctx_free(c, p, st); cudaStreamSynchronize(st); }
+  } guard{c, base, st};
+  const pdv_ss_set* d_sets = dev_in ? sets : (const pdv_ss_set*)(base + o_sets);
+  double* d_out = dev_out ? out : (double*)(base + o_out);
+  if (!dev_in)
+    CK(cudaMemcpyAsync(base + o_sets, sets, sizeof(pdv_ss_set) * (size_t)n_sets, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(base + o_bad, 0, sizeof(int), st));
+  CK(launch_ss_const(d_sets, n_sets, n_bins, v_lo, v_hi, (flags & PDV_PER_DV) ? 1 : 0,
+                     base + o_const, (int*)(base + o_bad), st));
+  CK(cudaEventRecord(c->ev0, st));
+  CK(launch_ss_bins(base + o_const, n_sets, n_bins, d_out, st));
+  CK(cudaEventRecord(c->ev1, st));
+  c->launches += 2;
+  if (!dev_out) CK(cudaMemcpyAsync(out, d_out, out_bytes, cudaMemcpyDeviceToHost, st));
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, base + o_bad, sizeof bad, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) c->last_model_ms = ms;
+  cudaGetLastError();
+  if (bad) return fail(PDV_EINVAL, "%d device-resident sets are invalid (their bins are NaN)", bad);
+  return PDV_OK;
+}
+
+extern "C" pdv_status pdv_extract_peaks(pdv_ctx* c, const double* spectra, int n_spectra,
+                                        int n_bins, double v_lo, double v_hi, double v_fs,
+                                        const pdv_peak_opts* opts, uint32_t flags, pdv_peak* out) {
+  if (!c || !opts) return fail(PDV_EINVAL, "ctx and opts must not be NULL");
+  if (n_spectra < 0) return fail(PDV_EINVAL, "n_spectra must be >= 0");
+  if (n_bins < 3 || n_bins > kPeakMaxBins) return fail(PDV_EINVAL, "n_bins must be in [3, %d]", kPeakMaxBins);
+  if (opts->k_c < 1 || 2 * opts->k_c >= n_bins) return fail(PDV_EINVAL, "k_c must satisfy 1 <= k_c < n_bins / 2");
+  if (!(v_hi > v_lo) || !std::isfinite(v_lo) || !std::isfinite(v_hi) || !(v_fs > 0.0) || !std::isfinite(v_fs))
+    return fail(PDV_EINVAL, "need finite v_lo < v_hi and v_fs > 0");
+  if (std::isnan(opts->x_min) || std::isnan(opts->x_max)) return fail(PDV_EINVAL, "window bounds are NaN");
+  if (flags & ~(PDV_IN_DEVICE | PDV_OUT_DEVICE)) return fail(PDV_EINVAL, "unknown flags");
+  if (n_spectra == 0) return PDV_OK;
+  if (!spectra || !out) return fail(PDV_EINVAL, "spectra and out must not be NULL");
+  const bool dev_in = (flags & PDV_IN_DEVICE) != 0, dev_out = (flags & PDV_OUT_DEVICE) != 0;
+  // window: bin centres x_j = (v_lo + (j + 1/2) dv) / v_fs inside [x_min, x_max]
+  const double dv = (v_hi - v_lo) / n_bins;
+  int j_lo = n_bins, j_hi = -1;
+  for (int j = 0; j < n_bins; ++j) {
+    const double x = (v_lo + ((double)j + 0.5) * dv) / v_fs;
+    if (x >= opts->x_min && j_lo == n_bins) j_lo = j;
+    if (x <= opts->x_max) j_hi = j;
+  }
+  CK(enter(c->device));
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaStream_t st = c->stream;
+  int occ = 0;
+  CK(peak_occupancy(n_bins, opts->k_c, &occ));
+  if (occ < 1) return fail(PDV_EINVAL, "extraction tables do not fit in shared memory");
+  const int grid = (int)std::min<long long>((long long)occ * c->sm_count, n_spectra);
+  const size_t in_bytes = sizeof(double) * (size_t)n_spectra * n_bins;
+  const size_t out_bytes = sizeof(pdv_peak) * (size_t)n_spectra;
+  Layout L;
+  const size_t o_tw = L.add(sizeof(float2) * (size_t)n_bins);
+  const size_t o_in = dev_in ? 0 : L.add(in_bytes);
+  const size_t o_out = dev_out ? 0 : L.add(out_bytes);
+  char* base = (char*)ctx_alloc(c, L.bytes, st);
+  if (!base) return fail(PDV_ENOMEM, "extraction allocation of %zu bytes failed", L.bytes);
+  struct Guard {
+    pdv_ctx* c; char* p; cudaStream_t st;
+    ~Guard() { ctx_free(c, p, st); cudaStreamSynchronize(st); }
+  } guard{c, base, st};
+  const double* d_in = dev_in ? spectra : (const double*)(base + o_in);
+  pdv_peak* d_out = dev_out ? out : (pdv_peak*)(base + o_out);
+  if (!dev_in) CK(cudaMemcpyAsync(base + o_in, spectra, in_bytes, cudaMemcpyHostToDevice, st));
+  CK(launch_twiddles(n_bins, (float2*)(base + o_tw), st));
+  CK(cudaEventRecord(c->ev0, st));
+  CK(launch_extract(d_in, n_spectra, n_bins, opts->k_c, j_lo, j_hi, v_lo, dv, v_fs,
+                    (const float2*)(base + o_tw), d_out, grid, st));
+  CK(cudaEventRecord(c->ev1, st));
+  c->launches += 2;
+  if (!dev_out) CK(cudaMemcpyAsync(out, d_out, out_bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) c->last_model_ms = ms;
+  cudaGetLastError();
   return PDV_OK;
 }

@@ -24,7 +24,8 @@ from . import build as _build
 
 PDV_OK, PDV_EINVAL, PDV_ENOMEM, PDV_ECUDA, PDV_EAGAIN = 0, -1, -2, -3, -4
 PDV_ENOTREADY, PDV_ETIMEOUT, PDV_ECANCELLED = -5, -6, -7
-PDV_OUT_DEVICE, PDV_PER_DV = 0x1, 0x2
+PDV_OUT_DEVICE, PDV_PER_DV, PDV_IN_DEVICE = 0x1, 0x2, 0x4
+PDV_PEAK_OK, PDV_PEAK_NO_PEAK, PDV_PEAK_NOT_MAX, PDV_PEAK_EDGE = 0, 1, 2, 3
 PDV_PREC_FP32, PDV_PREC_FP64 = 0, 1
 STATUS_NAMES = {0: "PDV_OK", -1: "PDV_EINVAL", -2: "PDV_ENOMEM", -3: "PDV_ECUDA",
                 -4: "PDV_EAGAIN", -5: "PDV_ENOTREADY", -6: "PDV_ETIMEOUT", -7: "PDV_ECANCELLED"}
@@ -38,6 +39,7 @@ ABI_FUNCTIONS = [
     "pdv_create_cloud", "pdv_set_phase_table", "pdv_cloud_get_info", "pdv_destroy_cloud",
     "pdv_phase_hg", "pdv_mie_table", "pdv_simulate_spectrum", "pdv_simulate_batch",
     "pdv_autotune", "pdv_submit", "pdv_poll", "pdv_cancel", "pdv_simulate_spectrum_static",
+    "pdv_ss_spectrum", "pdv_extract_peaks",
 ]
 
 
@@ -103,7 +105,29 @@ class pdv_cloud_info(C.Structure):
 class pdv_stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("last_transport_ms", C.c_double),
                 ("last_events", C.c_uint64), ("transport_grid", C.c_int),
-                ("transport_block", C.c_int)]
+                ("transport_block", C.c_int), ("last_model_ms", C.c_double)]
+
+
+class pdv_ss_set(C.Structure):
+    _fields_ = [("beta", C.c_double), ("tau0", C.c_double), ("v_fs", C.c_double),
+                ("v_max", C.c_double), ("prefactor", C.c_double)]
+
+
+class pdv_peak_opts(C.Structure):
+    _fields_ = [("k_c", C.c_int), ("reserved", C.c_int), ("x_min", C.c_double),
+                ("x_max", C.c_double)]
+
+
+class pdv_peak(C.Structure):
+    _fields_ = [("x_peak", C.c_double), ("i_peak", C.c_double), ("curvature", C.c_double),
+                ("beta", C.c_double), ("tau0", C.c_double), ("status", C.c_int32),
+                ("j_max", C.c_int32)]
+
+
+SS_SET_DTYPE = np.dtype([(f, np.float64) for f, _ in pdv_ss_set._fields_])
+PEAK_DTYPE = np.dtype([("x_peak", np.float64), ("i_peak", np.float64), ("curvature", np.float64),
+                       ("beta", np.float64), ("tau0", np.float64), ("status", np.int32),
+                       ("j_max", np.int32)])
 
 
 # ------------------------------------------------------------------ library
@@ -143,6 +167,9 @@ def lib():
                 "pdv_submit": ([vp, C.POINTER(pdv_request), C.POINTER(C.c_uint64)], ip),
                 "pdv_poll": ([vp, C.c_uint64, C.c_uint32], ip),
                 "pdv_cancel": ([vp, C.c_uint64], ip),
+                "pdv_ss_spectrum": ([vp, vp, ip, ip, C.c_double, C.c_double, C.c_uint32, vp], ip),
+                "pdv_extract_peaks": ([vp, vp, ip, ip, C.c_double, C.c_double, C.c_double,
+                                       C.POINTER(pdv_peak_opts), C.c_uint32, vp], ip),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -273,7 +300,72 @@ def pdv_cancel(ctx: int, ticket: int):
     _check(lib().pdv_cancel(C.c_void_p(ctx), C.c_uint64(ticket)))
 
 
+def _addr(a):
+    """(address, on_device) of a contiguous numpy array or torch tensor."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), a.is_cuda
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data, False
+
+
+def pdv_ss_spectrum(ctx: int, sets, n_sets: int, n_bins: int, v_lo: float, v_hi: float,
+                    out, per_dv: bool = False):
+    """Single-scattering spectra (Eq. 28) of ``n_sets`` parameter sets integrated
+    over ``n_bins`` bins. ``sets``: SS_SET_DTYPE array, or a CUDA tensor of
+    float64 [n_sets, 5] (beta, tau0, v_fs, v_max, prefactor); ``out``: float64
+    [n_sets * n_bins] numpy array or CUDA tensor."""
+    ps, dev_in = _addr(sets)
+    po, dev_out = _addr(out)
+    flags = (PDV_IN_DEVICE if dev_in else 0) | (PDV_OUT_DEVICE if dev_out else 0) | \
+        (PDV_PER_DV if per_dv else 0)
+    _check(lib().pdv_ss_spectrum(C.c_void_p(ctx), C.c_void_p(ps), n_sets, n_bins, v_lo, v_hi,
+                                 flags, C.c_void_p(po)))
+
+
+def pdv_extract_peaks(ctx: int, spectra, n_spectra: int, n_bins: int, v_lo: float, v_hi: float,
+                      v_fs: float, k_c: int, x_min: float, x_max: float, out):
+    """Main-peak extraction (Eq. 29-35). ``spectra``: float64 [n_spectra, n_bins]
+    (numpy or CUDA tensor); ``out``: PEAK_DTYPE array, or a CUDA uint8 tensor of
+    n_spectra * 48 bytes."""
+    ps, dev_in = _addr(spectra)
+    po, dev_out = _addr(out)
+    flags = (PDV_IN_DEVICE if dev_in else 0) | (PDV_OUT_DEVICE if dev_out else 0)
+    o = pdv_peak_opts(k_c=k_c, reserved=0, x_min=x_min, x_max=x_max)
+    _check(lib().pdv_extract_peaks(C.c_void_p(ctx), C.c_void_p(ps), n_spectra, n_bins, v_lo,
+                                   v_hi, v_fs, C.byref(o), flags, C.c_void_p(po)))
+
+
 # ------------------------------------------------------------------ conveniences
+def ss_spectrum(ctx: "Context", params, n_bins: int, v_lo: float, v_hi: float,
+                per_dv: bool = False) -> np.ndarray:
+    """Host convenience: ``params`` is a sequence of dicts or tuples (beta,
+    tau0, v_fs, v_max, prefactor); returns float64 [n_sets, n_bins]."""
+    arr = np.zeros(len(params), dtype=SS_SET_DTYPE)
+    for i, p in enumerate(params):
+        if isinstance(p, dict):
+            arr[i] = (p["beta"], p["tau0"], p["v_fs"], p.get("v_max", 0.0), p.get("prefactor", 1.0))
+        else:
+            arr[i] = tuple(p) + (0.0, 1.0)[len(p) - 3:] if len(p) < 5 else tuple(p)
+    out = np.zeros(len(params) * n_bins)
+    pdv_ss_spectrum(ctx.handle, arr, len(params), n_bins, v_lo, v_hi, out, per_dv)
+    return out.reshape(len(params), n_bins)
+
+
+def extract_peaks(ctx: "Context", spectra, v_lo: float, v_hi: float, v_fs: float, k_c: int,
+                  x_min: float = -math.inf, x_max: float = math.inf) -> np.ndarray:
+    """Host convenience: spectra float64 [n_spectra, n_bins] -> PEAK_DTYPE array."""
+    s = np.ascontiguousarray(spectra, dtype=np.float64)
+    if s.ndim == 1:
+        s = s[None, :]
+    out = np.zeros(s.shape[0], dtype=PEAK_DTYPE)
+    pdv_extract_peaks(ctx.handle, s, s.shape[0], s.shape[1], v_lo, v_hi, v_fs, k_c, x_min, x_max,
+                      out)
+    return out
+
+
 class Context:
     """A libpdv context on one device (``stream``: a cudaStream_t as int)."""
 

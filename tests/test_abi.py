@@ -46,6 +46,8 @@ def test_ctypes_layouts_match_the_header(tmp_path):
         "pdv_counters": pdv.pdv_counters, "pdv_request": pdv.pdv_request,
         "pdv_tuning": pdv.pdv_tuning, "pdv_cloud_info": pdv.pdv_cloud_info,
         "pdv_stats": pdv.pdv_stats, "pdv_allocator": pdv.pdv_allocator,
+        "pdv_ss_set": pdv.pdv_ss_set, "pdv_peak_opts": pdv.pdv_peak_opts,
+        "pdv_peak": pdv.pdv_peak,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdv.h"', "int main(void){"]
     for sname, cls in structs.items():
@@ -66,6 +68,8 @@ def test_ctypes_layouts_match_the_header(tmp_path):
         for f, _ in cls._fields_:
             assert int(got["%s.%s" % (sname, f)]) == getattr(cls, f).offset, (sname, f)
     assert int(got["pdv_packet_record"]) == pdv.PACKET_DTYPE.itemsize
+    assert C.sizeof(pdv.pdv_peak) == pdv.PEAK_DTYPE.itemsize
+    assert C.sizeof(pdv.pdv_ss_set) == pdv.SS_SET_DTYPE.itemsize
 
 
 def test_status_codes_and_error_path_without_gpu():
