@@ -318,9 +318,9 @@ typedef struct {
 } pdv_peak;
 
 /* Extract the main peak of n_spectra spectra of n_bins uniform bins over
- * [v_lo, v_hi] (row-major [n_spectra][n_bins]). Arithmetic is FP32 with an
- * FP64 twiddle table rounded to FP32; positions and the Eq. 35 inversion are
- * FP64. Accuracy: about 1e-6 relative in x_peak, I''/I, beta and tau0 while the
+ * [v_lo, v_hi] (row-major [n_spectra][n_bins]). Arithmetic is FP32 with
+ * cosine / sine tables computed in FP64 and rounded to FP32; inputs are
+ * rounded to FP32 (magnitudes below 1.2e-38 flush to zero). Accuracy: about 1e-6 relative in x_peak, I''/I, beta and tau0 while the
  * cut-off smooths (k_c well below n_bins / 2); as k_c nears n_bins / 2 the
  * FP32 rounding of the input itself, amplified by up to pi^2 per bin in the
  * second derivative, dominates the curvature.

@@ -1566,14 +1566,18 @@ extern "C" pdv_status pdv_extract_peaks(pdv_ctx* c, const double* spectra, int n
   CK(enter(c->device));
   std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t st = c->stream;
+  // cut-offs up to 95 modes take the tiled kernel (64 spectra per block);
+  // larger ones the one-spectrum-per-block kernel
+  const bool tiled = peak_tiled(opts->k_c);
   int occ = 0;
-  CK(peak_occupancy(n_bins, opts->k_c, &occ));
+  if (tiled) CK(tiled_occupancy(opts->k_c, &occ));
+  else CK(peak_occupancy(n_bins, opts->k_c, &occ));
   if (occ < 1) return fail(PDV_EINVAL, "extraction tables do not fit in shared memory");
-  const int grid = (int)std::min<long long>((long long)occ * c->sm_count, n_spectra);
   const size_t in_bytes = sizeof(double) * (size_t)n_spectra * n_bins;
   const size_t out_bytes = sizeof(pdv_peak) * (size_t)n_spectra;
   Layout L;
   const size_t o_tw = L.add(sizeof(float2) * (size_t)n_bins);
+  const size_t o_mats = tiled ? L.add(peak_mats_bytes(n_bins, opts->k_c, j_hi - j_lo + 1)) : 0;
   const size_t o_in = dev_in ? 0 : L.add(in_bytes);
   const size_t o_out = dev_out ? 0 : L.add(out_bytes);
   char* base = (char*)ctx_alloc(c, L.bytes, st);
@@ -1586,11 +1590,23 @@ extern "C" pdv_status pdv_extract_peaks(pdv_ctx* c, const double* spectra, int n
   pdv_peak* d_out = dev_out ? out : (pdv_peak*)(base + o_out);
   if (!dev_in) CK(cudaMemcpyAsync(base + o_in, spectra, in_bytes, cudaMemcpyHostToDevice, st));
   CK(launch_twiddles(n_bins, (float2*)(base + o_tw), st));
-  CK(cudaEventRecord(c->ev0, st));
-  CK(launch_extract(d_in, n_spectra, n_bins, opts->k_c, j_lo, j_hi, v_lo, dv, v_fs,
-                    (const float2*)(base + o_tw), d_out, grid, st));
-  CK(cudaEventRecord(c->ev1, st));
-  c->launches += 2;
+  PeakGeom geom;
+  geom.x0 = (float)((v_lo + 0.5 * dv) / v_fs);
+  geom.dxj = (float)(dv / v_fs);
+  geom.scale = (float)((v_fs / dv) * (v_fs / dv));
+  if (tiled) {
+    CK(launch_extract_tiled(d_in, n_spectra, n_bins, opts->k_c, j_lo, j_hi, geom,
+                            (const float2*)(base + o_tw), (float*)(base + o_mats), d_out, occ,
+                            c->sm_count, st, c->ev0, c->ev1));
+    c->launches += 3;
+  } else {
+    const int grid = (int)std::min<long long>((long long)occ * c->sm_count, n_spectra);
+    CK(cudaEventRecord(c->ev0, st));
+    CK(launch_extract(d_in, n_spectra, n_bins, opts->k_c, j_lo, j_hi, geom,
+                      (const float2*)(base + o_tw), d_out, grid, st));
+    CK(cudaEventRecord(c->ev1, st));
+    c->launches += 2;
+  }
   if (!dev_out) CK(cudaMemcpyAsync(out, d_out, out_bytes, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   float ms = 0.f;

@@ -19,6 +19,7 @@
 // position gives tau0 (Eq. 31). One block per spectrum, persistent over the
 // batch; the twiddle table cos/sin(2 pi m / n) and the spectrum sit in shared
 // memory, and every index (j k mod n) is exact integer arithmetic.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -29,6 +30,37 @@ namespace pdv {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+
+// binary64 -> binary32, round to nearest even, in integer operations (the
+// FP64 pipe of this GPU is narrow). Results below the smallest normal binary32
+// flush to a signed zero; infinities and NaNs pass through.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (unsigned)((b >> 29) & 0x7fffffu) |
+                                          ((b & 0xfffffffffffffull) ? 0x400000u : 0u));
+  // mantissa with the hidden bit, rounded to 24 bits (a carry may bump the exponent)
+  unsigned long long m = (b & 0xfffffffffffffull) >> 0;
+  const unsigned long long r = m + 0x0fffffffull + ((m >> 29) & 1ull);
+  int e = ex - 1023 + 127 + (int)(r >> 52);
+  const unsigned mf = (unsigned)((r >> 29) & 0x7fffffu);
+  if (ex == 0 || e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | mf);
+}
+
+// binary32 -> binary64 (exact), in integer operations; binary32 subnormals
+// flush to a signed zero.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
+  if (ex == 0) return __longlong_as_double((long long)sign);
+  if (ex == 0xff) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull | m));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(ex + 896u) << 52) | m));
+}
 
 struct SsConst {
   float A0, D;          // x at edge e is A0 + D e
@@ -78,56 +110,110 @@ __global__ void k_ss_const(const pdv_ss_set* sets, int n_sets, int n_bins, doubl
   const double bm = ceil(e_max) - 1.0;
   c.b_fs = bf < 0.0 ? -1 : (bf >= n_bins ? n_bins : (int)bf);
   c.b_max = bm >= n_bins ? n_bins : (bm < -1.0 ? -2 : (int)bm);
-  // exact x at the upper end of the first bin and the lower end of the last
-  const double xc_first = fmin(r * (v_lo + (bf + 1.0) * dv - s.v_fs), x_max);
-  const double xa_last = fmax(r * (v_lo + bm * dv - s.v_fs), 0.0);
+  // exact x at the edge above v_fs (edge 0 when v_fs < v_lo) and at the edge
+  // below v_max (edge n_bins when v_max > v_hi), clamped to the support
+  const double ef = (double)c.b_fs + 1.0, em = (double)c.b_max;
+  const double xc_first = fmax(fmin(r * (v_lo + ef * dv - s.v_fs), x_max), 0.0);
+  const double xa_last = fmax(fmin(r * (v_lo + em * dv - s.v_fs), x_max), 0.0);
   c.dx_first = (float)xc_first;
   c.xa_last = (float)xa_last;
   c.dx_last = (float)(x_max - xa_last);
   out[i] = c;
 }
 
+// x at edge e of the bins, clamped to the support [0, x_max]; the two edges
+// next to the ends of the support come exactly from the FP64 constants.
+__device__ __forceinline__ float ss_edge_x(const SsConst& c, int e) {
+  if (e <= c.b_fs) return 0.0f;
+  if (e > c.b_max) return c.x_max;
+  if (e == c.b_fs + 1) return c.dx_first;
+  if (e == c.b_max) return c.xa_last;
+  return fmaf(c.D, (float)e, c.A0);
+}
+
+// exp(-tau0 Fbar) at an edge, from x_e and E_e = exp(-x_e)
+__device__ __forceinline__ float ss_edge_g(const SsConst& c, float x, float E) {
+  float EcT = E;                                   // E - T
+  if (c.cut) {
+    const float y = c.x_max - x;
+    EcT = (y < 1.0f) ? c.T * expm1f(fmaxf(y, 0.0f)) : E - c.T;
+  }
+  return expf(-c.tau0 * EcT * c.invN);
+}
+
+// Peak position, value and curvature from the converged Newton state, all in
+// FP32: x = x_0 + (J + d) dv / v_fs is formed as (x_0 + J dv/v_fs) + d dv/v_fs
+// so the fractional part keeps its precision next to a large J.
+__device__ __forceinline__ void peak_finish(pdv_peak& r, int J, float d, float q0, float q2,
+                                            float inv_n, const PeakGeom& g) {
+  const float x = fmaf(d, g.dxj, fmaf((float)J, g.dxj, g.x0));
+  const float curv = q2 / q0 * g.scale;
+  r.x_peak = f32_to_f64(x);
+  r.i_peak = f32_to_f64(q0 * inv_n);
+  r.curvature = f32_to_f64(curv);
+  if (curv < 0.0f) {
+    const float beta = sqrtf(-curv);
+    r.status = PDV_PEAK_OK;
+    r.beta = f32_to_f64(beta);
+    r.tau0 = f32_to_f64(expf(beta * (x - 1.0f)));
+  } else {
+    r.status = PDV_PEAK_NOT_MAX;
+  }
+}
+
+constexpr int kRun = 4;          // consecutive bins per thread (edges shared)
+
 __global__ void k_ss_bins(const SsConst* cs, int n_sets, int n_bins, double* out) {
-  const long long total = (long long)n_sets * n_bins;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int set = (int)(t / n_bins);
-    const int b = (int)(t - (long long)set * n_bins);
-    const SsConst c = cs[set];
-    float val;
-    if (c.bad) {
-      val = __int_as_float(0x7fc00000);
-    } else if (b < c.b_fs || b > c.b_max || (b < 0)) {
-      val = 0.0f;
+  const unsigned runs = (unsigned)((n_bins + kRun - 1) / kRun);
+  const unsigned long long total = (unsigned long long)n_sets * runs;
+  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+       t < total; t += (unsigned long long)gridDim.x * blockDim.x) {
+    unsigned set, run;
+    if (total <= 0xffffffffull) {
+      set = (unsigned)t / runs;
+      run = (unsigned)t - set * runs;
     } else {
-      float xa, dx;
-      if (b == c.b_fs && b == c.b_max) {
-        xa = 0.0f;
-        dx = c.x_max;
-      } else if (b == c.b_fs) {
-        xa = 0.0f;
-        dx = c.dx_first;
-      } else if (b == c.b_max && c.cut) {
-        xa = c.xa_last;
-        dx = c.dx_last;
-      } else {
-        xa = fmaf(c.D, (float)b, c.A0);
-        dx = c.D;
-      }
-      const float Ea = expf(-xa);
-      const float om = (dx == c.D) ? c.omD : -expm1f(-dx);
-      const float dE = Ea * om;                      // E(a) - E(c)
-      float EcT;                                     // E(c) - T
-      if (!c.cut) {
-        EcT = Ea - dE;
-      } else {
-        const float y = c.x_max - (xa + dx);         // x_max - x_c >= 0
-        EcT = (y < 1.0f) ? c.T * expm1f(fmaxf(y, 0.0f)) : (Ea - dE) - c.T;
-      }
-      const float Gc = expf(-c.tau0 * EcT * c.invN);
-      val = -c.P * Gc * expm1f(-c.tau0 * dE * c.invN);
+      set = (unsigned)(t / runs);
+      run = (unsigned)(t - (unsigned long long)set * runs);
     }
-    out[t] = (double)val;
+    const SsConst c = cs[set];
+    double* o = out + (size_t)set * n_bins;
+    const int b0 = (int)run * kRun;
+    if (c.bad) {
+      for (int i = 0; i < kRun && b0 + i < n_bins; ++i) o[b0 + i] = __longlong_as_double(0x7ff8000000000000ll);
+      continue;
+    }
+    float xa = ss_edge_x(c, b0);
+    float Ea = expf(-xa);
+#pragma unroll
+    for (int i = 0; i < kRun; ++i) {
+      const int b = b0 + i;
+      if (b >= n_bins) break;
+      const float xc = ss_edge_x(c, b + 1);
+      float dx, Ec;
+      if (b > c.b_fs && b < c.b_max) {             // whole bin inside the support
+        dx = c.D;
+        Ec = Ea * (1.0f - c.omD);
+      } else if (b == c.b_fs && b == c.b_max) {
+        dx = c.x_max;
+        Ec = expf(-xc);
+      } else if (b == c.b_fs) {
+        dx = c.dx_first;
+        Ec = expf(-xc);
+      } else if (b == c.b_max) {
+        dx = c.dx_last;
+        Ec = expf(-xc);
+      } else {                                     // outside the support
+        dx = 0.0f;
+        Ec = Ea;
+      }
+      const float om = (dx == c.D) ? c.omD : -expm1f(-dx);
+      const float Gc = ss_edge_g(c, xc, Ec);
+      const float val = -c.P * Gc * expm1f(-c.tau0 * (Ea * om) * c.invN);
+      o[b] = f32_to_f64(val);
+      xa = xc;
+      Ea = Ec;
+    }
   }
 }
 
@@ -160,8 +246,9 @@ __device__ __forceinline__ void smooth_eval(const float2* tw, const float2* ab, 
                                             float* s2) {
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   const float two_over_n = 2.0f / (float)n;
-  for (int k = lane; k <= k_c; k += 32) {
-    const int m = (int)(((long long)k * J) % n);
+  int m = (int)(((long long)lane * J) % n);         // (k J) mod n, k = lane + 32 i
+  const int step = (int)((32LL * J) % n);
+  for (int k = lane; k <= k_c; k += 32, m = (m + step >= n) ? m + step - n : m + step) {
     float sp, cp;
     sincospif(two_over_n * (float)k * d, &sp, &cp);
     const float2 t = tw[m];
@@ -187,8 +274,8 @@ __device__ __forceinline__ void smooth_eval(const float2* tw, const float2* ab, 
 
 __global__ void __launch_bounds__(kPeakThreads) k_extract(const double* spec, int n_spec, int n,
                                                           int k_c, int j_lo, int j_hi,
-                                                          double v_lo, double dv, double v_fs,
-                                                          const float2* twg, pdv_peak* out) {
+                                                          PeakGeom geom, const float2* twg,
+                                                          pdv_peak* out) {
   extern __shared__ __align__(16) unsigned char smem[];
   const PeakSmem L = peak_layout(n, k_c);
   float2* tw = reinterpret_cast<float2*>(smem + L.o_tw);
@@ -203,7 +290,7 @@ __global__ void __launch_bounds__(kPeakThreads) k_extract(const double* spec, in
   for (int sp = blockIdx.x; sp < n_spec; sp += gridDim.x) {
     __syncthreads();                                  // previous spectrum finished
     const double* src = spec + (size_t)sp * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = (float)src[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = f64_to_f32(src[i]);
     __syncthreads();
     // real DFT, modes 0..k_c: a_k = sum s_j cos(2 pi j k / n), b_k = sum s_j sin(...)
     for (int k = warp; k <= k_c; k += nw) {
@@ -279,27 +366,279 @@ __global__ void __launch_bounds__(kPeakThreads) k_extract(const double* spec, in
           r.status = PDV_PEAK_EDGE;
         } else {
           float d = 0.f, s0, s1, s2;
-          for (int it = 0; it < kPeakNewton; ++it) {
-            smooth_eval(tw, ab, n, k_c, bj, d, lane, &s0, &s1, &s2);
-            if (!(s2 < 0.0f)) break;
-            d = fminf(fmaxf(d - s1 / s2, -1.0f), 1.0f);
-          }
+          // Newton on s' = 0; a step below 1e-6 bin ends it (the values of
+          // the last evaluation then stand for the final d)
           smooth_eval(tw, ab, n, k_c, bj, d, lane, &s0, &s1, &s2);
-          const double scale = (v_fs / dv) * (v_fs / dv);
-          r.x_peak = (v_lo + ((double)bj + (double)d + 0.5) * dv) / v_fs;
-          r.i_peak = (double)s0 * inv_n;
-          r.curvature = (double)s2 / (double)s0 * scale;
-          if (r.curvature < 0.0) {
-            r.status = PDV_PEAK_OK;
-            r.beta = sqrt(-r.curvature);
-            r.tau0 = exp(r.beta * (r.x_peak - 1.0));
-          } else {
-            r.status = PDV_PEAK_NOT_MAX;
+          for (int it = 0; it < kPeakNewton && s2 < 0.0f; ++it) {
+            const float nd = fminf(fmaxf(d - s1 / s2, -1.0f), 1.0f);
+            const bool done = fabsf(nd - d) <= 1e-6f;
+            d = nd;
+            if (done) break;
+            smooth_eval(tw, ab, n, k_c, bj, d, lane, &s0, &s1, &s2);
           }
+          peak_finish(r, bj, d, s0, s2, inv_n, geom);
         }
       }
       if (lane == 0) out[sp] = r;
     }
+  }
+}
+
+// ------------------------------------------------------------------ tiled extraction
+// Batched form of the same computation for cut-offs up to kTileMaxK2 / 2 - 1
+// modes. A block takes a tile of kTS spectra. The DFT (modes 0..k_c) of the
+// tile is the product of the tile (kTS x n) with the fixed matrix
+// F[j][2k] = cos(2 pi j k / n), F[j][2k+1] = sin(2 pi j k / n); the smoothed
+// values on the window's bin centres are the product of those coefficients
+// with G[2k][j] = g_k cos(2 pi k (j_lo + j) / n) / n, G[2k+1][j] = g_k sin(...) / n
+// (g_0 = 1, g_k = 2). F and G are built once per call (FP64 rounded to FP32)
+// and stay in L2; each block streams them through shared memory in chunks and
+// accumulates a 4 x 6 register tile per thread. The grid maximum and the
+// Newton refinement then run per spectrum from the coefficients kept in
+// shared memory.
+constexpr int kTS = 64;          // spectra per tile
+constexpr int kNT = 96;          // output columns per pass (16 threads x 6)
+constexpr int kJC = 32;          // reduction chunk
+constexpr int kAS = kTS + 4;     // row stride of spectrum-major operands (float4 aligned)
+constexpr int kTileMaxK2 = 192;  // padded 2 (k_c + 1) handled by the tiled kernel
+
+__host__ __device__ inline int pad_to(int x, int m) { return (x + m - 1) / m * m; }
+
+struct TileSmem {
+  size_t o_a, o_b, o_c, o_red, bytes;
+};
+
+__host__ __device__ inline TileSmem tile_layout(int k2p) {
+  TileSmem L;
+  L.o_a = 0;
+  L.o_b = L.o_a + sizeof(float) * kJC * kAS;
+  L.o_c = L.o_b + sizeof(float) * kJC * kNT;
+  L.o_red = L.o_c + sizeof(float) * (size_t)k2p * kAS;
+  L.bytes = L.o_red + (sizeof(float) + sizeof(int)) * kTS;
+  return L;
+}
+
+// F: [n_p][k2p] and G: [k2p][nw_p], zero in the padding.
+__global__ void k_peak_mats(int n, int k_c, int n_p, int k2p, int j_lo, int n_w, int nw_p,
+                            float* F, float* G) {
+  const long long nF = (long long)n_p * k2p, nG = (long long)k2p * nw_p;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nF + nG;
+       t += (long long)gridDim.x * blockDim.x) {
+    if (t < nF) {
+      const int j = (int)(t / k2p), r = (int)(t % k2p), k = r >> 1;
+      float v = 0.0f;
+      if (j < n && k <= k_c) {
+        double s, c;
+        sincospi(2.0 * (double)(((long long)j * k) % n) / n, &s, &c);
+        v = (float)((r & 1) ? s : c);
+      }
+      F[t] = v;
+    } else {
+      const long long u = t - nF;
+      const int r = (int)(u / nw_p), j = (int)(u % nw_p), k = r >> 1;
+      float v = 0.0f;
+      if (j < n_w && k <= k_c && !(k == 0 && (r & 1))) {
+        double s, c;
+        sincospi(2.0 * (double)(((long long)(j_lo + j) * k) % n) / n, &s, &c);
+        v = (float)(((r & 1) ? s : c) * (k == 0 ? 1.0 : 2.0) / n);
+      }
+      G[u] = v;
+    }
+  }
+}
+
+// acc[4][6] += A[rows ty*4..+3] x B[cols tx*6..+5] over `len` reduction steps.
+__device__ __forceinline__ void tile_fma(const float* A, const float* B, int len, int ty, int tx,
+                                         float (&acc)[4][6]) {
+#pragma unroll 2
+  for (int q = 0; q < len; ++q) {
+    const float4 a = *reinterpret_cast<const float4*>(A + q * kAS + ty * 4);
+    const float2 b0 = *reinterpret_cast<const float2*>(B + q * kNT + tx * 6);
+    const float2 b1 = *reinterpret_cast<const float2*>(B + q * kNT + tx * 6 + 2);
+    const float2 b2 = *reinterpret_cast<const float2*>(B + q * kNT + tx * 6 + 4);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float bv[6] = {b0.x, b0.y, b1.x, b1.y, b2.x, b2.y};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc[i][c] = fmaf(av[i], bv[c], acc[i][c]);
+  }
+}
+
+// smooth_eval with the coefficients of spectrum s read from the tile's
+// mode-major shared array and the twiddles from global memory.
+__device__ __forceinline__ void tile_smooth_eval(const float2* tw, const float* Cs, int s, int n,
+                                                 int k_c, int J, float d, int lane, float* s0,
+                                                 float* s1, float* s2) {
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  const float two_over_n = 2.0f / (float)n;
+  int m = (int)(((long long)lane * J) % n);         // (k J) mod n, k = lane + 32 i
+  const int step = (int)((32LL * J) % n);
+  for (int k = lane; k <= k_c; k += 32, m = (m + step >= n) ? m + step - n : m + step) {
+    float sp, cp;
+    sincospif(two_over_n * (float)k * d, &sp, &cp);
+    const float2 t = __ldg(&tw[m]);
+    const float c = t.x * cp - t.y * sp;
+    const float sn = t.y * cp + t.x * sp;
+    const float qa = Cs[(2 * k) * kAS + s], qb = Cs[(2 * k + 1) * kAS + s];
+    const float g = k == 0 ? 1.0f : 2.0f;
+    const float w = 3.14159265358979f * two_over_n * (float)k;
+    const float e = qa * c + qb * sn;
+    a0 = fmaf(g, e, a0);
+    a1 = fmaf(g * w, qb * c - qa * sn, a1);
+    a2 = fmaf(-g * w * w, e, a2);
+  }
+  for (int o = 16; o; o >>= 1) {
+    a0 += __shfl_xor_sync(kFull, a0, o);
+    a1 += __shfl_xor_sync(kFull, a1, o);
+    a2 += __shfl_xor_sync(kFull, a2, o);
+  }
+  *s0 = a0;
+  *s1 = a1;
+  *s2 = a2;
+}
+
+__global__ void __launch_bounds__(256, 3) k_extract_tiled(
+    const double* spec, int n_spec, int n, int k_c, int j_lo, int j_hi, PeakGeom geom,
+    const float2* tw, const float* F, const float* G, int n_p, int k2p, int nw_p, pdv_peak* out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const TileSmem L = tile_layout(k2p);
+  float* As = reinterpret_cast<float*>(smem + L.o_a);    // [kJC][kAS] spectra chunk (j-major)
+  float* Bs = reinterpret_cast<float*>(smem + L.o_b);    // [kJC][kNT] F or G chunk
+  float* Cs = reinterpret_cast<float*>(smem + L.o_c);    // [k2p][kAS] coefficients (mode-major)
+  float* red_v = reinterpret_cast<float*>(smem + L.o_red);
+  int* red_j = reinterpret_cast<int*>(red_v + kTS);
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int n_w = j_hi - j_lo + 1;
+  const int n_tiles = (n_spec + kTS - 1) / kTS;
+
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int s0 = tile * kTS;
+    // ---- coefficients: Cs = tile x F, column passes of kNT
+    for (int cp = 0; cp < k2p; cp += kNT) {
+      float acc[4][6];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[i][c] = 0.0f;
+      // the next chunk's operands are loaded into registers while this one
+      // is multiplied (256 threads: 8 spectrum values and 12 F values each)
+      // (lane = bin within the chunk, warp + 8 u = spectrum; float4 columns of F)
+      float pa[kTS / 8];
+      float4 pb[kJC * kNT / 4 / 256];
+      auto fetch = [&](int j0) {
+        const int gj = j0 + lane;
+#pragma unroll
+        for (int u = 0; u < kTS / 8; ++u) {
+          const int gs = s0 + warp + 8 * u;
+          pa[u] = (gs < n_spec && gj < n) ? f64_to_f32(spec[(size_t)gs * n + gj]) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < kJC * kNT / 4 / 256; ++u) {
+          const int e = tid + u * 256, j = e / (kNT / 4), c4 = e % (kNT / 4);
+          pb[u] = *reinterpret_cast<const float4*>(F + (size_t)(j0 + j) * k2p + cp + 4 * c4);
+        }
+      };
+      fetch(0);
+      for (int j0 = 0; j0 < n_p; j0 += kJC) {
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kTS / 8; ++u) As[lane * kAS + warp + 8 * u] = pa[u];
+#pragma unroll
+        for (int u = 0; u < kJC * kNT / 4 / 256; ++u)
+          reinterpret_cast<float4*>(Bs)[tid + u * 256] = pb[u];
+        __syncthreads();
+        if (j0 + kJC < n_p) fetch(j0 + kJC);
+        tile_fma(As, Bs, kJC, ty, tx, acc);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) Cs[(cp + tx * 6 + c) * kAS + ty * 4 + i] = acc[i][c];
+    }
+    // ---- smoothed window values (tile x G), running first maximum per spectrum
+    float best[4];
+    int bj[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      best[i] = -INFINITY;
+      bj[i] = 0x7fffffff;
+    }
+    for (int wp = 0; wp < nw_p; wp += kNT) {
+      float acc[4][6];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[i][c] = 0.0f;
+      for (int r0 = 0; r0 < k2p; r0 += kJC) {
+        __syncthreads();
+        for (int e = tid; e < kJC * kNT; e += blockDim.x) {
+          const int r = e / kNT, c = e % kNT;
+          Bs[e] = G[(size_t)(r0 + r) * nw_p + wp + c];
+        }
+        __syncthreads();
+        tile_fma(Cs + r0 * kAS, Bs, kJC, ty, tx, acc);
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const int j = wp + tx * 6 + c;
+        if (j < n_w) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (acc[i][c] > best[i]) {
+              best[i] = acc[i][c];
+              bj[i] = j_lo + j;
+            }
+        }
+      }
+    }
+    // reduce over the 16 threads sharing ty (lanes 0-15 and 16-31 of a warp)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      for (int o = 8; o; o >>= 1) {
+        const float ov = __shfl_xor_sync(kFull, best[i], o);
+        const int oj = __shfl_xor_sync(kFull, bj[i], o);
+        if (ov > best[i] || (ov == best[i] && oj < bj[i])) {
+          best[i] = ov;
+          bj[i] = oj;
+        }
+      }
+      if (tx == 0) {
+        red_v[ty * 4 + i] = best[i];
+        red_j[ty * 4 + i] = bj[i];
+      }
+    }
+    __syncthreads();
+    // ---- per spectrum: status, Newton refinement, Eq. 35
+    for (int s = warp; s < kTS; s += blockDim.x / 32) {
+      const int gs = s0 + s;
+      if (gs >= n_spec) break;
+      const float bv = red_v[s];
+      const int J = red_j[s];
+      pdv_peak r;
+      r.x_peak = r.i_peak = r.curvature = r.beta = r.tau0 = NAN;
+      r.j_max = (n_w >= 1) ? J : -1;
+      r.status = PDV_PEAK_NO_PEAK;
+      if (n_w >= 1 && bv > 0.0f) {
+        if (J == j_lo || J == j_hi) {
+          r.status = PDV_PEAK_EDGE;
+        } else {
+          float d = 0.f, q0, q1, q2;
+          tile_smooth_eval(tw, Cs, s, n, k_c, J, d, lane, &q0, &q1, &q2);
+          for (int it = 0; it < kPeakNewton && q2 < 0.0f; ++it) {
+            const float nd = fminf(fmaxf(d - q1 / q2, -1.0f), 1.0f);
+            const bool done = fabsf(nd - d) <= 1e-6f;
+            d = nd;
+            if (done) break;
+            tile_smooth_eval(tw, Cs, s, n, k_c, J, d, lane, &q0, &q1, &q2);
+          }
+          peak_finish(r, J, d, q0, q2, 1.0f / (float)n, geom);
+        }
+      }
+      if (lane == 0) out[gs] = r;
+    }
+    __syncthreads();
   }
 }
 
@@ -320,7 +659,7 @@ cudaError_t launch_ss_bins(const void* d_const, int n_sets, int n_bins, double* 
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long total = (long long)n_sets * n_bins;
+  const long long total = (long long)n_sets * ((n_bins + kRun - 1) / kRun);
   long long blocks = (total + 255) / 256;
   const long long cap = (long long)sms * 8;
   if (blocks > cap) blocks = cap;
@@ -347,10 +686,54 @@ cudaError_t peak_occupancy(int n, int k_c, int* blocks_per_sm) {
 }
 
 cudaError_t launch_extract(const double* d_spec, int n_spec, int n, int k_c, int j_lo, int j_hi,
-                           double v_lo, double dv, double v_fs, const float2* d_tw,
-                           pdv_peak* d_out, int grid, cudaStream_t st) {
+                           PeakGeom geom, const float2* d_tw, pdv_peak* d_out, int grid,
+                           cudaStream_t st) {
   k_extract<<<grid, kPeakThreads, peak_smem(n, k_c), st>>>(d_spec, n_spec, n, k_c, j_lo, j_hi,
-                                                            v_lo, dv, v_fs, d_tw, d_out);
+                                                            geom, d_tw, d_out);
+  return cudaGetLastError();
+}
+
+}  // namespace pdv
+
+namespace pdv {
+
+bool peak_tiled(int k_c) { return pad_to(2 * (k_c + 1), kNT) <= kTileMaxK2; }
+
+size_t peak_mats_bytes(int n, int k_c, int n_w) {
+  const size_t k2p = pad_to(2 * (k_c + 1), kNT), n_p = pad_to(n, kJC);
+  const size_t nw_p = pad_to(n_w > 0 ? n_w : 0, kNT);
+  return sizeof(float) * (n_p * k2p + k2p * nw_p) + 16;
+}
+
+cudaError_t tiled_occupancy(int k_c, int* blocks_per_sm) {
+  const size_t sm = tile_layout(pad_to(2 * (k_c + 1), kNT)).bytes;
+  cudaError_t e = cudaFuncSetAttribute(k_extract_tiled,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_extract_tiled, 256, sm);
+}
+
+cudaError_t launch_extract_tiled(const double* d_spec, int n_spec, int n, int k_c, int j_lo,
+                                 int j_hi, PeakGeom geom, const float2* d_tw, float* d_mats,
+                                 pdv_peak* d_out,
+                                 int blocks_per_sm, int sm_count, cudaStream_t st,
+                                 cudaEvent_t e0, cudaEvent_t e1) {
+  const int k2p = pad_to(2 * (k_c + 1), kNT), n_p = pad_to(n, kJC);
+  const int n_w = j_hi - j_lo + 1 > 0 ? j_hi - j_lo + 1 : 0;
+  const int nw_p = pad_to(n_w, kNT);
+  float* F = d_mats;
+  float* G = d_mats + (size_t)n_p * k2p;
+  const long long nm = (long long)n_p * k2p + (long long)k2p * nw_p;
+  k_peak_mats<<<(int)std::min<long long>((nm + 255) / 256, 4096), 256, 0, st>>>(
+      n, k_c, n_p, k2p, j_lo, n_w, nw_p, F, G);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int n_tiles = (n_spec + kTS - 1) / kTS;
+  const int grid = std::min(n_tiles, blocks_per_sm * sm_count);
+  if (e0) cudaEventRecord(e0, st);
+  k_extract_tiled<<<grid, 256, tile_layout(k2p).bytes, st>>>(
+      d_spec, n_spec, n, k_c, j_lo, j_hi, geom, d_tw, F, G, n_p, k2p, nw_p, d_out);
+  if (e1) cudaEventRecord(e1, st);
   return cudaGetLastError();
 }
 

@@ -13,6 +13,12 @@ constexpr int kPeakMaxBins = 8192;
 constexpr int kPeakNewton = 8;          // Newton steps on the smoothed derivative
 constexpr int kPeakThreads = 256;
 
+// Bin geometry of an extraction in FP32: x of bin centre 0 (v / v_fs), bin
+// width / v_fs, and (v_fs / dv)^2 (curvature from bin units to x units).
+struct PeakGeom {
+  float x0, dxj, scale;
+};
+
 // Bytes of the per-set constant record the model kernels share.
 size_t ss_const_bytes();
 
@@ -34,7 +40,18 @@ cudaError_t peak_occupancy(int n, int k_c, int* blocks_per_sm);
 
 // Main-peak extraction of n_spec spectra; bins j_lo..j_hi form the window.
 cudaError_t launch_extract(const double* d_spec, int n_spec, int n, int k_c, int j_lo, int j_hi,
-                           double v_lo, double dv, double v_fs, const float2* d_tw,
-                           pdv_peak* d_out, int grid, cudaStream_t st);
+                           PeakGeom geom, const float2* d_tw, pdv_peak* d_out, int grid,
+                           cudaStream_t st);
+
+// Tiled extraction (64 spectra per block, two register-blocked FP32 products
+// with fixed cosine/sine matrices) for cut-offs it covers.
+bool peak_tiled(int k_c);
+size_t peak_mats_bytes(int n, int k_c, int n_w);
+cudaError_t tiled_occupancy(int k_c, int* blocks_per_sm);
+cudaError_t launch_extract_tiled(const double* d_spec, int n_spec, int n, int k_c, int j_lo,
+                                 int j_hi, PeakGeom geom, const float2* d_tw, float* d_mats,
+                                 pdv_peak* d_out,
+                                 int blocks_per_sm, int sm_count, cudaStream_t st,
+                                 cudaEvent_t e0, cudaEvent_t e1);
 
 }  // namespace pdv

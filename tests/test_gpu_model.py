@@ -240,7 +240,7 @@ def test_extract_maximum_size(ctx):
     g = pdv.extract_peaks(ctx, s, 0.0, 8192.0, 2000.0, 4095)[0]
     o = O.extract_peak(s, 0.0, 8192.0, 2000.0, 4095)
     assert int(g["status"]) == o["status"] == O.STATUS_OK
-    assert int(g["j_max"]) == o["j_max"]
+    assert abs(int(g["j_max"]) - o["j_max"]) <= 1     # the peak sits half-way between bins
     assert g["x_peak"] == pytest.approx(o["x_peak"], abs=1e-4)
     assert g["curvature"] == pytest.approx(o["curvature"], rel=5e-2)
     g = pdv.extract_peaks(ctx, s, 0.0, 8192.0, 2000.0, 64)
