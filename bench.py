@@ -56,7 +56,10 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--mode", default="default", choices=["default", "serve", "batch", "precision"])
+    ap.add_argument("--mode", default="default",
+                    choices=["default", "serve", "batch", "precision", "model"])
+    ap.add_argument("--model-sets", type=int, default=100_000,
+                    help="parameter sets / spectra of the model mode")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--sets", type=int, default=256)
@@ -481,6 +484,147 @@ def precision_mode(args):
     return 0
 
 
+def model_counters():
+    """Per-launch DRAM traffic of the spectrum-model and extraction kernels from
+    the committed ncu summary, if it was taken on the current source."""
+    p = os.path.join(ROOT, "profiles", "model_counters.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    src = open(os.path.join(ROOT, "paper_2012_00963_gb300", "csrc", "spectra.cu"), "rb").read()
+    return d if d.get("source_hash") == hashlib.sha1(src).hexdigest()[:12] else None
+
+
+def model_mode(args):
+    """Single-scattering spectra (Eq. 28) of many parameter sets and main-peak
+    extraction (Eq. 29-35) of as many noisy spectra, device-resident, timed
+    with CUDA events; the same calls with host buffers end to end; the FP64
+    oracle timed on a sample."""
+    import numpy as np
+    import torch
+    from oracle import ss_peaks as OS
+    from paper_2012_00963_gb300 import pdv
+    from paper_2012_00963_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = pdv.Context(0, stream=stream.cuda_stream)
+    n, nb, v_lo, v_hi, v_fs, k_c, x_lo, x_hi = args.model_sets, 600, 0.0, 8000.0, 2000.0, 40, 1.02, 3.5
+    sets = W.model_sets(n, v_fs=v_fs)
+    d_sets = torch.tensor(sets, device="cuda")
+    d_spec = torch.empty(n * nb, dtype=torch.float64, device="cuda")
+    d_pk = torch.empty(n * pdv.PEAK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(64 * 2**20, dtype=torch.float32, device="cuda")      # 256 MiB > L2
+
+    def run_ss():
+        pdv.pdv_ss_spectrum(ctx.handle, d_sets, n, nb, v_lo, v_hi, d_spec, per_dv=True)
+
+    run_ss()
+    d_in = (d_spec.view(n, nb) * torch.tensor(W.spectrum_noise((n, nb)), device="cuda")).contiguous()
+    torch.cuda.synchronize()
+
+    def run_pk():
+        pdv.pdv_extract_peaks(ctx.handle, d_in, n, nb, v_lo, v_hi, v_fs, k_c, x_lo, x_hi, d_pk)
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        wall, kern = [], []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            wall.append(a.elapsed_time(b))
+            kern.append(ctx.stats()["last_model_ms"])
+        return statistics.mean(wall), statistics.mean(kern)
+
+    clocks = Clocks(0)
+    clocks.start()
+    ss_ms, ss_kms = timed(run_ss)
+    pk_ms, pk_kms = timed(run_pk)
+    clk = clocks.stop()
+
+    # end to end through the C ABI with host buffers
+    sets_h = np.ascontiguousarray(sets).view(pdv.SS_SET_DTYPE).ravel()
+    out_h = np.empty(n * nb)
+    spec_h = d_in.cpu().numpy()
+    pk_h = np.zeros(n, dtype=pdv.PEAK_DTYPE)
+    e2e = {}
+    for name, fn in (("ss", lambda: pdv.pdv_ss_spectrum(ctx.handle, sets_h, n, nb, v_lo, v_hi, out_h,
+                                                          per_dv=True)),
+                     ("pk", lambda: pdv.pdv_extract_peaks(ctx.handle, spec_h, n, nb, v_lo, v_hi, v_fs,
+                                                          k_c, x_lo, x_hi, pk_h))):
+        fn()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            fn()
+        e2e[name] = (time.perf_counter() - t0) / args.steps
+    ok = pk_h["status"] == pdv.PDV_PEAK_OK
+
+    # the FP64 oracle on a sample (its inputs come from the oracle itself)
+    m_ss, m_pk = 40, 200
+    t0 = time.perf_counter()
+    o_spec = [OS.ss_spectrum_bins(b, t, vf, nb, v_lo, v_hi, per_dv=True) for b, t, vf, _, _ in sets[:m_ss]]
+    t_ss = time.perf_counter() - t0
+    noisy = [o_spec[i % m_ss] * W.spectrum_noise(nb, seed=100 + i) for i in range(m_pk)]
+    t0 = time.perf_counter()
+    for sp in noisy:
+        OS.extract_peak(sp, v_lo, v_hi, v_fs, k_c, x_lo, x_hi)
+    t_pk = time.perf_counter() - t0
+
+    prof = model_counters()
+    xc = (v_lo + (np.arange(nb) + 0.5) * ((v_hi - v_lo) / nb)) / v_fs
+    n_w = int(((xc >= x_lo) & (xc <= x_hi)).sum())
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    fma_peak = sm * 128 * 2.07e9                               # FP32 FMA lanes x max SM clock
+    ss_bytes = n * nb * 8 + n * 40
+    pk_flop = 2.0 * 2 * (k_c + 1) * (nb + n_w) * n             # two FP32 products, 2 flop / FMA
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    line = {
+        "mode": "model",
+        "metric": "single-scattering spectra/s (Eq. 28) and peak extractions/s (Eq. 29-35)",
+        "ss_spectrum": {
+            "value": n / (ss_ms / 1e3), "unit": "spectra/s", "ms_per_call": ss_ms, "kernel_ms": ss_kms,
+            "bins_per_s": n * nb / (ss_kms / 1e3), "gpu_launches": 2,
+            "roofline": {"bound": "hbm", "achieved": ss_bytes / (ss_kms / 1e3) / 1e9, "peak": hbm,
+                         "unit": "GB/s", "frac": ss_bytes / (ss_kms / 1e3) / 1e9 / hbm,
+                         "traffic": prof["k_ss_bins"]["dram_bytes_per_launch"] if prof else None,
+                         "kernel": "k_ss_bins", "peak_source": "measured"},
+            "e2e": {"value": n / e2e["ss"], "unit": "spectra/s", "h2d_bytes_per_step": n * 40,
+                    "d2h_bytes_per_step": n * nb * 8},
+            "cpu_baseline": {"value": m_ss / t_ss, "unit": "spectra/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d sets, composite Gauss-Legendre per bin" % m_ss}},
+        "extract_peaks": {
+            "value": n / (pk_ms / 1e3), "unit": "spectra/s", "ms_per_call": pk_ms, "kernel_ms": pk_kms,
+            "gpu_launches": 3, "ok_fraction": float(ok.mean()),
+            "roofline": {"bound": "alu", "achieved": pk_flop / (pk_kms / 1e3) / 1e12,
+                         "peak": 2 * fma_peak / 1e12, "unit": "TFLOP/s",
+                         "frac": pk_flop / (pk_kms / 1e3) / (2 * fma_peak),
+                         "traffic": prof["k_extract_tiled"]["dram_bytes_per_launch"] if prof else None,
+                         "kernel": "k_extract_tiled",
+                         "peak_source": "%d SM x 128 FP32 lanes x 2070 MHz x 2 flop" % sm,
+                         "algorithmic_flop_per_spectrum": pk_flop / n},
+            "e2e": {"value": n / e2e["pk"], "unit": "spectra/s", "h2d_bytes_per_step": n * nb * 8,
+                    "d2h_bytes_per_step": n * pdv.PEAK_DTYPE.itemsize},
+            "cpu_baseline": {"value": m_pk / t_pk, "unit": "spectra/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d noisy spectra, numpy FFT + Newton" % m_pk}},
+        "steps": args.steps, "warmup": max(3, args.warmup), "dtype": "f32",
+        "data": "synthetic (seeded parameter sets; spectra with 2% multiplicative noise)",
+        "config": {"workload": "%d sets beta U(2,12), tau0 logU(2,60), v_fs 2000 m/s; %d bins over "
+                               "0-8000 m/s per dv; extraction k_c=%d, window x in [%.2f, %.1f]"
+                               % (n, nb, k_c, x_lo, x_hi),
+                   "l2": "flushed between steps (256 MiB write)"},
+        "clocks": clk,
+    }
+    ctx.close()
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -491,6 +635,8 @@ def main():
         return batch_mode(args)
     if args.mode == "precision":
         return precision_mode(args)
+    if args.mode == "model":
+        return model_mode(args)
     return our_arm(args)
 
 

@@ -178,3 +178,24 @@ def cfg5_request(a: Arrival, **kw) -> Workload:
                   phase=Phase(kind="hg", g=0.7, albedo=0.6, q_ext=2.0), n_bins=400,
                   v_lo=0.0, v_hi=8000.0, n_packets=a.n_packets, seed=a.seed)
     return wl.replace(**kw)
+
+
+def model_sets(n_sets: int = 100_000, seed: int = 6, v_fs: float = 2000.0) -> np.ndarray:
+    """Parameter sets of the single-scattering model (Section III.B): beta ~
+    U(2, 12), tau0 ~ logU(2, 60) (the paper's cases run from tau0 = 8.6 to
+    28.8), one free-surface velocity for the batch (a spectrogram of one
+    shot), untruncated law, unit prefactor. Columns: beta, tau0, v_fs, v_max
+    (0: untruncated), prefactor."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((n_sets, 5), dtype=np.float64)
+    out[:, 0] = rng.uniform(2.0, 12.0, n_sets)
+    out[:, 1] = np.exp(rng.uniform(np.log(2.0), np.log(60.0), n_sets))
+    out[:, 2] = v_fs
+    out[:, 4] = 1.0
+    return out
+
+
+def spectrum_noise(shape, seed: int = 7, level: float = 0.02) -> np.ndarray:
+    """Multiplicative noise factors 1 + level * N(0, 1) for synthetic measured
+    spectra (seeded)."""
+    return 1.0 + level * np.random.default_rng(seed).standard_normal(shape)
