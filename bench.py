@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mode", default="default",
-                    choices=["default", "serve", "batch", "precision", "model"])
+                    choices=["default", "serve", "batch", "precision", "model", "extract-mc"])
     ap.add_argument("--model-sets", type=int, default=100_000,
                     help="parameter sets / spectra of the model mode")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
@@ -625,6 +625,59 @@ def model_mode(args):
     return 0
 
 
+def extract_mc_mode(args):
+    """The study of Figs. 13-15 (Section III.B): Monte Carlo spectra of the two
+    clouds quoted there (tau0 = 23.4 and 8.6) over a range of beta, each
+    reduced by the peak extraction; the single-scattering prediction (Eq. 31,
+    Eq. 34) beside them, and the extraction of the model spectrum itself."""
+    import numpy as np
+    import torch
+    from paper_2012_00963_gb300 import pdv
+    from paper_2012_00963_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = pdv.Context(0, stream=stream.cuda_stream)
+    betas = (4.0, 6.0, 8.0, 10.0, 12.0, 14.0)
+    rows = []
+    for ci, c in enumerate(W.FIG13_CLOUDS):
+        for beta in betas:
+            wl = W.fig13(ci, beta, n_packets=int(args.packets) if args.packets != 1e8 else 10_000_000)
+            cloud = pdv.Cloud(ctx, wl)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = pdv.simulate_spectrum(ctx, cloud, wl, per_dv=True)
+            b.record(stream)
+            b.synchronize()
+            info = cloud.info()
+            cloud.close()
+            span = (wl.v_hi - wl.v_lo) / wl.v_fs
+            k_c = min(int(math.ceil(1.25 * beta * span)), wl.n_bins // 2 - 1)
+            pk = pdv.extract_peaks(ctx, r["spectrum"][0], wl.v_lo, wl.v_hi, wl.v_fs, k_c, 1.02,
+                                   3.5)[0]
+            ss = pdv.ss_spectrum(ctx, [(beta, c["tau0_paper"], wl.v_fs, 0.0, 1.0)], wl.n_bins,
+                                 wl.v_lo, wl.v_hi, per_dv=True)
+            pk_ss = pdv.extract_peaks(ctx, ss[0], wl.v_lo, wl.v_hi, wl.v_fs, k_c, 1.02, 3.5)[0]
+            cnt = pdv.counters_dict(r["counters"][0])
+            rows.append({
+                "cloud": c["label"], "beta": beta, "tau0_paper": c["tau0_paper"],
+                "tau_ext_cloud": info["tau_tot"], "k_c": k_c, "mc_ms": a.elapsed_time(b),
+                "detected_fraction": cnt["w_detected"] / 2.0**32 / wl.n_packets,
+                "theory": {"x_peak": 1.0 + math.log(c["tau0_paper"]) / beta, "curvature": -beta * beta},
+                "mc": {"x_peak": float(pk["x_peak"]), "curvature": float(pk["curvature"]),
+                       "beta": float(pk["beta"]), "tau0": float(pk["tau0"]), "status": int(pk["status"])},
+                "ss_model": {"x_peak": float(pk_ss["x_peak"]), "beta": float(pk_ss["beta"]),
+                             "tau0": float(pk_ss["tau0"]), "status": int(pk_ss["status"])}})
+    ctx.close()
+    print(json.dumps({"mode": "extract-mc",
+                      "metric": "peak position and relative curvature of Monte Carlo spectra vs "
+                                "the single-scattering relations (Eq. 31, Eq. 34)",
+                      "config": {"workload": "Figs. 13-15 clouds: m0 20 / 10 mg/cm^2, d_m 1.5 / 2.0 "
+                                             "um, sigma 0.5, Mie 3+9i, every upward photon, 1200 "
+                                             "bins 0-8000 m/s, t = 1 us"},
+                      "rows": rows}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -637,6 +690,8 @@ def main():
         return precision_mode(args)
     if args.mode == "model":
         return model_mode(args)
+    if args.mode == "extract-mc":
+        return extract_mc_mode(args)
     return our_arm(args)
 
 

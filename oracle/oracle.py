@@ -204,6 +204,12 @@ def phase_table(wl):
     if ph.kind == "table":
         return (np.asarray(ph.theta, np.float64), np.asarray(ph.p, np.float64), ph.q_ext,
                 ph.albedo)
+    if ph.kind == "mie_iso":
+        # uniform scattering (Section II.D, second case of Fig. 6): the size-averaged
+        # Mie extinction and albedo of the cloud, with an isotropic phase function
+        theta, _, q_ext, albedo, _ = mie_table(ph.m, wl.wavelength, wl.d_m, wl.sigma_ln,
+                                               ph.n_angle, ph.n_size)
+        return theta, np.ones_like(theta), q_ext, albedo
     raise ValueError(ph.kind)
 
 

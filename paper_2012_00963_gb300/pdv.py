@@ -405,6 +405,11 @@ def phase_table(ctx: Context, wl):
         return th, p, q_ext, albedo
     if ph.kind == "table":
         return np.asarray(ph.theta, np.float64), np.asarray(ph.p, np.float64), ph.q_ext, ph.albedo
+    if ph.kind == "mie_iso":
+        # uniform scattering with the cloud's size-averaged Mie extinction and albedo
+        th, _, q_ext, albedo, _ = ctx.mie_table(ph.m, wl.wavelength * 1e9, wl.d_m * 1e6,
+                                                wl.sigma_ln, ph.n_size, ph.n_angle)
+        return th, np.ones_like(th), q_ext, albedo
     raise ValueError(ph.kind)
 
 

@@ -38,8 +38,9 @@ US = 1.0e-6
 @dataclass
 class Phase:
     """Phase-function choice: Henyey–Greenstein with given albedo and Q_ext,
-    size-averaged Mie for a complex index, or an explicit table."""
-    kind: str = "hg"                  # "hg" | "mie" | "table"
+    size-averaged Mie for a complex index, isotropic scattering with the Mie
+    extinction and albedo ("mie_iso"), or an explicit table."""
+    kind: str = "hg"                  # "hg" | "mie" | "mie_iso" | "table"
     g: float = 0.7
     albedo: float = 0.6
     q_ext: float = 2.0
@@ -199,3 +200,43 @@ def spectrum_noise(shape, seed: int = 7, level: float = 0.02) -> np.ndarray:
     """Multiplicative noise factors 1 + level * N(0, 1) for synthetic measured
     spectra (seeded)."""
     return 1.0 + level * np.random.default_rng(seed).standard_normal(shape)
+
+
+def fig6(case: int = 1, **kw) -> Workload:
+    """The comparison cloud of Section II.D (Fig. 6): tin, m0 = 10.7 mg/cm^2,
+    log-normal d_m = 1.5 um, sigma = 0.5, beta = 8, lambda = 1550 nm; case 1
+    scatters by the Mie phase function, case 2 isotropically (with the same
+    Mie extinction and albedo). Every upward photon is counted, as the paper
+    does; 600 bins over 0-8000 m/s, one snapshot at 1 us, 1e7 packets."""
+    if case not in (1, 2):
+        raise ValueError("case 1 (Mie) or 2 (uniform scattering)")
+    wl = Workload(
+        name="fig6-case%d" % case, m0=10.7 * MG_CM2, beta=8.0, v_max=0.0, d_m=1.5 * UM,
+        sigma_ln=0.5, phase=Phase(kind="mie" if case == 1 else "mie_iso", m=3.0 + 9.0j,
+                                  n_angle=1801, n_size=256),
+        r_ap=0.0, cone_alpha=math.pi / 2, t_snap=(1.0 * US,), n_bins=600, v_lo=0.0,
+        v_hi=8000.0, n_packets=10_000_000, seed=8)
+    return wl.replace(**kw)
+
+
+# The two clouds of Figs. 13-15 (Section III.B), quoted there with the
+# single-scattering optical thickness tau0 of Eq. 27.
+FIG13_CLOUDS = (
+    dict(label="tau0=23.4", tau0_paper=23.4, m0=20.0 * MG_CM2, d_m=1.5 * UM, sigma_ln=0.5),
+    dict(label="tau0=8.6", tau0_paper=8.6, m0=10.0 * MG_CM2, d_m=2.0 * UM, sigma_ln=0.5),
+)
+
+
+def fig13(cloud: int, beta: float, **kw) -> Workload:
+    """One Monte Carlo case of the peak-position / curvature study of
+    Figs. 13-15: cloud 0 (tau0 = 23.4) or 1 (tau0 = 8.6) at velocity
+    coefficient beta; Mie 3+9i at 1550 nm, every upward photon counted, 1200
+    bins over 0-8000 m/s, 1e7 packets (the paper's count)."""
+    c = FIG13_CLOUDS[cloud]
+    wl = Workload(
+        name="fig13-%s-beta%g" % (c["label"], beta), m0=c["m0"], beta=beta, v_max=0.0,
+        d_m=c["d_m"], sigma_ln=c["sigma_ln"],
+        phase=Phase(kind="mie", m=3.0 + 9.0j, n_angle=1801, n_size=256),
+        r_ap=0.0, cone_alpha=math.pi / 2, t_snap=(1.0 * US,), n_bins=1200, v_lo=0.0,
+        v_hi=8000.0, n_packets=10_000_000, seed=13)
+    return wl.replace(**kw)

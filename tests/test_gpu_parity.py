@@ -108,8 +108,11 @@ def test_cfg3_heavy_multiple_scattering(ctx, precision):
     dict(beta=10.0, v_max=0.0, v_fs=1500.0, m0=3 * W.MG_CM2, v_hi=4000.0),
     dict(max_events=2),
     dict(n_bins=1, v_lo=1000.0, v_hi=5000.0),
+    dict(phase=W.Phase(kind="mie_iso", m=3.0 + 9.0j, n_angle=1801, n_size=64), d_m=1.5e-6,
+         sigma_ln=0.5, m0=2 * W.MG_CM2, v_max=0.0),
+    dict(r_ap=0.0, cone_alpha=2.0),
 ], ids=["lambert", "specular", "R0", "albedo1", "albedo0", "tabulated", "steep", "maxev2",
-        "onebin"])
+        "onebin", "isotropic", "detect_all"])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_variants(ctx, precision, kw):
     wl = W.cfg1(n_packets=50000, **WIDE).replace(**kw)
