@@ -451,6 +451,78 @@ static void orc_trace_put(orc_vertex* tr, int max_v, int* nv, double x, double y
   ++*nv;
 }
 
+/* Step (6) at the top of the cloud: vacuum flight from (x, y, z_top) to the
+ * probe plane, the acceptance test, and the Eq. 19 tally. Returns detected. */
+static int orc_escape(const orc_setup* st, orc_tally* ta, double x, double y, double z_top,
+                      const double u[3], uint64_t W, double vapp, uint32_t order,
+                      orc_vertex* trace, int max_v, int* nv) {
+  const orc_problem* pb = st->pb;
+  x += u[0] * (pb->z_probe - z_top) / u[2];
+  y += u[1] * (pb->z_probe - z_top) / u[2];
+  orc_trace_put(trace, max_v, nv, x, y, pb->z_probe, 0.0, u, 3);
+  ta->cnt[ORC_ESCAPES] += 1;
+  int cone_ok = st->cone_all || u[2] >= st->cos_alpha;
+  int ap_ok = st->ap_all || (x * x + y * y <= pb->r_ap * pb->r_ap);
+  if (!(cone_ok && ap_ok)) {
+    ta->cnt[ORC_W_ESC_UNDETECTED] += W;
+    return 0;
+  }
+  /* Eq. 19: the spectrum counts out-photons by frequency shift */
+  ta->cnt[ORC_DETECTED] += 1;
+  double fb = floor((vapp - pb->v_lo) * ((double)pb->n_bins / (pb->v_hi - pb->v_lo)));
+  if (fb < 0.0) ta->cnt[ORC_W_UNDER] += W;
+  else if (fb >= (double)pb->n_bins) ta->cnt[ORC_W_OVER] += W;
+  else {
+    int b = (int)fb;
+    ta->hist[b] += W;
+    ta->cnt[ORC_W_DETECTED] += W;
+    if (ta->order) {
+      uint32_t o = order;
+      if (o >= ORC_NORDER) o = ORC_NORDER - 1;
+      ta->order[(size_t)o * pb->n_bins + b] += W;
+    }
+  }
+  return 1;
+}
+
+/* Step (6) at the free surface: reflectivity in 2^32 fixed point (rounded; the
+ * paper has none), the new direction by the surface law from r[1], r[2], and
+ * the Doppler shift of the moving wall. Returns 1 when no weight is left. */
+static int orc_surface(const orc_setup* st, orc_tally* ta, const uint32_t r[4], double u[3],
+                       uint64_t* Wp, double* vapp) {
+  const orc_problem* pb = st->pb;
+  uint64_t W = *Wp;
+  ta->cnt[ORC_EVENTS] += 1;
+  ta->cnt[ORC_SURFACE_HITS] += 1;
+  uint64_t Wn = st->R_q >= ((uint64_t)1 << 32) ? W : (W * st->R_q + ((uint64_t)1 << 31)) >> 32;
+  ta->cnt[ORC_W_ABS_SURFACE] += W - Wn;
+  *Wp = Wn;
+  double uz_old = u[2];
+  if (pb->surface_mode == 2) {
+    u[2] = -u[2];                      /* specular */
+  } else {
+    double ct, stt;
+    if (pb->surface_mode == 1) {       /* Lambertian: cos = sqrt(u) */
+      double a = orc_u01(r[1]);
+      ct = sqrt(a);
+      stt = sqrt(1.0 - a);
+    } else {
+      /* the paper's ideal diffuse reflection (Section II.B): polar angle
+       * uniform; measured from +z it is uniform in [0, pi/2) */
+      double th = 0.5 * ORC_PI * orc_u01(r[1]);
+      ct = cos(th);
+      stt = sin(th);
+    }
+    double ph = 2.0 * ORC_PI * orc_u01(r[2]);
+    u[0] = stt * cos(ph);
+    u[1] = stt * sin(ph);
+    u[2] = ct;
+  }
+  /* the moving wall shifts the frequency like a particle at v_fs */
+  *vapp += 0.5 * (u[2] - uz_old) * pb->v_fs;
+  return Wn == 0;
+}
+
 static void orc_transport(const orc_setup* st, uint64_t pk, double t, orc_tally* ta,
                           orc_result* res, orc_vertex* trace, int max_v) {
   const orc_problem* pb = st->pb;
@@ -496,37 +568,12 @@ static void orc_transport(const orc_setup* st, uint64_t pk, double t, orc_tally*
     } else {
       Tn = T + tau * u[2];
       if (Tn >= st->tau_tot) {
-        /* Step (6): leaves through the top; vacuum flight to the probe plane */
+        /* Step (6): leaves through the top */
         double z_top = st->v_top * t;
         x += u[0] * (z_top - z) / u[2];
         y += u[1] * (z_top - z) / u[2];
-        x += u[0] * (pb->z_probe - z_top) / u[2];
-        y += u[1] * (pb->z_probe - z_top) / u[2];
-        orc_trace_put(trace, max_v, &nv, x, y, pb->z_probe, 0.0, u, 3);
+        detected = orc_escape(st, ta, x, y, z_top, u, W, vapp, nsca + nsurf, trace, max_v, &nv);
         fate = ORC_FATE_ESCAPED;
-        ta->cnt[ORC_ESCAPES] += 1;
-        int cone_ok = st->cone_all || u[2] >= st->cos_alpha;
-        int ap_ok = st->ap_all || (x * x + y * y <= pb->r_ap * pb->r_ap);
-        if (cone_ok && ap_ok) {
-          /* Eq. 19: the spectrum counts out-photons by frequency shift */
-          detected = 1;
-          ta->cnt[ORC_DETECTED] += 1;
-          double fb = floor((vapp - pb->v_lo) * ((double)pb->n_bins / (pb->v_hi - pb->v_lo)));
-          if (fb < 0.0) ta->cnt[ORC_W_UNDER] += W;
-          else if (fb >= (double)pb->n_bins) ta->cnt[ORC_W_OVER] += W;
-          else {
-            int b = (int)fb;
-            ta->hist[b] += W;
-            ta->cnt[ORC_W_DETECTED] += W;
-            if (ta->order) {
-              uint32_t o = nsca + nsurf;
-              if (o >= ORC_NORDER) o = ORC_NORDER - 1;
-              ta->order[(size_t)o * pb->n_bins + b] += W;
-            }
-          }
-        } else {
-          ta->cnt[ORC_W_ESC_UNDETECTED] += W;
-        }
         break;
       } else if (Tn <= 0.0) {
         /* Step (6): reaches the free surface z_fs = v_fs t */
@@ -537,41 +584,12 @@ static void orc_transport(const orc_setup* st, uint64_t pk, double t, orc_tally*
         vcur = pb->v_fs;
         ++nev;
         ++nsurf;
-        ta->cnt[ORC_EVENTS] += 1;
-        ta->cnt[ORC_SURFACE_HITS] += 1;
-        /* reflectivity R in 2^32 fixed point, rounded (not in the paper) */
-        uint64_t Wn = st->R_q >= ((uint64_t)1 << 32) ? W
-                                                      : (W * st->R_q + ((uint64_t)1 << 31)) >> 32;
-        ta->cnt[ORC_W_ABS_SURFACE] += W - Wn;
-        W = Wn;
-        double uz_old = u[2];
-        if (pb->surface_mode == 2) {
-          u[2] = -u[2];                      /* specular */
-        } else {
-          double ct, stt;
-          if (pb->surface_mode == 1) {       /* Lambertian: cos = sqrt(u) */
-            double a = orc_u01(r[1]);
-            ct = sqrt(a);
-            stt = sqrt(1.0 - a);
-          } else {
-            /* the paper's ideal diffuse reflection (Section II.B): polar angle
-             * uniform; measured from +z it is uniform in [0, pi/2) */
-            double th = 0.5 * ORC_PI * orc_u01(r[1]);
-            ct = cos(th);
-            stt = sin(th);
-          }
-          double ph = 2.0 * ORC_PI * orc_u01(r[2]);
-          u[0] = stt * cos(ph);
-          u[1] = stt * sin(ph);
-          u[2] = ct;
-        }
-        /* the moving wall shifts the frequency like a particle at v_fs */
-        vapp += 0.5 * (u[2] - uz_old) * pb->v_fs;
-        orc_trace_put(trace, max_v, &nv, x, y, z, pb->v_fs, u, 2);
-        if (W == 0) {
+        if (orc_surface(st, ta, r, u, &W, &vapp)) {
+          orc_trace_put(trace, max_v, &nv, x, y, z, pb->v_fs, u, 2);
           fate = ORC_FATE_ABS_SURFACE;
           break;
         }
+        orc_trace_put(trace, max_v, &nv, x, y, z, pb->v_fs, u, 2);
       } else {
         vn = orc_inverse(st, Tn / st->tau_tot);
         double zn = vn * t;
