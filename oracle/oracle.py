@@ -62,7 +62,7 @@ class _Problem(C.Structure):
         ("n_snap", C.c_int), ("t_snap", C.POINTER(C.c_double)),
         ("n_bins", C.c_int), ("v_lo", C.c_double), ("v_hi", C.c_double),
         ("packet_begin", C.c_uint64), ("n_packets", C.c_uint64), ("seed", C.c_uint64),
-        ("stream_id", C.c_uint32), ("max_events", C.c_uint32),
+        ("stream_id", C.c_uint32), ("max_events", C.c_uint32), ("n_layers", C.c_uint32),
     ]
 
 
@@ -108,6 +108,8 @@ def lib():
             L.orc_phase_sample.restype = C.c_double
             L.orc_rotate.argtypes = [dp, C.c_double, C.c_double, C.c_double, C.c_double]
             L.orc_rotate.restype = None
+            L.orc_phase_ar_cos.argtypes = [C.POINTER(_Problem), C.c_uint64, C.c_uint32]
+            L.orc_phase_ar_cos.restype = C.c_double
             L.orc_simulate.argtypes = [C.POINTER(_Problem), C.c_int, u64p, u64p, u64p, C.c_void_p,
                                        C.c_int, C.c_int, C.c_void_p]
             L.orc_simulate.restype = C.c_int
@@ -190,6 +192,15 @@ def rotate(u, cos_t, sin_t, cos_p, sin_p):
     return v
 
 
+def phase_ar_cos(wl, packets, step=1, table=None):
+    """cos(theta) from the layer-stepping scheme's acceptance-rejection for each
+    packet index in `packets` at the given step (seed, stream and phase table
+    of the workload)."""
+    prob = Problem(wl, table=table)
+    return np.array([lib().orc_phase_ar_cos(C.byref(prob.pb), int(k), int(step))
+                     for k in packets])
+
+
 # ---------------------------------------------------------------- problems
 def phase_table(wl):
     """The oracle's own phase table, albedo and Q_ext for a workload."""
@@ -258,6 +269,7 @@ class Problem:
         pb.seed = wl.seed
         pb.stream_id = wl.stream_id
         pb.max_events = wl.max_events
+        pb.n_layers = getattr(wl, "n_layers", 0)
         self.pb = pb
         self.q_ext = q_ext
         self.albedo = albedo

@@ -77,6 +77,7 @@ typedef struct {
   uint64_t R_q;          /* round(R 2^32) */
   uint32_t* cq;          /* phase CDF, 2^24 scale */
   uint32_t max_events;
+  double p_max;          /* largest tabulated p(theta) (acceptance-rejection) */
 } orc_setup;
 
 static int orc_setup_profile(orc_setup* st, const orc_problem* pb) {
@@ -639,6 +640,162 @@ static void orc_transport(const orc_setup* st, uint64_t pk, double t, orc_tally*
 }
 
 /* ------------------------------------------------------------------------ */
+/* The paper's literal scheme (Section II.B steps (2)-(6)): synchronous      */
+/* steps of H / n_layers, a Bernoulli pass per layer with the layer's        */
+/* Beer-Lambert probability (Eq. 7, Eq. 10), and the polar angle by           */
+/* acceptance-rejection (step (4)).                                           */
+/* ------------------------------------------------------------------------ */
+
+/* p(theta) linear between the tabulated nodes (Eq. 13 as tabulated). */
+static double orc_phase_p(const orc_problem* pb, double th) {
+  int lo = 0, hi = pb->n_phase - 2;
+  while (lo < hi) {                       /* largest i <= n-2 with theta_i <= th */
+    int mid = (lo + hi + 1) / 2;
+    if (pb->theta[mid] <= th) lo = mid; else hi = mid - 1;
+  }
+  double a = pb->theta[lo], b = pb->theta[lo + 1];
+  double f = (th - a) / (b - a);
+  if (f < 0.0) f = 0.0;
+  if (f > 1.0) f = 1.0;
+  return pb->p[lo] + (pb->p[lo + 1] - pb->p[lo]) * f;
+}
+
+/* Acceptance-rejection for the scattering angle: a direction uniform over the
+ * sphere (cos theta uniform in (-1, 1)) is accepted with probability
+ * p(theta) / max p. The draws come from a second Philox key, counter
+ * (packet, step, attempt pair, -): words (r0, r1) and (r2, r3) are two
+ * attempts. Returns cos theta. */
+static double orc_ar_cos(const orc_setup* st, uint64_t pk, uint32_t step) {
+  const orc_problem* pb = st->pb;
+  uint32_t key[2] = {(uint32_t)pb->seed ^ 0xA4093822u, (uint32_t)(pb->seed >> 32) ^ pb->stream_id};
+  uint32_t ctr[4] = {(uint32_t)pk, (uint32_t)(pk >> 32), step, 0u};
+  uint32_t r[4];
+  double mu = 0.0;
+  for (uint32_t a = 0; a < (1u << 24); ++a) {
+    ctr[3] = a;
+    orc_philox4x32_10(ctr, key, r);
+    for (int h = 0; h < 2; ++h) {
+      mu = 2.0 * orc_u01(r[2 * h]) - 1.0;
+      if (orc_u01(r[2 * h + 1]) * st->p_max < orc_phase_p(pb, acos(mu))) return mu;
+    }
+  }
+  return mu;     /* 2^25 rejections in a row: keep the last proposal */
+}
+
+double orc_phase_ar_cos(const orc_problem* pb, uint64_t pk, uint32_t step) {
+  orc_setup st;
+  memset(&st, 0, sizeof st);
+  st.pb = pb;
+  for (int i = 0; i < pb->n_phase; ++i)
+    if (pb->p[i] > st.p_max) st.p_max = pb->p[i];
+  return orc_ar_cos(&st, pk, step);
+}
+
+static void orc_transport_stepped(const orc_setup* st, uint64_t pk, double t, orc_tally* ta,
+                                  orc_result* res, orc_vertex* trace, int max_v) {
+  const orc_problem* pb = st->pb;
+  uint32_t key[2] = {(uint32_t)pb->seed, (uint32_t)(pb->seed >> 32)};
+  uint32_t ctr[4] = {(uint32_t)pk, (uint32_t)(pk >> 32), 0u, pb->stream_id};
+  uint32_t r[4];
+  int nv = 0;
+
+  /* Step (1): launch as in the exact scheme (event 0) */
+  orc_philox4x32_10(ctr, key, r);
+  double rad = pb->r_beam * sqrt(orc_u01(r[0]));
+  double psi = 2.0 * ORC_PI * orc_u01(r[1]);
+  double x = rad * cos(psi), y = rad * sin(psi);
+  double u[3] = {0.0, 0.0, -1.0};
+  orc_trace_put(trace, max_v, &nv, x, y, pb->z_probe, 0.0, u, 0);
+  const double z_fs = pb->v_fs * t, z_top = st->v_top * t;
+  /* Step (2): every step is a thousandth (1 / n_layers) of the ejecta height */
+  const double h = (z_top - z_fs) / (double)pb->n_layers;
+  double z = z_top;
+  double vapp = 0.0;
+  uint64_t W = (uint64_t)1 << 32;
+  uint32_t nev = 0, nsca = 0, nsurf = 0, fate = 0;
+  int detected = 0;
+
+  for (uint32_t k = 1; fate == 0; ++k) {
+    ctr[2] = k;
+    orc_philox4x32_10(ctr, key, r);
+    /* Step (3): one step along u; the optical depth of the layer crossed is
+     * the mass it holds (Eq. 10 per layer), over |u_z| for a slant path */
+    double zn = z + u[2] * h;
+    double zc = zn < z_fs ? z_fs : (zn > z_top ? z_top : zn);
+    double dtau;
+    if (fabs(u[2]) < 1e-9)
+      dtau = st->tau_tot * orc_density(st, z / t) * h / t;
+    else
+      dtau = st->tau_tot * fabs(orc_cdf(st, zc / t) - orc_cdf(st, z / t)) / fabs(u[2]);
+    if (orc_u01(r[0]) < exp(-dtau)) {
+      /* passes the layer: step (5) moves it; step (6) checks the boundaries */
+      if (zn >= z_top) {
+        x += u[0] * (z_top - z) / u[2];
+        y += u[1] * (z_top - z) / u[2];
+        detected = orc_escape(st, ta, x, y, z_top, u, W, vapp, nsca + nsurf, trace, max_v, &nv);
+        fate = ORC_FATE_ESCAPED;
+        break;
+      } else if (zn <= z_fs) {
+        x += u[0] * (z_fs - z) / u[2];
+        y += u[1] * (z_fs - z) / u[2];
+        z = z_fs;
+        ++nev;
+        ++nsurf;
+        int dead = orc_surface(st, ta, r, u, &W, &vapp);
+        orc_trace_put(trace, max_v, &nv, x, y, z, pb->v_fs, u, 2);
+        if (dead) {
+          fate = ORC_FATE_ABS_SURFACE;
+          break;
+        }
+      } else {
+        x += u[0] * h;
+        y += u[1] * h;
+        z = zn;
+      }
+    } else {
+      /* stopped in the layer: the interaction is at the end of the step
+       * (inside the cloud); step (4) decides scatter or absorption (Eq. 11) */
+      double len = fabs(u[2]) < 1e-9 ? h : (zc - z) / u[2];
+      x += u[0] * len;
+      y += u[1] * len;
+      z = zc;
+      double vn = z / t;
+      ++nev;
+      ta->cnt[ORC_EVENTS] += 1;
+      if (orc_m24(r[1]) < st->omega_q) {
+        double ct = orc_ar_cos(st, pk, k);
+        double ph = 2.0 * ORC_PI * orc_u01(r[3]);              /* Eq. 15 */
+        double uz_old = u[2];
+        orc_rotate(u, ct, sqrt(1.0 - ct * ct), cos(ph), sin(ph));   /* Eq. 16-17 */
+        vapp += 0.5 * (u[2] - uz_old) * vn;                    /* Eq. 4, 18 */
+        ++nsca;
+        ta->cnt[ORC_SCATTERS] += 1;
+        orc_trace_put(trace, max_v, &nv, x, y, z, vn, u, 1);
+      } else {
+        ta->cnt[ORC_W_ABS_PARTICLE] += W;
+        orc_trace_put(trace, max_v, &nv, x, y, z, vn, u, 4);
+        fate = ORC_FATE_ABS_PARTICLE;
+        break;
+      }
+    }
+    if (k >= st->max_events) {
+      /* the step limit of this scheme (the paper is silent) */
+      ta->cnt[ORC_W_TRUNCATED] += W;
+      ta->cnt[ORC_TRUNCATED] += 1;
+      fate = ORC_FATE_TRUNCATED;
+      break;
+    }
+  }
+  res->n_events = nev;
+  res->n_scatters = nsca;
+  res->n_surface = nsurf;
+  res->fate = fate;
+  res->weight = W;
+  res->v_app = vapp;
+  res->detected = detected;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Driver: packets split into contiguous ranges over threads; every thread  */
 /* keeps private integer tallies, summed at the end (order independent).    */
 /* ------------------------------------------------------------------------ */
@@ -671,7 +828,10 @@ static void* orc_worker(void* arg) {
       orc_vertex* tr = NULL;
       if (s == 0 && jb->trace && i < (uint64_t)jb->n_trace)
         tr = jb->trace + (size_t)i * (size_t)jb->max_v;
-      orc_transport(st, pk, pb->t_snap[s], &ta, &res, tr, jb->max_v);
+      if (pb->n_layers)
+        orc_transport_stepped(st, pk, pb->t_snap[s], &ta, &res, tr, jb->max_v);
+      else
+        orc_transport(st, pk, pb->t_snap[s], &ta, &res, tr, jb->max_v);
       if (res.detected && s < 64) mask |= (uint64_t)1 << s;
       if (s == 0 && jb->packets) {
         orc_packet* o = &jb->packets[i];
@@ -714,6 +874,9 @@ int orc_simulate(const orc_problem* pb, int n_threads, uint64_t* hist, uint64_t*
   st.omega_q = (uint32_t)floor(pb->albedo * 16777216.0 + 0.5);
   st.R_q = (uint64_t)floor(pb->reflectivity * ORC_TWO32 + 0.5);
   st.max_events = pb->max_events ? pb->max_events : 1000000u;
+  st.p_max = 0.0;
+  for (int i = 0; i < pb->n_phase; ++i)
+    if (pb->p[i] > st.p_max) st.p_max = pb->p[i];
 
   size_t nb = (size_t)pb->n_bins, ns = (size_t)pb->n_snap;
   if (n_threads < 1) n_threads = 1;

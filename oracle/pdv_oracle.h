@@ -100,7 +100,10 @@ typedef struct {
   uint64_t n_packets;
   uint64_t seed;
   uint32_t stream_id;
-  uint32_t max_events;   /* event limit per packet (0 = 1000000)             */
+  uint32_t max_events;   /* event limit per packet (0 = 1000000); with layer
+                            stepping it bounds the steps                       */
+  uint32_t n_layers;     /* 0: exact free paths; > 0: the paper's synchronous
+                            stepping, H / n_layers per step (Section II.B)     */
 } orc_problem;
 
 typedef struct {
@@ -151,6 +154,10 @@ double orc_phase_sample(int n, const double* theta, const uint32_t* cq, uint32_t
 
 /* Direction rotation by (theta, phi), Eq. 16-17, renormalised. */
 void orc_rotate(double u[3], double cos_t, double sin_t, double cos_p, double sin_p);
+
+/* cos(theta) drawn by the layer-stepping scheme's acceptance-rejection for
+ * packet pk at step `step` (uses seed, stream_id and the phase table of pb). */
+double orc_phase_ar_cos(const orc_problem* pb, uint64_t pk, uint32_t step);
 
 /* Full simulation. hist: [n_snap][n_bins]; counters: [n_snap][ORC_NCOUNTERS];
  * order_hist (optional): [n_snap][ORC_NORDER][n_bins]; packets (optional):

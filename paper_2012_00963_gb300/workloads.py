@@ -82,7 +82,8 @@ class Workload:
     n_packets: int = 1_000_000
     seed: int = 1
     stream_id: int = 0
-    max_events: int = 1_000_000
+    max_events: int = 1_000_000       # with layer stepping: the step limit
+    n_layers: int = 0                 # 0 exact free paths; > 0 the paper's H / n_layers steps
     precision: str = "fp32"           # "fp32" | "fp64"
     name: str = "custom"
 
