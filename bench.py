@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mode", default="default",
-                    choices=["default", "serve", "batch", "precision", "model", "extract-mc"])
+                    choices=["default", "serve", "batch", "precision", "model", "extract-mc",
+                             "stepping"])
     ap.add_argument("--model-sets", type=int, default=100_000,
                     help="parameter sets / spectra of the model mode")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
@@ -678,6 +679,82 @@ def extract_mc_mode(args):
     return 0
 
 
+def stepping_mode(args):
+    """The paper's own scheme (1000 layers, acceptance-rejection angles) on the
+    workload its timings are quoted on (Fig. 4: 1e7 photons), against the exact
+    free-path scheme on the same cloud, and the oracle's stepping on a sample."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_2012_00963_gb300 import pdv
+    from paper_2012_00963_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = pdv.Context(0, stream=stream.cuda_stream)
+    n = int(args.packets) if args.packets != 1e8 else 10_000_000
+    wl = W.fig4(n_packets=n)
+    cloud = pdv.Cloud(ctx, wl)
+    out = {}
+    clocks = Clocks(0)
+    clocks.start()
+    for name, w in (("stepping", wl), ("exact", wl.replace(n_layers=0))):
+        pdv.simulate_spectrum(ctx, cloud, w, n_packets=min(n, 100000))      # warm-up
+        ms, kms = [], []
+        for _ in range(max(1, args.steps)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = pdv.simulate_spectrum(ctx, cloud, w, per_dv=True)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            kms.append(ctx.stats()["last_transport_ms"])
+        c = pdv.counters_dict(r["counters"][0])
+        st = ctx.stats()
+        hist = r["raw"][0, 1:-1].astype(np.float64) / 2.0**32
+        vc = (np.arange(wl.n_bins) + 0.5) * (wl.v_hi - wl.v_lo) / wl.n_bins + wl.v_lo
+        out[name] = {"ms": statistics.mean(ms), "kernel_ms": statistics.mean(kms),
+                     "photons_per_s": n / (statistics.mean(ms) / 1e3),
+                     "scatter_events_per_s": c["scatters"] / (statistics.mean(ms) / 1e3),
+                     "events": c["events"], "scatters": c["scatters"],
+                     "detected_fraction": c["w_detected"] / 2.0**32 / n,
+                     "mean_v_app_detected": float((hist * vc).sum() / hist.sum()),
+                     "hist": hist}
+        if name == "stepping":
+            out[name]["steps"] = st["last_steps"]
+            out[name]["steps_per_s"] = st["last_steps"] / (statistics.mean(kms) / 1e3)
+    clk = clocks.stop()
+    info = cloud.info()
+    cloud.close()
+    ctx.close()
+    h_s, h_e = out["stepping"].pop("hist"), out["exact"].pop("hist")
+    sel = (h_s + h_e) > 50
+    chi2 = float(np.mean((h_s[sel] - h_e[sel]) ** 2 / (h_s[sel] + h_e[sel])))
+    # the oracle's stepping on a sample of the same workload
+    m = 400
+    t0 = time.perf_counter()
+    O.simulate(wl, n_packets=m, n_threads=os.cpu_count())
+    t_cpu = time.perf_counter() - t0
+    paper_photons_per_s = 1e7 / 500.0                  # GTX960, Section II.D
+    line = {
+        "mode": "stepping",
+        "metric": "photons/s of the paper's layer-stepping scheme (1000 layers), 1e7-photon spectrum",
+        "value": out["stepping"]["photons_per_s"], "unit": "photons/s",
+        "vs_paper_gtx960": out["stepping"]["photons_per_s"] / paper_photons_per_s,
+        "seconds_per_1e7_photon_spectrum": 1e7 / out["stepping"]["photons_per_s"],
+        "stepping": out["stepping"], "exact": out["exact"],
+        "exact_over_stepping_speed": out["exact"]["photons_per_s"] / out["stepping"]["photons_per_s"],
+        "spectrum_chi2_per_bin_stepping_vs_exact": chi2,
+        "mean_v_app_shift_m_s": out["stepping"]["mean_v_app_detected"] - out["exact"]["mean_v_app_detected"],
+        "tau_tot": info["tau_tot"], "dtype": "f32", "data": "synthetic (seeded)",
+        "cpu_baseline": {"value": m / t_cpu, "unit": "photons/s", "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": "%d photons of the same workload, layer stepping" % m},
+        "config": {"workload": "Fig. 4 cloud: tin, beta 10, d_m 1.5 um, sigma 0.5, 20 mg/cm^2, Mie 3+9i "
+                               "at 1550 nm, every upward photon, %d photons, 1000 layers, 600 bins" % n},
+        "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -692,6 +769,8 @@ def main():
         return model_mode(args)
     if args.mode == "extract-mc":
         return extract_mc_mode(args)
+    if args.mode == "stepping":
+        return stepping_mode(args)
     return our_arm(args)
 
 

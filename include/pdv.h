@@ -140,6 +140,16 @@ typedef struct {
   uint64_t* out_raw;               /* optional [n_snap * (n_bins + 2)]: under, bins, over */
   pdv_counters* out_counters;      /* optional [n_snap]                  */
   pdv_packet_record* out_packets;  /* optional [n_packets] (n_packets <= 2^26) */
+  uint32_t n_layers;               /* 0: exact free paths (the default). > 0: the
+                                      paper's own scheme (Section II.B steps (2)-(6)):
+                                      synchronous steps of (v_max - v_fs) t / n_layers,
+                                      a Bernoulli pass per layer with Eq. 7 / Eq. 10,
+                                      the interaction at the step's end, and the polar
+                                      angle by acceptance-rejection over the sphere
+                                      (p(theta) / max p). FP32 only, through
+                                      pdv_simulate_spectrum; max_events then bounds
+                                      the steps. The paper uses 1000.        */
+  uint32_t reserved;               /* 0                                   */
 } pdv_request;
 
 /* Launch parameters of the persistent FP32 kernel (pdv_autotune picks them). */
@@ -167,6 +177,7 @@ typedef struct {
   int transport_grid, transport_block;
   double last_model_ms;            /* CUDA-event time of the last pdv_ss_spectrum /
                                       pdv_extract_peaks main kernel      */
+  uint64_t last_steps;             /* layer steps of the last layer-stepping call */
 } pdv_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -320,8 +331,9 @@ typedef struct {
 /* Extract the main peak of n_spectra spectra of n_bins uniform bins over
  * [v_lo, v_hi] (row-major [n_spectra][n_bins]). Arithmetic is FP32 with
  * cosine / sine tables computed in FP64 and rounded to FP32; inputs are
- * rounded to FP32 (magnitudes below 1.2e-38 flush to zero). Accuracy: about 1e-6 relative in x_peak, I''/I, beta and tau0 while the
- * cut-off smooths (k_c well below n_bins / 2); as k_c nears n_bins / 2 the
+ * rounded to FP32 (magnitudes below 1.2e-38 flush to zero). Accuracy: about
+ * 1e-6 relative in x_peak, I''/I, beta and tau0 while the cut-off smooths
+ * (k_c well below n_bins / 2); as k_c nears n_bins / 2 the
  * FP32 rounding of the input itself, amplified by up to pi^2 per bin in the
  * second derivative, dominates the curvature.
  * spectra: host array, or device with PDV_IN_DEVICE. out: host array,

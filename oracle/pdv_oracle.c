@@ -709,6 +709,10 @@ static void orc_transport_stepped(const orc_setup* st, uint64_t pk, double t, or
   const double z_fs = pb->v_fs * t, z_top = st->v_top * t;
   /* Step (2): every step is a thousandth (1 / n_layers) of the ejecta height */
   const double h = (z_top - z_fs) / (double)pb->n_layers;
+  /* a step that ends within 1e-6 of the ejecta height of the top or of the
+   * free surface reaches it: n_layers vertical steps land exactly on the
+   * surface, and rounding must not decide whether they do */
+  const double eps = 1e-6 * (z_top - z_fs);
   double z = z_top;
   double vapp = 0.0;
   uint64_t W = (uint64_t)1 << 32;
@@ -729,13 +733,13 @@ static void orc_transport_stepped(const orc_setup* st, uint64_t pk, double t, or
       dtau = st->tau_tot * fabs(orc_cdf(st, zc / t) - orc_cdf(st, z / t)) / fabs(u[2]);
     if (orc_u01(r[0]) < exp(-dtau)) {
       /* passes the layer: step (5) moves it; step (6) checks the boundaries */
-      if (zn >= z_top) {
+      if (zn >= z_top - eps) {
         x += u[0] * (z_top - z) / u[2];
         y += u[1] * (z_top - z) / u[2];
         detected = orc_escape(st, ta, x, y, z_top, u, W, vapp, nsca + nsurf, trace, max_v, &nv);
         fate = ORC_FATE_ESCAPED;
         break;
-      } else if (zn <= z_fs) {
+      } else if (zn <= z_fs + eps) {
         x += u[0] * (z_fs - z) / u[2];
         y += u[1] * (z_fs - z) / u[2];
         z = z_fs;

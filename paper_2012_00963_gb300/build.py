@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpdv.so")
-SOURCES = ["tables.cu", "transport.cu", "spectra.cu", "api.cu"]
+SOURCES = ["tables.cu", "transport.cu", "spectra.cu", "stepping.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Host code is compiled without FMA contraction (gcc contracts by default on
 # Arm), so host-side floating point gives the same bits on x86 and Arm.

@@ -22,6 +22,7 @@
 
 #include "pdv_internal.cuh"
 #include "spectra.cuh"
+#include "stepping.cuh"
 
 using namespace pdv;
 
@@ -72,6 +73,7 @@ struct pdv_ctx {
   std::atomic<unsigned long long> launches{0};
   double last_transport_ms = 0.0;
   double last_model_ms = 0.0;
+  unsigned long long last_steps = 0;
   unsigned long long last_events = 0;
   int last_grid = 0, last_block = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -144,6 +146,7 @@ struct pdv_cloud {
   double tau_tot = 0, q_ext = 0, albedo = 0, g_tab = 0;
   bool has_phase = false;
   CloudTables t;
+  float* pn = nullptr;                // p(theta) / max p at the phase nodes (layer stepping)
   void* mass_arena = nullptr;
   void* phase_arena = nullptr;
 };
@@ -243,6 +246,7 @@ extern "C" pdv_status pdv_get_stats(pdv_ctx* c, pdv_stats* out) {
   out->transport_grid = c->last_grid;
   out->transport_block = c->last_block;
   out->last_model_ms = c->last_model_ms;
+  out->last_steps = c->last_steps;
   return PDV_OK;
 }
 
@@ -403,8 +407,15 @@ extern "C" pdv_status pdv_set_phase_table(pdv_cloud* cl, int n, const double* th
   const size_t oin = L.add(sizeof(double) * 2 * n);
   const size_t owk = L.add(sizeof(double) * 2 * n);
   const size_t og = L.add(sizeof(double));
+  const size_t opn = L.add(sizeof(float) * n);
   char* base = (char*)ctx_alloc(c, L.bytes, c->stream);
   if (!base) return fail(PDV_ENOMEM, "phase table allocation failed");
+  // p / max p for the layer-stepping scheme's acceptance-rejection
+  double p_max = 0.0;
+  for (int i = 0; i < n; ++i) p_max = std::max(p_max, p[i]);
+  std::vector<float> pn(n);
+  for (int i = 0; i < n; ++i) pn[i] = (float)(p[i] / p_max);
+  cl->pn = (float*)(base + opn);
   cl->phase_arena = base;
   cl->t.Cq = (unsigned*)(base + oCq);
   cl->t.thpi = (float*)(base + oth);
@@ -419,6 +430,8 @@ extern "C" pdv_status pdv_set_phase_table(pdv_cloud* cl, int n, const double* th
   cudaError_t e = cudaMemcpyAsync(din, theta, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(din + n, p, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cl->pn, pn.data(), sizeof(float) * n, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = build_phase_cdf(din, din + n, n, dwk, &cl->t, dg, c->stream);
   c->launches += 6;
   double g = 0.0;
@@ -544,6 +557,9 @@ static pdv_status validate_request(const pdv_request* r) {
   if (r->out_packets && r->n_packets > ((r->flags & PDV_OUT_DEVICE) ? (1ull << 28) : (1ull << 26)))
     return fail(PDV_EINVAL, "packet dumps need n_packets <= 2^26 (2^28 into device memory)");
   if (r->flags & ~(PDV_OUT_DEVICE | PDV_PER_DV)) return fail(PDV_EINVAL, "unknown flags");
+  if (r->reserved) return fail(PDV_EINVAL, "reserved must be 0");
+  if (r->n_layers && r->precision != PDV_PREC_FP32)
+    return fail(PDV_EINVAL, "the layer-stepping scheme runs in FP32");
   const pdv_probe& pr = r->probe;
   if (!(pr.z_probe_mm > 0) || !(pr.beam_radius_mm >= 0) || !std::isfinite(pr.aperture_radius_mm) ||
       !(pr.cone_half_angle_rad > 0))
@@ -621,7 +637,7 @@ static void fill_times(const pdv_request* r, double* out) {
 // snapshot times and staged outputs.
 struct ReqBuffers {
   size_t o_set, o_ctr, o_cnt, o_hist, o_t, o_spec, o_craw, o_cout, o_pk, o_ptr_spec, o_ptr_cnt,
-      o_ptr_raw, o_flags;
+      o_ptr_raw, o_flags, o_steps;
   size_t bytes;
 };
 
@@ -642,6 +658,7 @@ static ReqBuffers plan_request(const pdv_request* r, bool device_out) {
   b.o_ptr_cnt = L.add(sizeof(void*));
   b.o_ptr_raw = L.add(sizeof(void*));
   b.o_flags = L.add(sizeof(unsigned));
+  b.o_steps = L.add(sizeof(unsigned long long));
   b.bytes = L.bytes;
   return b;
 }
@@ -677,6 +694,43 @@ static pdv_status f32_geometry(pdv_ctx* c, size_t smem, int hist_mode, bool dump
 static pdv_status enqueue_transport(pdv_ctx* c, const pdv_request* r, const SetDesc& d,
                                     char* base, const ReqBuffers& b, cudaStream_t st,
                                     bool timed) {
+  if (r->n_layers) {
+    // the paper's layer stepping (Section II.B steps (2)-(6))
+    const pdv_cloud* cl = r->cloud;
+    const double span = cl->v_top - cl->v_bot;
+    const double h_v = (cl->v_top - cl->desc.v_fs) / (double)r->n_layers;
+    StepConst sc;
+    sc.P_fs = std::llround((cl->desc.v_fs - cl->v_bot) / span * kTwo62);
+    sc.h_P = std::llround(h_v / span * kTwo62);
+    sc.h_v = (float)h_v;
+    sc.v_per_P = (float)(span / kTwo62);
+    sc.tau_S = (float)(cl->tau_tot / kTwo62);
+    sc.tau_hv_dv = (float)(cl->tau_tot / kTwo62 * h_v / (span / cl->t.n_v));
+    sc.key2x = (unsigned)r->seed ^ 0xA4093822u;
+    sc.key2y = (unsigned)(r->seed >> 32) ^ r->stream_id;
+    sc.eps_P = std::llround(1e-6 * (kTwo62 - (double)sc.P_fs));
+    sc.expo = cl->desc.profile_kind == PDV_PROFILE_EXPONENTIAL ? 1 : 0;
+    sc.b_vfs = (float)(cl->desc.beta / cl->desc.v_fs);
+    sc.invE = sc.expo ? (float)(1.0 / -std::expm1(-cl->desc.beta * (cl->v_top / cl->desc.v_fs - 1.0))) : 0.f;
+    sc.tau_f = (float)cl->tau_tot;
+    const size_t smem = transport_step_smem(d.n_v, d.n_p, d.n_snap, d.phase_uniform);
+    if (smem > (size_t)c->max_smem) return fail(PDV_EINVAL, "tables need %zu bytes of shared memory", smem);
+    int occ = 0;
+    CK(transport_step_occupancy(smem, &occ));
+    if (occ < 1) return fail(PDV_EINVAL, "layer-stepping kernel does not fit");
+    const unsigned long long want = (r->n_packets + 255) / 256;
+    const int grid = (int)std::min<unsigned long long>(want, (unsigned long long)c->sm_count * occ);
+    CK(cudaMemsetAsync(base + b.o_steps, 0, sizeof(unsigned long long), st));
+    if (timed) cudaEventRecord(c->ev0, st);
+    CK(launch_transport_step((const SetDesc*)(base + b.o_set), cl->pn, sc,
+                             (unsigned long long*)(base + b.o_ctr),
+                             (unsigned long long*)(base + b.o_steps), std::max(grid, 1), smem, st));
+    if (timed) cudaEventRecord(c->ev1, st);
+    c->last_grid = std::max(grid, 1);
+    c->last_block = 256;
+    c->launches += 1;
+    return PDV_OK;
+  }
   if (timed) cudaEventRecord(c->ev0, st);
   if (r->precision == PDV_PREC_FP32) {
     const int hm = pick_hist_mode(c, d);
@@ -753,9 +807,12 @@ extern "C" pdv_status pdv_simulate_spectrum(pdv_ctx* c, const pdv_request* r) {
     if (r->out_raw) CK(cudaMemcpyAsync(r->out_raw, raw, sizeof(unsigned long long) * (size_t)r->n_snap * (r->n_bins + 2), cudaMemcpyDeviceToHost, st));
     if (r->out_packets) CK(cudaMemcpyAsync(r->out_packets, d.packets, sizeof(pdv_packet_record) * r->n_packets, cudaMemcpyDeviceToHost, st));
   }
-  unsigned long long ev = 0;
+  unsigned long long ev = 0, steps = 0;
   CK(cudaMemcpyAsync(&ev, base + b.o_cnt + sizeof(unsigned long long) * C_EVENTS, sizeof ev, cudaMemcpyDeviceToHost, st));
+  if (r->n_layers)
+    CK(cudaMemcpyAsync(&steps, base + b.o_steps, sizeof steps, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  c->last_steps = steps;
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) c->last_transport_ms = ms;
   cudaGetLastError();
@@ -962,6 +1019,8 @@ extern "C" pdv_status pdv_simulate_batch(pdv_ctx* c, const pdv_request* rs, int 
   for (int i = 0; i < n; ++i) {
     pdv_status s = validate_request(&rs[i]);
     if (s != PDV_OK) return fail(s, "request %d: %s", i, g_err.c_str());
+    if (rs[i].n_layers)
+      return fail(PDV_EINVAL, "request %d: layer stepping runs through pdv_simulate_spectrum only", i);
   }
   std::vector<pdv_request> f32;
   for (int i = 0; i < n; ++i) {
@@ -982,7 +1041,8 @@ extern "C" pdv_status pdv_autotune(pdv_ctx* c, const pdv_request* rs, int n, pdv
   for (int i = 0; i < n; ++i) {
     pdv_status s = validate_request(&rs[i]);
     if (s != PDV_OK) return fail(s, "request %d: %s", i, g_err.c_str());
-    if (rs[i].precision != PDV_PREC_FP32) return fail(PDV_EINVAL, "autotune takes FP32 requests");
+    if (rs[i].precision != PDV_PREC_FP32 || rs[i].n_layers)
+      return fail(PDV_EINVAL, "autotune takes FP32 exact-free-path requests");
   }
   CK(enter(c->device));
   // a shortened copy of the batch (1/16 of the packets, at least 65536 each)
@@ -1258,6 +1318,7 @@ extern "C" pdv_status pdv_submit(pdv_ctx* c, const pdv_request* r, pdv_ticket* o
   if (!c || !out) return fail(PDV_EINVAL, "NULL argument");
   pdv_status s = validate_request(r);
   if (s != PDV_OK) return s;
+  if (r->n_layers) return fail(PDV_EINVAL, "layer stepping runs through pdv_simulate_spectrum only");
   if (r->precision != PDV_PREC_FP32) return fail(PDV_EINVAL, "serving runs FP32 requests");
   if (r->out_packets) return fail(PDV_EINVAL, "serving does not dump packets");
   CK(enter(c->device));
@@ -1424,6 +1485,7 @@ extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request
   if (!c) return fail(PDV_EINVAL, "ctx is NULL");
   pdv_status s = validate_request(r);
   if (s != PDV_OK) return s;
+  if (r->n_layers) return fail(PDV_EINVAL, "layer stepping runs through pdv_simulate_spectrum only");
   if (r->precision != PDV_PREC_FP32) return fail(PDV_EINVAL, "the static-scratch call runs FP32 requests");
   if (!(r->flags & PDV_OUT_DEVICE)) return fail(PDV_EINVAL, "the static-scratch call needs PDV_OUT_DEVICE outputs");
   // scratch layout: set descriptor, packet counter, counters, histogram,

@@ -1,0 +1,378 @@
+// stepping.cu — the paper's own transport scheme, taken literally
+// (arXiv:2012.00963 Section II.B steps (2)-(6)):
+//   (2) every step is H / n_layers long (H: the ejecta height v_max t - v_fs t);
+//   (3) the photon takes one step along its direction; it passes the layer it
+//       crossed with the Beer-Lambert probability of the mass the layer holds
+//       (Eq. 7, Eq. 10), drawn as a Bernoulli trial;
+//   (4) a photon stopped in the layer interacts at the end of the step: it is
+//       absorbed or scattered (Eq. 11), the polar angle by acceptance-rejection
+//       against p(theta) (a direction uniform over the sphere, accepted with
+//       probability p(theta) / max p), the azimuth uniform (Eq. 15), the new
+//       direction by Eq. 16-17 and the Doppler update by Eq. 4 / Eq. 18;
+//   (6) the free surface reflects, the top lets photons out to the probe.
+//
+// The photon's height is the fixed-point coordinate P = (v - v_bot) /
+// (v_top - v_bot) 2^62 of the velocity variable v = z / t, so that a step is
+// the same in P at every snapshot time (one history serves all of them), and
+// the mass S(P) held below a height is the velocity table's interpolation in
+// exact integer arithmetic; for the exponential law of Eq. 20 the layer mass
+// is evaluated in closed form instead (exp(-x0) (1 - exp(-dx)) / E), so the
+// layer optical depth tau_tot dS / |u_z| carries neither cancellation nor the
+// table's interpolation error.
+//
+// Random numbers: step k of packet p draws Philox4x32-10 with counter
+// (p, k, stream) under the request's seed (k = 0 is the launch): word 0 the
+// Bernoulli trial, word 1 scatter/absorb (24-bit) or the surface polar angle,
+// word 2 the surface azimuth, word 3 the scattering azimuth. The
+// acceptance-rejection draws use a second key (seed ^ 0xA4093822, seed_hi ^
+// stream) and counter (p, k, attempt pair), two attempts per call.
+#include <cmath>
+
+#include "stepping.cuh"
+
+namespace pdv {
+
+namespace {
+
+constexpr unsigned kFullS = 0xffffffffu;
+constexpr long long kOneP = 1ll << 62;
+
+struct StepSmem {
+  size_t o_sq, o_pn, o_th, o_ts, bytes;
+};
+
+__host__ __device__ inline size_t align16s(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline StepSmem step_layout(int n_v, int n_p, int n_snap, int uniform) {
+  StepSmem L;
+  size_t o = 0;
+  L.o_sq = o; o = align16s(o + sizeof(unsigned long long) * (size_t)(n_v + 1));
+  L.o_pn = o; o = align16s(o + sizeof(float) * (size_t)n_p);
+  L.o_th = o; o = align16s(o + sizeof(float) * (size_t)(uniform ? 0 : n_p));
+  L.o_ts = o; o = align16s(o + sizeof(float) * (size_t)n_snap);
+  L.bytes = o;
+  return L;
+}
+
+// S(P), 2^62 scale: 0 below the cloud, 2^62 above it, and inside the table's
+// linear interpolation between its velocity nodes, in integer arithmetic.
+__device__ __forceinline__ long long mass_at(const unsigned long long* Sq, int n_v, long long P) {
+  if (P <= 0) return 0;
+  if (P >= kOneP) return kOneP;
+  const unsigned long long q = (unsigned long long)P << 2;           // P 2^2 < 2^64
+  const int j = (int)__umul64hi(q, (unsigned long long)n_v);         // floor(P n_v / 2^62)
+  const unsigned long long frac = q * (unsigned long long)n_v;       // position in the node, 2^64 scale
+  return (long long)(Sq[j] + __umul64hi(Sq[j + 1] - Sq[j], frac));
+}
+
+// p(theta) / max p at cos(theta) = mu, linear in theta between the nodes.
+__device__ __forceinline__ float phase_ratio(float mu, const float* pn, const float* thpi, int n_p,
+                                             int uniform, float inv_nm1) {
+  const float tpi = acosf(mu) * 0.318309886183790672f;               // theta / pi
+  int i;
+  float f;
+  if (uniform) {
+    const float pos = tpi / inv_nm1;
+    i = min((int)pos, n_p - 2);
+    f = pos - (float)i;
+  } else {
+    int lo = 0, hi = n_p - 2;                                         // largest thpi_i <= tpi
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (thpi[mid] <= tpi) lo = mid; else hi = mid - 1;
+    }
+    i = lo;
+    f = (tpi - thpi[i]) / (thpi[i + 1] - thpi[i]);
+  }
+  f = fminf(fmaxf(f, 0.0f), 1.0f);
+  return fmaf(pn[i + 1] - pn[i], f, pn[i]);
+}
+
+// Section II.B step (4): acceptance-rejection for cos(theta).
+__device__ __forceinline__ float ar_cos(unsigned long long pk, unsigned step, uint2 key2,
+                                        const float* pn, const float* thpi, int n_p, int uniform,
+                                        float inv_nm1) {
+  float mu = 0.0f;
+  for (unsigned a = 0; a < (1u << 24); ++a) {
+    const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), step, a), key2);
+    mu = fmaf(2.0f, u23f(r.x), -1.0f);                                // exact
+    if (u23f(r.y) < phase_ratio(mu, pn, thpi, n_p, uniform, inv_nm1)) return mu;
+    mu = fmaf(2.0f, u23f(r.z), -1.0f);
+    if (u23f(r.w) < phase_ratio(mu, pn, thpi, n_p, uniform, inv_nm1)) return mu;
+  }
+  return mu;
+}
+
+__device__ __forceinline__ void launch_xy(unsigned long long pk, unsigned sid, uint2 key,
+                                          float r_beam, float& x0, float& y0) {
+  const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), 0u, sid), key);
+  const float rad = r_beam * sqrtf(u23f(r.x));
+  float sp, cp;
+  sincospif(2.0f * u23f(r.y), &sp, &cp);
+  x0 = rad * cp;
+  y0 = rad * sp;
+}
+
+__device__ __forceinline__ void kahan(float& sum, float& comp, float term) {
+  const float y = term - comp;
+  const float t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
+
+__global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restrict__ set,
+                                                        const float* __restrict__ pn_g,
+                                                        StepConst sc,
+                                                        unsigned long long* __restrict__ ctr,
+                                                        unsigned long long* __restrict__ steps_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ SetDesc sd;
+  __shared__ unsigned long long s_cnt[C_NCOUNT];
+  __shared__ unsigned long long s_steps;
+  {
+    const int* src = reinterpret_cast<const int*>(set);
+    int* dst = reinterpret_cast<int*>(&sd);
+    for (int i = threadIdx.x; i < (int)(sizeof(SetDesc) / sizeof(int)); i += blockDim.x)
+      dst[i] = src[i];
+    if (threadIdx.x < C_NCOUNT) s_cnt[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) s_steps = 0ull;
+  }
+  __syncthreads();
+  const StepSmem L = step_layout(sd.n_v, sd.n_p, sd.n_snap, sd.phase_uniform);
+  unsigned long long* Sq = reinterpret_cast<unsigned long long*>(smem + L.o_sq);
+  float* pn = reinterpret_cast<float*>(smem + L.o_pn);
+  float* thpi = reinterpret_cast<float*>(smem + L.o_th);
+  float* ts = reinterpret_cast<float*>(smem + L.o_ts);
+  for (int i = threadIdx.x; i <= sd.n_v; i += blockDim.x) Sq[i] = sd.Sq[i];
+  for (int i = threadIdx.x; i < sd.n_p; i += blockDim.x) {
+    pn[i] = pn_g[i];
+    if (!sd.phase_uniform) thpi[i] = sd.thpi[i];
+  }
+  for (int i = threadIdx.x; i < sd.n_snap; i += blockDim.x) ts[i] = (float)sd.t_snap[i];
+  __syncthreads();
+
+  const uint2 key = make_uint2((unsigned)sd.seed, (unsigned)(sd.seed >> 32));
+  const uint2 key2 = make_uint2(sc.key2x, sc.key2y);
+  const unsigned sid = sd.stream_id;
+  const int n_bins = sd.n_bins, row = hist_row(sd.n_bins), n_snap = sd.n_snap;
+  const float h_Pf = (float)sc.h_P;
+
+  unsigned st_launch = 0, st_events = 0, st_scat = 0, st_surf = 0;
+  unsigned long long st_steps = 0;
+  bool alive = false;
+  unsigned long long pk = 0, W = 0, dmask = 0;
+  long long P = 0;
+  unsigned k = 0, nev = 0, nsca = 0, nsurf = 0;
+  float vcur = 0.f, ux = 0.f, uy = 0.f, uz = -1.f, iuz = -1.f;
+  float Xx = 0.f, Xy = 0.f, vapp = 0.f, vcomp = 0.f;
+
+  for (;;) {
+    if (!alive) {
+      // Step (1): the next packet of the request, at the top moving along -z
+      const unsigned long long i = atomicAdd(ctr, 1ull);
+      if (i >= sd.n_packets) break;
+      pk = sd.packet_begin + i;
+      P = kOneP;
+      vcur = sd.v_top_f;
+      ux = 0.f; uy = 0.f; uz = -1.f; iuz = -1.f;
+      Xx = 0.f; Xy = 0.f; vapp = 0.f; vcomp = 0.f;
+      W = 1ull << 32;
+      k = 1; nev = 0; nsca = 0; nsurf = 0; dmask = 0;
+      ++st_launch;
+      alive = true;
+    }
+    const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), k, sid), key);
+    // Step (3): one step along u and the optical depth of the layer crossed
+    const long long Pn = P + __float2ll_rn(uz * h_Pf);
+    const long long Pc = Pn < sc.P_fs ? sc.P_fs : (Pn > kOneP ? kOneP : Pn);
+    const bool horizontal = fabsf(uz) < 1e-9f;
+    float dtau;
+    if (sc.expo) {
+      // Eq. 20 in closed form: with x = beta (v - v_fs) / v_fs the mass
+      // fraction between two heights is exp(-x0) (1 - exp(-(x1 - x0))) / E
+      const float e0 = expf(-sc.b_vfs * ((float)P * sc.v_per_P));
+      if (horizontal) {
+        dtau = sc.tau_f * sc.b_vfs * e0 * sc.invE * sc.h_v;
+      } else {
+        const float dx = sc.b_vfs * ((float)(Pc - P) * sc.v_per_P);
+        dtau = sc.tau_f * e0 * fabsf(expm1f(-dx)) * sc.invE / fabsf(uz);
+      }
+    } else if (horizontal) {
+      float d = 0.0f;
+      if (P > 0 && P < kOneP) {
+        const int j = (int)__umul64hi((unsigned long long)P << 2, (unsigned long long)sd.n_v);
+        d = u64_to_f(Sq[j + 1] - Sq[j]);
+      }
+      dtau = d * sc.tau_hv_dv;
+    } else {
+      const long long dS = mass_at(Sq, sd.n_v, Pc) - mass_at(Sq, sd.n_v, P);
+      dtau = (float)(dS < 0 ? -dS : dS) * sc.tau_S / fabsf(uz);
+    }
+    ++st_steps;
+    unsigned fate = 0;
+    if (u23f(r.x) < expf(-dtau)) {
+      if (Pn >= kOneP - sc.eps_P) {
+        // Step (6): out through the top; vacuum flight to the probe plane
+        const float d = sd.v_top_f - vcur;
+        Xx = fmaf(ux * iuz, d, Xx);
+        Xy = fmaf(uy * iuz, d, Xy);
+        if (sd.cone_all || uz >= sd.cos_alpha_f) {
+          float x0, y0;
+          launch_xy(pk, sid, key, sd.r_beam_f, x0, y0);
+          const float tx = ux * iuz, ty = uy * iuz;
+          const float ax = fmaf(tx, sd.z_probe_f, x0), ay = fmaf(ty, sd.z_probe_f, y0);
+          const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
+          const float fb = floorf((vapp - vcomp - sd.v_lo_f) * sd.inv_dbin_f);
+          const int idx = fb < 0.0f ? 0 : (fb >= (float)n_bins ? n_bins + 1 : (int)fb + 1);
+          for (int s = 0; s < n_snap; ++s) {
+            const float t = ts[s];
+            const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
+            if (sd.ap_all || fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
+              atomicAdd(&sd.hist[(size_t)s * row + idx], W);             // Eq. 19
+              atomicAdd(&sd.hist[(size_t)s * row + n_bins + 2], 1ull);
+              if (s < 64) dmask |= 1ull << s;
+            }
+          }
+        }
+        atomicAdd(&s_cnt[C_ESCAPES], 1ull);
+        atomicAdd(&s_cnt[C_W_ESCAPED], W);
+        fate = 1;
+      } else if (Pn <= sc.P_fs + sc.eps_P) {
+        // Step (6): the free surface; reflectivity in 2^32 fixed point
+        const float d = sd.v_fs_f - vcur;
+        Xx = fmaf(ux * iuz, d, Xx);
+        Xy = fmaf(uy * iuz, d, Xy);
+        P = sc.P_fs;
+        vcur = sd.v_fs_f;
+        ++nev; ++nsurf; ++st_events; ++st_surf;
+        const unsigned long long Wn =
+            sd.R_q >= (1ull << 32) ? W : ((W * sd.R_q + (1ull << 31)) >> 32);
+        if (Wn != W) atomicAdd(&s_cnt[C_W_ABS_SURFACE], W - Wn);
+        W = Wn;
+        float nx, ny, nz;
+        if (sd.surface_mode == PDV_SURFACE_SPECULAR) {
+          nx = ux; ny = uy; nz = -uz;
+        } else {
+          float st, ct, sp, cp;
+          if (sd.surface_mode == PDV_SURFACE_LAMBERT) {
+            const float a = u23f(r.y);
+            ct = sqrtf(a);
+            st = sqrtf(1.0f - a);
+          } else {
+            sincospif(0.5f * u23f(r.y), &st, &ct);
+          }
+          sincospif(2.0f * u23f(r.z), &sp, &cp);
+          nx = st * cp; ny = st * sp; nz = ct;
+          const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+          nx *= inv_n; ny *= inv_n; nz *= inv_n;
+        }
+        kahan(vapp, vcomp, __fmul_rn(0.5f * (nz - uz), sd.v_fs_f));
+        ux = nx; uy = ny; uz = nz;
+        iuz = rcp_approx(nz);
+        if (W == 0) fate = 3;
+      } else {
+        // Step (5): passed the layer
+        P = Pn;
+        vcur = fmaf((float)Pn, sc.v_per_P, sd.v_bot_f);
+        Xx = fmaf(ux, sc.h_v, Xx);
+        Xy = fmaf(uy, sc.h_v, Xy);
+      }
+    } else {
+      // stopped in the layer: the interaction is at the end of the step
+      const float vn = Pc == sc.P_fs ? sd.v_fs_f : fmaf((float)Pc, sc.v_per_P, sd.v_bot_f);
+      if (horizontal) {
+        Xx = fmaf(ux, sc.h_v, Xx);
+        Xy = fmaf(uy, sc.h_v, Xy);
+      } else {
+        const float d = vn - vcur;
+        Xx = fmaf(ux * iuz, d, Xx);
+        Xy = fmaf(uy * iuz, d, Xy);
+      }
+      P = Pc;
+      vcur = vn;
+      ++nev; ++st_events;
+      if ((r.y >> 8) < sd.omega_q) {
+        // Step (4): scattered; the polar angle by acceptance-rejection
+        const float ct = ar_cos(pk, k, key2, pn, thpi, sd.n_p, sd.phase_uniform, sd.inv_nm1);
+        const float st = sqrtf(fmaxf(0.0f, fmaf(-ct, ct, 1.0f)));
+        float sp, cp;
+        sincospif(2.0f * u23f(r.w), &sp, &cp);                         // Eq. 15
+        float nx, ny, nz;
+        if (fabsf(uz) > 1.0f - 1e-6f) {                                // Eq. 17
+          nx = st * cp;
+          ny = st * sp;
+          nz = uz >= 0.0f ? ct : -ct;
+        } else {                                                       // Eq. 16
+          const float h2 = fmaf(ux, ux, uy * uy);
+          const float rs = rsqrtf(h2);
+          const float s = h2 * rs;
+          const float a = st * rs;
+          nx = fmaf(a, fmaf(ux * uz, cp, -uy * sp), ux * ct);
+          ny = fmaf(a, fmaf(uy * uz, cp, ux * sp), uy * ct);
+          nz = fmaf(-st * cp, s, uz * ct);
+        }
+        const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+        nx *= inv_n; ny *= inv_n; nz *= inv_n;
+        kahan(vapp, vcomp, __fmul_rn(0.5f * (nz - uz), vn));        // Eq. 4 / Eq. 18
+        ux = nx; uy = ny; uz = nz;
+        iuz = rcp_approx(nz);
+        ++nsca; ++st_scat;
+      } else {
+        atomicAdd(&s_cnt[C_W_ABS_PARTICLE], W);                         // Eq. 11: absorbed
+        fate = 2;
+      }
+    }
+    if (fate == 0 && k >= sd.max_events) {
+      atomicAdd(&s_cnt[C_W_TRUNCATED], W);
+      atomicAdd(&s_cnt[C_TRUNCATED], 1ull);
+      fate = 4;
+    }
+    ++k;
+    if (fate) {
+      if (sd.packets) {
+        pdv_packet_record rec;
+        rec.n_events = nev;
+        rec.n_scatters = nsca;
+        rec.n_surface = nsurf;
+        rec.fate = fate;
+        rec.weight = W;
+        rec.v_app = (double)vapp - (double)vcomp;
+        rec.detect_mask = dmask;
+        sd.packets[pk - sd.packet_begin] = rec;
+      }
+      alive = false;
+    }
+  }
+
+  // flush the block's counters
+  atomicAdd(&s_cnt[C_LAUNCHED], (unsigned long long)st_launch);
+  atomicAdd(&s_cnt[C_EVENTS], (unsigned long long)st_events);
+  atomicAdd(&s_cnt[C_SCATTERS], (unsigned long long)st_scat);
+  atomicAdd(&s_cnt[C_SURFACE_HITS], (unsigned long long)st_surf);
+  atomicAdd(&s_steps, st_steps);
+  __syncthreads();
+  if (threadIdx.x < C_NCOUNT && s_cnt[threadIdx.x]) atomicAdd(&sd.cnt[threadIdx.x], s_cnt[threadIdx.x]);
+  if (threadIdx.x == 0) atomicAdd(steps_out, s_steps);
+}
+
+}  // namespace
+
+size_t transport_step_smem(int n_v, int n_p, int n_snap, int phase_uniform) {
+  return step_layout(n_v, n_p, n_snap, phase_uniform).bytes;
+}
+
+cudaError_t transport_step_occupancy(size_t smem, int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_transport_step,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_transport_step, 256, smem);
+}
+
+cudaError_t launch_transport_step(const SetDesc* d_set, const float* pn, const StepConst& sc,
+                                  unsigned long long* d_ctr, unsigned long long* d_steps,
+                                  int grid, size_t smem, cudaStream_t st) {
+  k_transport_step<<<grid, 256, smem, st>>>(d_set, pn, sc, d_ctr, d_steps);
+  return cudaGetLastError();
+}
+
+}  // namespace pdv

@@ -88,6 +88,7 @@ class pdv_request(C.Structure):
         ("n_bins", C.c_int), ("v_lo", C.c_double), ("v_hi", C.c_double), ("precision", C.c_int),
         ("flags", C.c_uint32), ("out_spectrum", C.c_void_p), ("out_raw", C.c_void_p),
         ("out_counters", C.c_void_p), ("out_packets", C.c_void_p),
+        ("n_layers", C.c_uint32), ("reserved", C.c_uint32),
     ]
 
 
@@ -105,7 +106,8 @@ class pdv_cloud_info(C.Structure):
 class pdv_stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("last_transport_ms", C.c_double),
                 ("last_events", C.c_uint64), ("transport_grid", C.c_int),
-                ("transport_block", C.c_int), ("last_model_ms", C.c_double)]
+                ("transport_block", C.c_int), ("last_model_ms", C.c_double),
+                ("last_steps", C.c_uint64)]
 
 
 class pdv_ss_set(C.Structure):
@@ -470,6 +472,7 @@ class Request:
         r.seed = int(wl.seed)
         r.stream_id = int(wl.stream_id)
         r.max_events = int(wl.max_events)
+        r.n_layers = int(getattr(wl, "n_layers", 0))
         r.n_bins = int(wl.n_bins)
         r.v_lo = wl.v_lo
         r.v_hi = wl.v_hi

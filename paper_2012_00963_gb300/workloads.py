@@ -241,3 +241,17 @@ def fig13(cloud: int, beta: float, **kw) -> Workload:
         r_ap=0.0, cone_alpha=math.pi / 2, t_snap=(1.0 * US,), n_bins=1200, v_lo=0.0,
         v_hi=8000.0, n_packets=10_000_000, seed=13)
     return wl.replace(**kw)
+
+
+def fig4(**kw) -> Workload:
+    """The convergence and timing case of Section II.D (Fig. 4; the paper's
+    CPU / GPU timings are quoted on it): tin, beta = 10, log-normal d_m = 1.5
+    um, sigma = 0.5, m0 = 20 mg/cm^2, lambda = 1550 nm, Mie phase function;
+    every upward photon is counted; 1e7 photons, the paper's 1000 layers;
+    600 bins over 0-8000 m/s at 1 us."""
+    wl = Workload(
+        name="fig4", m0=20.0 * MG_CM2, beta=10.0, v_max=0.0, d_m=1.5 * UM, sigma_ln=0.5,
+        phase=Phase(kind="mie", m=3.0 + 9.0j, n_angle=1801, n_size=256),
+        r_ap=0.0, cone_alpha=math.pi / 2, t_snap=(1.0 * US,), n_bins=600, v_lo=0.0,
+        v_hi=8000.0, n_packets=10_000_000, seed=9, n_layers=1000)
+    return wl.replace(**kw)
