@@ -713,6 +713,10 @@ static pdv_status enqueue_transport(pdv_ctx* c, const pdv_request* r, const SetD
     sc.b_vfs = (float)(cl->desc.beta / cl->desc.v_fs);
     sc.invE = sc.expo ? (float)(1.0 / -std::expm1(-cl->desc.beta * (cl->v_top / cl->desc.v_fs - 1.0))) : 0.f;
     sc.tau_f = (float)cl->tau_tot;
+    sc.shift_d = 0;
+    while ((sc.h_P >> sc.shift_d) >= (1ll << 30)) ++sc.shift_d;
+    if (sc.P_fs < -(1ll << 62))
+      return fail(PDV_EINVAL, "layer stepping needs the cloud to start within one cloud height of the free surface");
     const size_t smem = transport_step_smem(d.n_v, d.n_p, d.n_snap, d.phase_uniform);
     if (smem > (size_t)c->max_smem) return fail(PDV_EINVAL, "tables need %zu bytes of shared memory", smem);
     int occ = 0;

@@ -88,19 +88,50 @@ __device__ __forceinline__ float phase_ratio(float mu, const float* pn, const fl
   return fmaf(pn[i + 1] - pn[i], f, pn[i]);
 }
 
-// Section II.B step (4): acceptance-rejection for cos(theta).
-__device__ __forceinline__ float ar_cos(unsigned long long pk, unsigned step, uint2 key2,
-                                        const float* pn, const float* thpi, int n_p, int uniform,
-                                        float inv_nm1) {
-  float mu = 0.0f;
-  for (unsigned a = 0; a < (1u << 24); ++a) {
-    const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), step, a), key2);
-    mu = fmaf(2.0f, u23f(r.x), -1.0f);                                // exact
-    if (u23f(r.y) < phase_ratio(mu, pn, thpi, n_p, uniform, inv_nm1)) return mu;
-    mu = fmaf(2.0f, u23f(r.z), -1.0f);
-    if (u23f(r.w) < phase_ratio(mu, pn, thpi, n_p, uniform, inv_nm1)) return mu;
+// Section II.B step (4): acceptance-rejection for cos(theta), run by the whole
+// warp for one lane's packet. Attempt pairs are independent Philox counters,
+// so lane i tries pair base + i; the first acceptance in counter order (lowest
+// lane, then the pair's first attempt) is the one a sequential loop would take.
+__device__ __forceinline__ float ar_cos_warp(unsigned long long pk, unsigned step, uint2 key2,
+                                             const float* pn, const float* thpi, int n_p,
+                                             int uniform, float inv_nm1, int lane) {
+  float last = 0.0f;
+  for (unsigned base = 0; base < (1u << 24); base += 32) {
+    const uint4 r = philox4x32_10(
+        make_uint4((unsigned)pk, (unsigned)(pk >> 32), step, base + (unsigned)lane), key2);
+    const float mu0 = fmaf(2.0f, u23f(r.x), -1.0f);                   // exact
+    const float mu1 = fmaf(2.0f, u23f(r.z), -1.0f);
+    const bool acc0 = u23f(r.y) < phase_ratio(mu0, pn, thpi, n_p, uniform, inv_nm1);
+    const bool acc1 = u23f(r.w) < phase_ratio(mu1, pn, thpi, n_p, uniform, inv_nm1);
+    const unsigned b = __ballot_sync(kFullS, acc0 || acc1);
+    if (b) return __shfl_sync(kFullS, acc0 ? mu0 : mu1, __ffs(b) - 1);
+    last = __shfl_sync(kFullS, mu1, 31);
   }
-  return mu;
+  return last;     // 2^25 rejections in a row: the last proposal
+}
+
+// Height in m/s above v_bot from the fixed-point coordinate, through a 32-bit
+// conversion (P >> 32 keeps 30 significant bits; 64-bit integer conversions
+// run on the narrow FP64 pipe of this GPU).
+__device__ __forceinline__ float p_to_v(long long P, float v_per_P32) {
+  return (float)(int)(P >> 32) * v_per_P32;
+}
+
+// |u_z| h_P in P units: u_z to 32-bit fixed point, then the high half of a
+// 64 x 64 product (2^-32 relative, no 64-bit conversion).
+__device__ __forceinline__ long long step_P(float uz, unsigned long long h_P) {
+  const unsigned m = __float2uint_rz(fabsf(uz) * 4294967296.0f);    // saturates at |u_z| = 1
+  const long long d = (long long)__umul64hi((unsigned long long)m << 32, h_P);
+  return uz < 0.0f ? -d : d;
+}
+
+// exp(y) - 1: the Taylor series through y^6 for |y| <= 1/16 (truncation below
+// 2e-11 relative, i.e. exact at binary32), the library function beyond.
+__device__ __forceinline__ float expm1_small(float y) {
+  if (fabsf(y) > 0.0625f) return expm1f(y);
+  const float p = fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, 1.0f / 720.0f, 1.0f / 120.0f),
+                                                1.0f / 24.0f), 1.0f / 6.0f), 0.5f), 1.0f);
+  return y * p;
 }
 
 __device__ __forceinline__ void launch_xy(unsigned long long pk, unsigned sid, uint2 key,
@@ -155,7 +186,8 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
   const uint2 key2 = make_uint2(sc.key2x, sc.key2y);
   const unsigned sid = sd.stream_id;
   const int n_bins = sd.n_bins, row = hist_row(sd.n_bins), n_snap = sd.n_snap;
-  const float h_Pf = (float)sc.h_P;
+  const float vP32 = sc.v_per_P * 4294967296.0f;           // m/s per unit of P >> 32
+  const float vPd = sc.v_per_P * (float)(1ll << sc.shift_d);    // m/s per unit of dP >> shift_d
 
   unsigned st_launch = 0, st_events = 0, st_scat = 0, st_surf = 0;
   unsigned long long st_steps = 0;
@@ -165,162 +197,203 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
   unsigned k = 0, nev = 0, nsca = 0, nsurf = 0;
   float vcur = 0.f, ux = 0.f, uy = 0.f, uz = -1.f, iuz = -1.f;
   float Xx = 0.f, Xy = 0.f, vapp = 0.f, vcomp = 0.f;
+  float e0 = 0.f, em1 = 0.f;
+  bool e0_ok = false;
 
+  const int lane = threadIdx.x & 31;
+  bool exhausted = false;
   for (;;) {
-    if (!alive) {
+    if (!alive && !exhausted) {
       // Step (1): the next packet of the request, at the top moving along -z
       const unsigned long long i = atomicAdd(ctr, 1ull);
-      if (i >= sd.n_packets) break;
-      pk = sd.packet_begin + i;
-      P = kOneP;
-      vcur = sd.v_top_f;
-      ux = 0.f; uy = 0.f; uz = -1.f; iuz = -1.f;
-      Xx = 0.f; Xy = 0.f; vapp = 0.f; vcomp = 0.f;
-      W = 1ull << 32;
-      k = 1; nev = 0; nsca = 0; nsurf = 0; dmask = 0;
-      ++st_launch;
-      alive = true;
-    }
-    const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), k, sid), key);
-    // Step (3): one step along u and the optical depth of the layer crossed
-    const long long Pn = P + __float2ll_rn(uz * h_Pf);
-    const long long Pc = Pn < sc.P_fs ? sc.P_fs : (Pn > kOneP ? kOneP : Pn);
-    const bool horizontal = fabsf(uz) < 1e-9f;
-    float dtau;
-    if (sc.expo) {
-      // Eq. 20 in closed form: with x = beta (v - v_fs) / v_fs the mass
-      // fraction between two heights is exp(-x0) (1 - exp(-(x1 - x0))) / E
-      const float e0 = expf(-sc.b_vfs * ((float)P * sc.v_per_P));
-      if (horizontal) {
-        dtau = sc.tau_f * sc.b_vfs * e0 * sc.invE * sc.h_v;
+      if (i >= sd.n_packets) {
+        exhausted = true;
       } else {
-        const float dx = sc.b_vfs * ((float)(Pc - P) * sc.v_per_P);
-        dtau = sc.tau_f * e0 * fabsf(expm1f(-dx)) * sc.invE / fabsf(uz);
+        pk = sd.packet_begin + i;
+        alive = true;
       }
-    } else if (horizontal) {
-      float d = 0.0f;
-      if (P > 0 && P < kOneP) {
-        const int j = (int)__umul64hi((unsigned long long)P << 2, (unsigned long long)sd.n_v);
-        d = u64_to_f(Sq[j + 1] - Sq[j]);
+      if (alive) {
+        P = kOneP;
+        vcur = sd.v_top_f;
+        ux = 0.f; uy = 0.f; uz = -1.f; iuz = -1.f;
+        Xx = 0.f; Xy = 0.f; vapp = 0.f; vcomp = 0.f;
+        W = 1ull << 32;
+        k = 1; nev = 0; nsca = 0; nsurf = 0; dmask = 0;
+        e0_ok = false;
+        ++st_launch;
       }
-      dtau = d * sc.tau_hv_dv;
-    } else {
-      const long long dS = mass_at(Sq, sd.n_v, Pc) - mass_at(Sq, sd.n_v, P);
-      dtau = (float)(dS < 0 ? -dS : dS) * sc.tau_S / fabsf(uz);
     }
-    ++st_steps;
+    if (!__any_sync(kFullS, alive)) break;
     unsigned fate = 0;
-    if (u23f(r.x) < expf(-dtau)) {
-      if (Pn >= kOneP - sc.eps_P) {
-        // Step (6): out through the top; vacuum flight to the probe plane
-        const float d = sd.v_top_f - vcur;
-        Xx = fmaf(ux * iuz, d, Xx);
-        Xy = fmaf(uy * iuz, d, Xy);
-        if (sd.cone_all || uz >= sd.cos_alpha_f) {
-          float x0, y0;
-          launch_xy(pk, sid, key, sd.r_beam_f, x0, y0);
-          const float tx = ux * iuz, ty = uy * iuz;
-          const float ax = fmaf(tx, sd.z_probe_f, x0), ay = fmaf(ty, sd.z_probe_f, y0);
-          const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
-          const float fb = floorf((vapp - vcomp - sd.v_lo_f) * sd.inv_dbin_f);
-          const int idx = fb < 0.0f ? 0 : (fb >= (float)n_bins ? n_bins + 1 : (int)fb + 1);
-          for (int s = 0; s < n_snap; ++s) {
-            const float t = ts[s];
-            const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
-            if (sd.ap_all || fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
-              atomicAdd(&sd.hist[(size_t)s * row + idx], W);             // Eq. 19
-              atomicAdd(&sd.hist[(size_t)s * row + n_bins + 2], 1ull);
-              if (s < 64) dmask |= 1ull << s;
+    bool need_ar = false;
+    unsigned r_phi = 0;
+    if (alive) {
+      const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), k, sid), key);
+      // Step (3): one step along u and the optical depth of the layer crossed
+      const long long Pn = P + step_P(uz, (unsigned long long)sc.h_P);
+      const long long Pc = Pn < sc.P_fs ? sc.P_fs : (Pn > kOneP ? kOneP : Pn);
+      const bool horizontal = fabsf(uz) < 1e-9f;
+      float dtau;
+      em1 = 0.0f;
+      if (sc.expo) {
+        // Eq. 20 in closed form: with x = beta (v - v_fs) / v_fs the mass
+        // fraction between two heights is exp(-x0) (1 - exp(-(x1 - x0))) / E.
+        // exp(-x0) is carried from step to step (times exp(-dx)) and taken
+        // afresh after every event and every 64 steps.
+        if (!e0_ok || (k & 63u) == 0) {
+          e0 = expf(-sc.b_vfs * p_to_v(P, vP32));
+          e0_ok = true;
+        }
+        if (horizontal) {
+          dtau = sc.tau_f * sc.b_vfs * e0 * sc.invE * sc.h_v;
+        } else {
+          const float dx = sc.b_vfs * ((float)(int)((Pc - P) >> sc.shift_d) * vPd);
+          em1 = expm1_small(-dx);
+          dtau = sc.tau_f * e0 * fabsf(em1) * sc.invE / fabsf(uz);
+        }
+      } else if (horizontal) {
+        float d = 0.0f;
+        if (P > 0 && P < kOneP) {
+          const int j = (int)__umul64hi((unsigned long long)P << 2, (unsigned long long)sd.n_v);
+          d = u64_to_f(Sq[j + 1] - Sq[j]);
+        }
+        dtau = d * sc.tau_hv_dv;
+      } else {
+        const long long dS = mass_at(Sq, sd.n_v, Pc) - mass_at(Sq, sd.n_v, P);
+        dtau = u64_to_f((unsigned long long)(dS < 0 ? -dS : dS)) * sc.tau_S / fabsf(uz);
+      }
+      ++st_steps;
+      if (u23f(r.x) < expf(-dtau)) {
+        if (Pn >= kOneP - sc.eps_P) {
+          // Step (6): out through the top; vacuum flight to the probe plane
+          const float d = sd.v_top_f - vcur;
+          Xx = fmaf(ux * iuz, d, Xx);
+          Xy = fmaf(uy * iuz, d, Xy);
+          if (sd.cone_all || uz >= sd.cos_alpha_f) {
+            float x0, y0;
+            launch_xy(pk, sid, key, sd.r_beam_f, x0, y0);
+            const float tx = ux * iuz, ty = uy * iuz;
+            const float ax = fmaf(tx, sd.z_probe_f, x0), ay = fmaf(ty, sd.z_probe_f, y0);
+            const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
+            const float fb = floorf((vapp - vcomp - sd.v_lo_f) * sd.inv_dbin_f);
+            const int idx = fb < 0.0f ? 0 : (fb >= (float)n_bins ? n_bins + 1 : (int)fb + 1);
+            for (int s = 0; s < n_snap; ++s) {
+              const float t = ts[s];
+              const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
+              if (sd.ap_all || fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
+                atomicAdd(&sd.hist[(size_t)s * row + idx], W);             // Eq. 19
+                atomicAdd(&sd.hist[(size_t)s * row + n_bins + 2], 1ull);
+                if (s < 64) dmask |= 1ull << s;
+              }
             }
           }
-        }
-        atomicAdd(&s_cnt[C_ESCAPES], 1ull);
-        atomicAdd(&s_cnt[C_W_ESCAPED], W);
-        fate = 1;
-      } else if (Pn <= sc.P_fs + sc.eps_P) {
-        // Step (6): the free surface; reflectivity in 2^32 fixed point
-        const float d = sd.v_fs_f - vcur;
-        Xx = fmaf(ux * iuz, d, Xx);
-        Xy = fmaf(uy * iuz, d, Xy);
-        P = sc.P_fs;
-        vcur = sd.v_fs_f;
-        ++nev; ++nsurf; ++st_events; ++st_surf;
-        const unsigned long long Wn =
-            sd.R_q >= (1ull << 32) ? W : ((W * sd.R_q + (1ull << 31)) >> 32);
-        if (Wn != W) atomicAdd(&s_cnt[C_W_ABS_SURFACE], W - Wn);
-        W = Wn;
-        float nx, ny, nz;
-        if (sd.surface_mode == PDV_SURFACE_SPECULAR) {
-          nx = ux; ny = uy; nz = -uz;
-        } else {
-          float st, ct, sp, cp;
-          if (sd.surface_mode == PDV_SURFACE_LAMBERT) {
-            const float a = u23f(r.y);
-            ct = sqrtf(a);
-            st = sqrtf(1.0f - a);
+          atomicAdd(&s_cnt[C_ESCAPES], 1ull);
+          atomicAdd(&s_cnt[C_W_ESCAPED], W);
+          fate = 1;
+        } else if (Pn <= sc.P_fs + sc.eps_P) {
+          // Step (6): the free surface; reflectivity in 2^32 fixed point
+          const float d = sd.v_fs_f - vcur;
+          Xx = fmaf(ux * iuz, d, Xx);
+          Xy = fmaf(uy * iuz, d, Xy);
+          P = sc.P_fs;
+          vcur = sd.v_fs_f;
+          e0_ok = false;
+          ++nev; ++nsurf; ++st_events; ++st_surf;
+          const unsigned long long Wn =
+              sd.R_q >= (1ull << 32) ? W : ((W * sd.R_q + (1ull << 31)) >> 32);
+          if (Wn != W) atomicAdd(&s_cnt[C_W_ABS_SURFACE], W - Wn);
+          W = Wn;
+          float nx, ny, nz;
+          if (sd.surface_mode == PDV_SURFACE_SPECULAR) {
+            nx = ux; ny = uy; nz = -uz;
           } else {
-            sincospif(0.5f * u23f(r.y), &st, &ct);
+            float st, ct, sp, cp;
+            if (sd.surface_mode == PDV_SURFACE_LAMBERT) {
+              const float a = u23f(r.y);
+              ct = sqrtf(a);
+              st = sqrtf(1.0f - a);
+            } else {
+              sincospif(0.5f * u23f(r.y), &st, &ct);
+            }
+            sincospif(2.0f * u23f(r.z), &sp, &cp);
+            nx = st * cp; ny = st * sp; nz = ct;
+            const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+            nx *= inv_n; ny *= inv_n; nz *= inv_n;
           }
-          sincospif(2.0f * u23f(r.z), &sp, &cp);
-          nx = st * cp; ny = st * sp; nz = ct;
-          const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
-          nx *= inv_n; ny *= inv_n; nz *= inv_n;
+          kahan(vapp, vcomp, __fmul_rn(0.5f * (nz - uz), sd.v_fs_f));
+          ux = nx; uy = ny; uz = nz;
+          iuz = rcp_approx(nz);
+          if (W == 0) fate = 3;
+        } else {
+          // Step (5): passed the layer
+          P = Pn;
+          e0 = fmaf(e0, em1, e0);                                       // exp(-x) at Pn
+          vcur = p_to_v(Pn, vP32) + sd.v_bot_f;
+          Xx = fmaf(ux, sc.h_v, Xx);
+          Xy = fmaf(uy, sc.h_v, Xy);
         }
-        kahan(vapp, vcomp, __fmul_rn(0.5f * (nz - uz), sd.v_fs_f));
-        ux = nx; uy = ny; uz = nz;
-        iuz = rcp_approx(nz);
-        if (W == 0) fate = 3;
       } else {
-        // Step (5): passed the layer
-        P = Pn;
-        vcur = fmaf((float)Pn, sc.v_per_P, sd.v_bot_f);
-        Xx = fmaf(ux, sc.h_v, Xx);
-        Xy = fmaf(uy, sc.h_v, Xy);
-      }
-    } else {
-      // stopped in the layer: the interaction is at the end of the step
-      const float vn = Pc == sc.P_fs ? sd.v_fs_f : fmaf((float)Pc, sc.v_per_P, sd.v_bot_f);
-      if (horizontal) {
-        Xx = fmaf(ux, sc.h_v, Xx);
-        Xy = fmaf(uy, sc.h_v, Xy);
-      } else {
-        const float d = vn - vcur;
-        Xx = fmaf(ux * iuz, d, Xx);
-        Xy = fmaf(uy * iuz, d, Xy);
-      }
-      P = Pc;
-      vcur = vn;
-      ++nev; ++st_events;
-      if ((r.y >> 8) < sd.omega_q) {
-        // Step (4): scattered; the polar angle by acceptance-rejection
-        const float ct = ar_cos(pk, k, key2, pn, thpi, sd.n_p, sd.phase_uniform, sd.inv_nm1);
-        const float st = sqrtf(fmaxf(0.0f, fmaf(-ct, ct, 1.0f)));
-        float sp, cp;
-        sincospif(2.0f * u23f(r.w), &sp, &cp);                         // Eq. 15
-        float nx, ny, nz;
-        if (fabsf(uz) > 1.0f - 1e-6f) {                                // Eq. 17
-          nx = st * cp;
-          ny = st * sp;
-          nz = uz >= 0.0f ? ct : -ct;
-        } else {                                                       // Eq. 16
-          const float h2 = fmaf(ux, ux, uy * uy);
-          const float rs = rsqrtf(h2);
-          const float s = h2 * rs;
-          const float a = st * rs;
-          nx = fmaf(a, fmaf(ux * uz, cp, -uy * sp), ux * ct);
-          ny = fmaf(a, fmaf(uy * uz, cp, ux * sp), uy * ct);
-          nz = fmaf(-st * cp, s, uz * ct);
+        // stopped in the layer: the interaction is at the end of the step
+        const float vn = Pc == sc.P_fs ? sd.v_fs_f : p_to_v(Pc, vP32) + sd.v_bot_f;
+        if (horizontal) {
+          Xx = fmaf(ux, sc.h_v, Xx);
+          Xy = fmaf(uy, sc.h_v, Xy);
+        } else {
+          const float d = vn - vcur;
+          Xx = fmaf(ux * iuz, d, Xx);
+          Xy = fmaf(uy * iuz, d, Xy);
         }
-        const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
-        nx *= inv_n; ny *= inv_n; nz *= inv_n;
-        kahan(vapp, vcomp, __fmul_rn(0.5f * (nz - uz), vn));        // Eq. 4 / Eq. 18
-        ux = nx; uy = ny; uz = nz;
-        iuz = rcp_approx(nz);
-        ++nsca; ++st_scat;
-      } else {
-        atomicAdd(&s_cnt[C_W_ABS_PARTICLE], W);                         // Eq. 11: absorbed
-        fate = 2;
+        P = Pc;
+        vcur = vn;
+        e0_ok = false;
+        ++nev; ++st_events;
+        if ((r.y >> 8) < sd.omega_q) {
+          need_ar = true;                                                 // Step (4): scattered
+          r_phi = r.w;
+        } else {
+          atomicAdd(&s_cnt[C_W_ABS_PARTICLE], W);                         // Eq. 11: absorbed
+          fate = 2;
+        }
       }
+    }   // alive
+    // the scattered lanes' polar angles, one lane at a time by the whole warp
+    unsigned want = __ballot_sync(kFullS, need_ar);
+    float my_ct = 0.0f;
+    while (want) {
+      const int src = __ffs(want) - 1;
+      want &= want - 1;
+      const unsigned long long spk = __shfl_sync(kFullS, pk, src);
+      const unsigned sk = __shfl_sync(kFullS, k, src);
+      const float c = ar_cos_warp(spk, sk, key2, pn, thpi, sd.n_p, sd.phase_uniform, sd.inv_nm1,
+                                  lane);
+      if (lane == src) my_ct = c;
+    }
+    if (!alive) continue;
+    if (need_ar) {
+      const float ct = my_ct;
+      const float st = sqrtf(fmaxf(0.0f, fmaf(-ct, ct, 1.0f)));
+      float sp, cp;
+      sincospif(2.0f * u23f(r_phi), &sp, &cp);                         // Eq. 15
+      float nx, ny, nz;
+      if (fabsf(uz) > 1.0f - 1e-6f) {                                // Eq. 17
+        nx = st * cp;
+        ny = st * sp;
+        nz = uz >= 0.0f ? ct : -ct;
+      } else {                                                       // Eq. 16
+        const float h2 = fmaf(ux, ux, uy * uy);
+        const float rs = rsqrtf(h2);
+        const float s = h2 * rs;
+        const float a = st * rs;
+        nx = fmaf(a, fmaf(ux * uz, cp, -uy * sp), ux * ct);
+        ny = fmaf(a, fmaf(uy * uz, cp, ux * sp), uy * ct);
+        nz = fmaf(-st * cp, s, uz * ct);
+      }
+      const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+      nx *= inv_n; ny *= inv_n; nz *= inv_n;
+      kahan(vapp, vcomp, __fmul_rn(0.5f * (nz - uz), vcur));      // Eq. 4 / Eq. 18
+      ux = nx; uy = ny; uz = nz;
+      iuz = rcp_approx(nz);
+      ++nsca; ++st_scat;
     }
     if (fate == 0 && k >= sd.max_events) {
       atomicAdd(&s_cnt[C_W_TRUNCATED], W);

@@ -26,6 +26,7 @@ struct StepConst {
   float b_vfs;             // beta / v_fs
   float invE;              // 1 / (1 - exp(-beta (v_top / v_fs - 1)))
   float tau_f;             // tau_tot
+  int shift_d;             // dP >> shift_d fits 31 bits for a whole step
 };
 
 // Shared-memory bytes of the stepping kernel for a set.
