@@ -735,6 +735,20 @@ def stepping_mode(args):
     O.simulate(wl, n_packets=m, n_threads=os.cpu_count())
     t_cpu = time.perf_counter() - t0
     paper_photons_per_s = 1e7 / 500.0                  # GTX960, Section II.D
+    # issue-rate roofline of the stepping kernel: algorithmic work per step is
+    # one Philox4x32-10 call (64), the Bernoulli exponential (10), the layer
+    # mass of Eq. 20 (16) and the step itself (20): 110 thread-instructions
+    a_step = 110.0
+    sm = torch.cuda.get_device_properties(0).multi_processor_count if torch.cuda.is_available() else 152
+    issue_peak = sm * 4 * 32 * 2.07e9
+    achieved = a_step * out["stepping"]["steps_per_s"]
+    prof = None
+    pp = os.path.join(ROOT, "profiles", "transport_step_counters.json")
+    if os.path.exists(pp):
+        d = json.load(open(pp))
+        src = open(os.path.join(ROOT, "paper_2012_00963_gb300", "csrc", "stepping.cu"), "rb").read()
+        if d.get("source_hash") == hashlib.sha1(src).hexdigest()[:12]:
+            prof = d
     line = {
         "mode": "stepping",
         "metric": "photons/s of the paper's layer-stepping scheme (1000 layers), 1e7-photon spectrum",
@@ -745,6 +759,12 @@ def stepping_mode(args):
         "exact_over_stepping_speed": out["exact"]["photons_per_s"] / out["stepping"]["photons_per_s"],
         "spectrum_chi2_per_bin_stepping_vs_exact": chi2,
         "mean_v_app_shift_m_s": out["stepping"]["mean_v_app_detected"] - out["exact"]["mean_v_app_detected"],
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": issue_peak / 1e9,
+                     "unit": "Ginst/s", "frac": achieved / issue_peak,
+                     "traffic": prof["dram_bytes_per_step"] * out["stepping"]["steps"] if prof else None,
+                     "kernel": "k_transport_step", "algo_inst_per_step": a_step,
+                     "peak_basis": "%d SM x 4 schedulers x 32 lanes x 2070 MHz (issue rate)" % sm},
+        "gpu_launches": 1,
         "tau_tot": info["tau_tot"], "dtype": "f32", "data": "synthetic (seeded)",
         "cpu_baseline": {"value": m / t_cpu, "unit": "photons/s", "cores": os.cpu_count(),
                          "kind": "oracle", "sample": "%d photons of the same workload, layer stepping" % m},
