@@ -58,7 +58,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mode", default="default",
                     choices=["default", "serve", "batch", "precision", "model", "extract-mc",
-                             "stepping"])
+                             "stepping", "spectrogram"])
+    ap.add_argument("--times", type=int, default=512, help="snapshot times of the spectrogram mode")
+    ap.add_argument("--out", default="", help="spectrogram mode: write the v-t image (PGM) here")
     ap.add_argument("--model-sets", type=int, default=100_000,
                     help="parameter sets / spectra of the model mode")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
@@ -775,6 +777,51 @@ def stepping_mode(args):
     return 0
 
 
+def spectrogram_mode(args):
+    """A v-t spectrogram of the 50-snapshot workload's cloud at --times
+    snapshot times (one transport serves every time), device-resident."""
+    import numpy as np
+    import torch
+    from paper_2012_00963_gb300 import pdv
+    from paper_2012_00963_gb300 import spectrogram as S
+    from paper_2012_00963_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = pdv.Context(0, stream=stream.cuda_stream)
+    n = int(args.packets)
+    t = np.linspace(0.5e-6, 5e-6, args.times)
+    wl = W.cfg2(n_packets=n)
+    cloud = pdv.Cloud(ctx, wl)
+    S.spectrogram(ctx, cloud, wl, t[:4])                        # warm-up
+    clocks = Clocks(0)
+    clocks.start()
+    ms, kms = [], []
+    for _ in range(max(1, args.steps)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sg = S.spectrogram(ctx, cloud, wl, t)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+        kms.append(ctx.stats()["last_transport_ms"])
+    clk = clocks.stop()
+    c = pdv.counters_dict(sg["counters"][0])
+    if args.out:
+        S.write_pgm(args.out, sg["image"])
+    cloud.close()
+    ctx.close()
+    mean = statistics.mean(ms)
+    print(json.dumps({
+        "mode": "spectrogram", "metric": "spectra/s of a v-t spectrogram (one transport, every time)",
+        "value": args.times / (mean / 1e3), "unit": "spectra/s", "ms_per_image": mean,
+        "kernel_ms": statistics.mean(kms), "scatter_events_per_s": c["scatters"] / (mean / 1e3),
+        "times": args.times, "packets": n, "gpu_launches": 2, "dtype": "f32",
+        "config": {"workload": "cfg2 cloud (log-normal Mie 3+9i, 5 mg/cm^2, beta 5), %d snapshot times "
+                               "0.5-5 us, %d packets, 600 bins, aperture 1 mm / 0.1 rad" % (args.times, n)},
+        "clocks": clk}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -791,6 +838,8 @@ def main():
         return extract_mc_mode(args)
     if args.mode == "stepping":
         return stepping_mode(args)
+    if args.mode == "spectrogram":
+        return spectrogram_mode(args)
     return our_arm(args)
 
 
