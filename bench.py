@@ -363,7 +363,7 @@ def serving_run(ctx, seconds, rate):
     from paper_2012_00963_gb300 import workloads as W
     g = np.load(os.path.join(ROOT, "tests", "golden", "serving_target.npz"))
     target = g["hist"][0].astype(np.float64) / 2.0**32
-    probe = dict(r_ap=3.0 * W.MM, cone_alpha=0.5)
+    probe = dict(r_ap=0.0, cone_alpha=math.pi / 2)       # every upward photon, as the target
     res = serving.run_sweep(ctx, target, int(g["n_packets"]), probe, duration=seconds, rate=rate)
     hidden = {"beta": 6.0, "m0": 3.0 * W.MG_CM2, "d_m": 2.0 * W.UM, "tau0": float(g["tau_tot"])}
     return serving.summary(res, hidden)
@@ -383,7 +383,7 @@ def serve_mode(args):
             "unit": "ms", "rate_per_s": args.rate, "seconds": args.serve_seconds,
             "config": {"workload": "cfg5: Poisson stream of fit candidates (beta, m0, d), HG "
                                    "g=0.7 albedo 0.6, 400 bins 0-8000 m/s, 1e5-1e7 packets per "
-                                   "request, aperture 3 mm, cone 0.5 rad"},
+                                   "request, every upward photon counted"},
             "clocks": clk}
     line.update(out)
     print(json.dumps(line))

@@ -6,12 +6,14 @@ Calls only the FP64 oracle (oracle/). Run from the repository root:
 
 * serving_target.npz — the synthetic "measured" spectrum that the serving
   benchmark fits: the served request shape (HG g = 0.7, albedo 0.6,
-  Q_ext = 2, 400 bins over 0-8000 m/s, t = 1 us) with the hidden parameters
-  beta = 6, m0 = 3 mg/cm^2, d = 2 um, 1e7 packets (seed 77).
+  Q_ext = 2, 400 bins over 0-8000 m/s, t = 1 us, every upward photon
+  counted as the paper does) with the hidden parameters beta = 6,
+  m0 = 3 mg/cm^2, d = 2 um, 1e7 packets (seed 77).
 * precision_cfg3.npz — the heavy multiple-scattering cloud (20 mg/cm^2 of
   1 um tin, beta = 3, Mie m = 3 + 9i) at 1e7 packets (seed 3): the reference
   for the per-bin error of the GPU paths.
 """
+import math
 import os
 import sys
 import time
@@ -26,7 +28,7 @@ from oracle import oracle as O  # noqa: E402
 from paper_2012_00963_gb300 import workloads as W  # noqa: E402
 
 SERVING_HIDDEN = dict(beta=6.0, m0=3.0 * W.MG_CM2, d_m=2.0 * W.UM)
-SERVING_PROBE = dict(r_ap=3.0 * W.MM, cone_alpha=0.5)
+SERVING_PROBE = dict(r_ap=0.0, cone_alpha=math.pi / 2)     # every upward photon (Eq. 19)
 
 
 def serving_workload(beta, m0, d_m, n_packets, seed):
