@@ -18,6 +18,9 @@
  *     particle scatterings and free-surface reflections (Eq. 4 and Eq. 18 with
  *     the sign that makes an approaching scatterer blueshift);
  *   - the spectrum counts escaping packets by apparent velocity (Eq. 19).
+ * With n_layers > 0 the paper's own scheme runs instead (orc_transport_stepped:
+ * steps of H / n_layers with a Bernoulli pass per layer, acceptance-rejection
+ * angles), with the readings stated there.
  */
 #define _GNU_SOURCE
 #include "pdv_oracle.h"

@@ -259,3 +259,42 @@ def test_extract_recovers_model_parameters_on_gpu(ctx):
         assert int(g["status"]) == pdv.PDV_PEAK_OK
         assert g["beta"] == pytest.approx(p[0], rel=5e-3)
         assert g["tau0"] == pytest.approx(p[1], rel=1.5e-2)
+
+
+def test_bench_size_sampled():
+    """At the measured size (1e5 sets / spectra of 600 bins, the launch
+    configuration bench.py times), sampled outputs against the oracle one by
+    one. The extraction inputs come from a seeded generator, not from the
+    CUDA path."""
+    torch = pytest.importorskip("torch")
+    from paper_2012_00963_gb300 import workloads as W
+    ctx = pdv.Context(0)
+    try:
+        n, nb = 100_000, 600
+        sets = W.model_sets(n)
+        d_sets = torch.tensor(sets, device="cuda")
+        d_out = torch.empty(n * nb, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        pdv.pdv_ss_spectrum(ctx.handle, d_sets, n, nb, 0.0, 8000.0, d_out, per_dv=True)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(8)
+        for i in rng.choice(n, 12, replace=False):
+            b, t, vf, vm, P = sets[i]
+            g = d_out[i * nb:(i + 1) * nb].cpu().numpy()
+            assert_bins_close(g, O.ss_spectrum_bins(b, t, vf, nb, 0.0, 8000.0, prefactor=P,
+                                                    per_dv=True))
+        j0 = rng.uniform(170.0, 330.0, n)
+        width = rng.uniform(8.0, 25.0, n)
+        jj = np.arange(nb)[None, :]
+        z = np.clip((jj - j0[:, None] + 3 * width[:, None]) / width[:, None], 0.0, None)
+        spec = z ** 3 * np.exp(-z) * (1.0 + 0.02 * rng.standard_normal((n, nb)))
+        d_in = torch.tensor(spec, device="cuda")
+        d_pk = torch.zeros(n * pdv.PEAK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        pdv.pdv_extract_peaks(ctx.handle, d_in, n, nb, 0.0, 8000.0, 2000.0, 40, 1.02, 3.5, d_pk)
+        torch.cuda.synchronize()
+        got = np.frombuffer(d_pk.cpu().numpy().tobytes(), dtype=pdv.PEAK_DTYPE)
+        for i in rng.choice(n, 40, replace=False):
+            compare_peak(got[i], O.extract_peak(spec[i], 0.0, 8000.0, 2000.0, 40, 1.02, 3.5))
+    finally:
+        ctx.close()

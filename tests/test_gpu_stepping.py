@@ -130,3 +130,42 @@ def test_invalid_combinations(ctx):
             pdv.pdv_simulate_spectrum(ctx.handle, req.c)
     finally:
         cloud.close()
+
+
+def test_full_size_fig4_sampled_packets(ctx):
+    """The measured workload (Fig. 4 cloud, 1e7 photons x 1000 layers) in the
+    launch bench.py times, with packet records dumped to device memory;
+    2000 packets from three places in the range against the oracle."""
+    torch = pytest.importorskip("torch")
+    wl = W.fig4()
+    n = wl.n_packets
+    cloud = pdv.Cloud(ctx, wl)
+    try:
+        dev = {"spectrum": torch.zeros(wl.n_bins, dtype=torch.float64, device="cuda"),
+               "raw": torch.zeros(wl.n_bins + 2, dtype=torch.int64, device="cuda"),
+               "counters": torch.zeros(14, dtype=torch.int64, device="cuda"),
+               "packets": torch.zeros(n * pdv.PACKET_DTYPE.itemsize, dtype=torch.uint8,
+                                      device="cuda")}
+        req = pdv.Request(cloud, wl, device_out=dev)
+        req.c.out_packets = dev["packets"].data_ptr()
+        torch.cuda.synchronize()
+        pdv.pdv_simulate_spectrum(ctx.handle, req.c)
+        torch.cuda.synchronize()
+        cnt = dev["counters"].cpu().numpy().astype(np.uint64)
+        assert conserved(cnt)
+        table = O.phase_table(wl)
+        same = tot = 0
+        for begin in (0, n // 2, n - 700):
+            m = 700 if begin == n - 700 else 650
+            g = np.frombuffer(dev["packets"][begin * pdv.PACKET_DTYPE.itemsize:
+                                             (begin + m) * pdv.PACKET_DTYPE.itemsize]
+                              .cpu().numpy().tobytes(), dtype=pdv.PACKET_DTYPE)
+            o = O.simulate(wl, n_packets=m, packet_begin=begin, packets=True, table=table)["packets"]
+            eq = g["n_events"] == o["n_events"]
+            same += int(eq.sum())
+            tot += m
+            err = np.abs(g["v_app"] - o["v_app"]) / np.maximum(np.abs(o["v_app"]), wl.v_fs)
+            assert (err[eq] <= 1e-5).mean() >= 0.998
+        assert same / tot >= 0.999, same / tot
+    finally:
+        cloud.close()
