@@ -77,6 +77,15 @@ def workload(args, rank=0):
     return W.cfg2(n_packets=int(args.packets), t_snap=t, seed=2 + 1000 * rank)
 
 
+def reduce_max(values, world):
+    """Element-wise maximum over ranks of a float64 tensor (the slowest rank's
+    times set the whole job's rate); identity on one process."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(values, op=dist.ReduceOp.MAX)
+    return values
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -289,9 +298,7 @@ def our_arm(args):
 
     vals = torch.tensor([total_s, sum(e_ms) / 1e3, sum(f_ms) / 1e3], dtype=torch.float64,
                         device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
-    total_s, e_s, f_s = [float(x) for x in vals.cpu()]
+    total_s, e_s, f_s = [float(x) for x in reduce_max(vals, world).cpu()]
     steps = args.steps
     value = world * scat * steps / total_s
     spectra = world * ns * steps / total_s
