@@ -187,7 +187,10 @@ typedef struct {
  * allocator. On error *out is NULL. */
 pdv_status pdv_ctx_create(int device, void* cuda_stream, const pdv_allocator* alloc,
                           pdv_ctx** out);
-/* Waits for the context's work, stops the serving thread, frees everything. */
+/* Waits for the context's work, stops the serving thread, frees everything.
+ * Destroy every cloud made on the context (pdv_destroy_cloud) first: device
+ * memory comes from the context's own stream-ordered pool, which keeps up to
+ * 2 GiB of freed memory mapped between calls and is released here. */
 pdv_status pdv_ctx_destroy(pdv_ctx* ctx);
 const char* pdv_last_error(void);
 pdv_status pdv_get_stats(pdv_ctx* ctx, pdv_stats* out);

@@ -60,12 +60,18 @@ extern "C" const char* pdv_last_error(void) { return g_err.c_str(); }
 // ------------------------------------------------------------------ objects
 struct Request;  // serving
 
+constexpr unsigned long long kPoolKeep = 2ull << 30;   // bytes a context's pool keeps mapped
+
 struct pdv_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   pdv_allocator alloc{};
   bool has_alloc = false;
+  // the context's own stream-ordered pool: it keeps up to kPoolKeep bytes of
+  // freed memory mapped across synchronisations, so per-call allocations do
+  // not map fresh memory each time (the default pool releases at every sync)
+  cudaMemPool_t pool = nullptr;
   int sm_count = 0;
   int max_smem = 0;
   pdv_tuning tuning{};
@@ -156,7 +162,9 @@ static void* ctx_alloc(pdv_ctx* c, size_t bytes, cudaStream_t st) {
   if (bytes == 0) bytes = 16;
   if (c->has_alloc) return c->alloc.alloc(bytes, (void*)st, c->alloc.user);
   void* p = nullptr;
-  if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+  const cudaError_t e = c->pool ? cudaMallocFromPoolAsync(&p, bytes, c->pool, st)
+                                : cudaMallocAsync(&p, bytes, st);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
@@ -207,6 +215,19 @@ extern "C" pdv_status pdv_ctx_create(int device, void* cuda_stream, const pdv_al
     c->alloc = *alloc;
     c->has_alloc = true;
   }
+  if (!c->has_alloc) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&c->pool, &props) == cudaSuccess) {
+      unsigned long long keep = kPoolKeep;      // a cuuint64_t attribute
+      cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      cudaGetLastError();
+      c->pool = nullptr;                 // fall back to the device's default pool
+    }
+  }
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   c->max_smem = transport_f32_max_smem();
   c->tuning.block_threads = 256;
@@ -234,6 +255,8 @@ extern "C" pdv_status pdv_ctx_destroy(pdv_ctx* c) {
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream) cudaStreamDestroy(c->stream);
+  // released once its last allocation is freed (clouds are destroyed first)
+  if (c->pool) cudaMemPoolDestroy(c->pool);
   delete c;
   return PDV_OK;
 }
