@@ -412,7 +412,7 @@ __host__ __device__ inline TileSmem tile_layout(int k2p) {
   TileSmem L;
   L.o_a = 0;
   L.o_b = L.o_a + sizeof(float) * kJC * kAS;
-  L.o_c = L.o_b + sizeof(float) * kJC * kNT;
+  L.o_c = L.o_b + 2 * sizeof(float) * kJC * kNT;           // two buffers
   L.o_red = L.o_c + sizeof(float) * (size_t)k2p * kAS;
   L.bytes = L.o_red + (sizeof(float) + sizeof(int)) * kTS;
   return L;
@@ -498,6 +498,26 @@ __device__ __forceinline__ void tile_smooth_eval(const float2* tw, const float* 
   *s2 = a2;
 }
 
+// 16-byte global-to-shared copies that bypass registers (cp.async, .cg: L2 only).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// One kJC x kNT chunk of a row-major matrix (row stride `ld` floats) into a
+// shared buffer, 16 bytes per copy: 768 copies, three per thread.
+__device__ __forceinline__ void load_chunk_async(float* dst, const float* src, size_t ld,
+                                                 int tid) {
+#pragma unroll
+  for (int u = 0; u < kJC * kNT / 4 / 256; ++u) {
+    const int e = tid + u * 256, r = e / (kNT / 4), c4 = e % (kNT / 4);
+    cp_async16(dst + 4 * e, src + (size_t)r * ld + 4 * c4);
+  }
+  cp_async_commit();
+}
+
 __global__ void __launch_bounds__(256, 3) k_extract_tiled(
     const double* spec, int n_spec, int n, int k_c, int j_lo, int j_hi, PeakGeom geom,
     const float2* tw, const float* F, const float* G, int n_p, int k2p, int nw_p, pdv_peak* out) {
@@ -522,35 +542,35 @@ __global__ void __launch_bounds__(256, 3) k_extract_tiled(
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int c = 0; c < 6; ++c) acc[i][c] = 0.0f;
-      // the next chunk's operands are loaded into registers while this one
-      // is multiplied (256 threads: 8 spectrum values and 12 F values each)
-      // (lane = bin within the chunk, warp + 8 u = spectrum; float4 columns of F)
+      // the next chunk is in flight while this one is multiplied: F by
+      // cp.async into the other shared buffer, the spectra (converted to FP32
+      // on the way) through registers (lane = bin of the chunk, warp + 8 u =
+      // spectrum)
       float pa[kTS / 8];
-      float4 pb[kJC * kNT / 4 / 256];
-      auto fetch = [&](int j0) {
+      auto fetch_a = [&](int j0) {
         const int gj = j0 + lane;
 #pragma unroll
         for (int u = 0; u < kTS / 8; ++u) {
           const int gs = s0 + warp + 8 * u;
           pa[u] = (gs < n_spec && gj < n) ? f64_to_f32(spec[(size_t)gs * n + gj]) : 0.0f;
         }
-#pragma unroll
-        for (int u = 0; u < kJC * kNT / 4 / 256; ++u) {
-          const int e = tid + u * 256, j = e / (kNT / 4), c4 = e % (kNT / 4);
-          pb[u] = *reinterpret_cast<const float4*>(F + (size_t)(j0 + j) * k2p + cp + 4 * c4);
-        }
       };
-      fetch(0);
-      for (int j0 = 0; j0 < n_p; j0 += kJC) {
-        __syncthreads();
+      fetch_a(0);
+      __syncthreads();                               // B buffers free (previous users done)
+      load_chunk_async(Bs, F + cp, (size_t)k2p, tid);
+      for (int j0 = 0, c = 0; j0 < n_p; j0 += kJC, ++c) {
+        float* Bc = Bs + (c & 1) * (kJC * kNT);
+        __syncthreads();                             // previous chunk's products done
 #pragma unroll
         for (int u = 0; u < kTS / 8; ++u) As[lane * kAS + warp + 8 * u] = pa[u];
-#pragma unroll
-        for (int u = 0; u < kJC * kNT / 4 / 256; ++u)
-          reinterpret_cast<float4*>(Bs)[tid + u * 256] = pb[u];
-        __syncthreads();
-        if (j0 + kJC < n_p) fetch(j0 + kJC);
-        tile_fma(As, Bs, kJC, ty, tx, acc);
+        cp_async_wait_all();
+        __syncthreads();                             // As and this chunk of F visible
+        if (j0 + kJC < n_p) {
+          load_chunk_async(Bs + ((c + 1) & 1) * (kJC * kNT), F + (size_t)(j0 + kJC) * k2p + cp,
+                           (size_t)k2p, tid);
+          fetch_a(j0 + kJC);
+        }
+        tile_fma(As, Bc, kJC, ty, tx, acc);
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
@@ -565,31 +585,44 @@ __global__ void __launch_bounds__(256, 3) k_extract_tiled(
       best[i] = -INFINITY;
       bj[i] = 0x7fffffff;
     }
-    for (int wp = 0; wp < nw_p; wp += kNT) {
+    // chunks run column tile by column tile, the next chunk of G copied into
+    // the other shared buffer (cp.async) while this one is multiplied
+    {
+      const int nr = k2p / kJC, nchunks = nr * (nw_p / kNT);
+      auto g_src = [&](int ch) {
+        return G + (size_t)((ch % nr) * kJC) * nw_p + (ch / nr) * kNT;
+      };
       float acc[4][6];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int c = 0; c < 6; ++c) acc[i][c] = 0.0f;
-      for (int r0 = 0; r0 < k2p; r0 += kJC) {
-        __syncthreads();
-        for (int e = tid; e < kJC * kNT; e += blockDim.x) {
-          const int r = e / kNT, c = e % kNT;
-          Bs[e] = G[(size_t)(r0 + r) * nw_p + wp + c];
-        }
-        __syncthreads();
-        tile_fma(Cs + r0 * kAS, Bs, kJC, ty, tx, acc);
-      }
+      __syncthreads();                               // B buffers free
+      if (nchunks) load_chunk_async(Bs, g_src(0), (size_t)nw_p, tid);
+      for (int ch = 0; ch < nchunks; ++ch) {
+        cp_async_wait_all();
+        __syncthreads();                             // this chunk visible; the other buffer free
+        if (ch + 1 < nchunks)
+          load_chunk_async(Bs + ((ch + 1) & 1) * (kJC * kNT), g_src(ch + 1), (size_t)nw_p, tid);
+        tile_fma(Cs + (ch % nr) * kJC * kAS, Bs + (ch & 1) * (kJC * kNT), kJC, ty, tx, acc);
+        if (ch % nr == nr - 1) {
+          const int wp = (ch / nr) * kNT;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const int j = wp + tx * 6 + c;
-        if (j < n_w) {
+          for (int c = 0; c < 6; ++c) {
+            const int j = wp + tx * 6 + c;
+            if (j < n_w) {
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                if (acc[i][c] > best[i]) {
+                  best[i] = acc[i][c];
+                  bj[i] = j_lo + j;
+                }
+            }
+          }
 #pragma unroll
           for (int i = 0; i < 4; ++i)
-            if (acc[i][c] > best[i]) {
-              best[i] = acc[i][c];
-              bj[i] = j_lo + j;
-            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc[i][c] = 0.0f;
         }
       }
     }
