@@ -348,9 +348,11 @@ def ss_spectrum(ctx: "Context", params, n_bins: int, v_lo: float, v_hi: float,
     arr = np.zeros(len(params), dtype=SS_SET_DTYPE)
     for i, p in enumerate(params):
         if isinstance(p, dict):
-            arr[i] = (p["beta"], p["tau0"], p["v_fs"], p.get("v_max", 0.0), p.get("prefactor", 1.0))
-        else:
-            arr[i] = tuple(p) + (0.0, 1.0)[len(p) - 3:] if len(p) < 5 else tuple(p)
+            p = (p["beta"], p["tau0"], p["v_fs"], p.get("v_max", 0.0), p.get("prefactor", 1.0))
+        p = tuple(p)
+        if not 3 <= len(p) <= 5:
+            raise ValueError("a set is (beta, tau0, v_fs[, v_max[, prefactor]])")
+        arr[i] = p + (0.0, 1.0)[len(p) - 3:]       # defaults: untruncated, unit prefactor
     out = np.zeros(len(params) * n_bins)
     pdv_ss_spectrum(ctx.handle, arr, len(params), n_bins, v_lo, v_hi, out, per_dv)
     return out.reshape(len(params), n_bins)
