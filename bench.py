@@ -373,7 +373,35 @@ def serving_run(ctx, seconds, rate):
     probe = dict(r_ap=0.0, cone_alpha=math.pi / 2)       # every upward photon, as the target
     res = serving.run_sweep(ctx, target, int(g["n_packets"]), probe, duration=seconds, rate=rate)
     hidden = {"beta": 6.0, "m0": 3.0 * W.MG_CM2, "d_m": 2.0 * W.UM, "tau0": float(g["tau_tot"])}
-    return serving.summary(res, hidden)
+    out = serving.summary(res, hidden)
+    out["capacity"] = serving_capacity(ctx, probe)
+    return out
+
+
+def serving_capacity(ctx, probe, n=64):
+    """Spectra/s one GPU sustains on the served request mix (the first n
+    arrivals of the stream) when each request runs alone on the FP32 path and
+    on the plain FP64 path: both draw the same random numbers, so this is the
+    comparison at equal spectrum error."""
+    import torch
+    from paper_2012_00963_gb300 import pdv
+    from paper_2012_00963_gb300 import workloads as W
+    arr = W.cfg5_arrivals()[:n]
+    wls = [W.cfg5_request(a, **probe) for a in arr]
+    clouds = [pdv.Cloud(ctx, w) for w in wls]
+    out = {}
+    for prec in ("fp32", "fp64"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c, w in zip(clouds, wls):
+            pdv.simulate_spectrum(ctx, c, w, precision=prec, raw=False)
+        out[prec + "_spectra_per_s"] = n / (time.perf_counter() - t0)
+    for c in clouds:
+        c.close()
+    out["ratio_fp32_over_fp64"] = out["fp32_spectra_per_s"] / out["fp64_spectra_per_s"]
+    out["requests"] = n
+    out["packets"] = int(sum(w.n_packets for w in wls))
+    return out
 
 
 def serve_mode(args):
@@ -429,10 +457,21 @@ def batch_mode(args):
     clk = clocks.stop()
     tot = sum(times) / 1e3
     n_packets = sum(w.n_packets for w in sets)
+    # the same sets through the plain FP64 path, one request at a time (the two
+    # paths draw the same random numbers: equal spectrum error)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for c, w in zip(clouds, sets):
+        pdv.simulate_spectrum(ctx, c, w, precision="fp64", raw=False)
+    b.record(stream)
+    b.synchronize()
+    fp64_s = a.elapsed_time(b) / 1e3
     line = {"mode": "batch", "metric": "batched spectra/s", "value": len(sets) * args.steps / tot,
             "unit": "spectra/s", "scatter_events_per_s": scat / tot, "events_per_s": ev / tot,
             "ms_per_launch": 1e3 * tot / args.steps, "kernel_ms": statistics.mean(kern),
             "packets_per_launch": n_packets, "sets": len(sets), "tuning": tuning,
+            "fp64_plain": {"spectra_per_s": len(sets) / fp64_s, "seconds": fp64_s},
+            "speedup_vs_fp64_plain": (len(sets) * args.steps / tot) / (len(sets) / fp64_s),
             "gpu_launches_per_step": 2,
             "config": {"workload": "cfg4: %d sets, beta U(2,10), m0 logU(0.1,20) mg/cm^2, d "
                                    "logU(0.5,10) um Mie 3+9i, v_fs U(1.5,3) km/s, t U(1,4) us, "
