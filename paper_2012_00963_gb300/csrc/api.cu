@@ -738,6 +738,7 @@ static pdv_status enqueue_transport(pdv_ctx* c, const pdv_request* r, const SetD
     sc.tau_f = (float)cl->tau_tot;
     sc.shift_d = 0;
     while ((sc.h_P >> sc.shift_d) >= (1ll << 30)) ++sc.shift_d;
+    sc.ff = sc.h_P <= (1ll << 56) ? 1 : 0;
     if (sc.P_fs < -(1ll << 62))
       return fail(PDV_EINVAL, "layer stepping needs the cloud to start within one cloud height of the free surface");
     const size_t smem = transport_step_smem(d.n_v, d.n_p, d.n_snap, d.phase_uniform);

@@ -20,6 +20,17 @@
 // layer optical depth tau_tot dS / |u_z| carries neither cancellation nor the
 // table's interpolation error.
 //
+// Scheduling: one photon per lane, claimed one at a time. A step's decision is
+// a pure function of (height, direction, step index), and nothing else
+// changes while a photon passes layers (the lateral shift of a run of passed
+// layers is taken when the run ends). So once a photon has passed a few
+// layers in a row, the whole warp moves it on 32 steps per round, one lane
+// per step, up to the step that ends the run; the photon's lane then takes
+// that step itself. The histories are the ones the step-by-step loop makes,
+// bit for bit, whatever the schedule, and the near-horizontal photons that
+// wander high in the thin top of the cloud for up to 1e6 steps no longer
+// hold the launch open one step per iteration.
+//
 // Random numbers: step k of packet p draws Philox4x32-10 with counter
 // (p, k, stream) under the request's seed (k = 0 is the launch): word 0 the
 // Bernoulli trial, word 1 scatter/absorb (24-bit) or the surface polar angle,
@@ -151,6 +162,76 @@ __device__ __forceinline__ void kahan(float& sum, float& comp, float term) {
   sum = t;
 }
 
+// Section II.B steps (2)-(3) for one step of a photon at height P moving with
+// u_z: the step's end Pn, that end inside the cloud Pc, and whether the photon
+// passes the layer it crossed (the Bernoulli trial on word rx of its draw).
+// A pure function of (P, u_z, rx), so the per-lane loop and the warp's
+// fast-forward below take identical decisions from it.
+__device__ __forceinline__ bool step_passes(const StepConst& sc, const unsigned long long* Sq,
+                                            int n_v, float vP32, float vPd, long long P, float uz,
+                                            unsigned rx, long long& Pn, long long& Pc) {
+  Pn = P + step_P(uz, (unsigned long long)sc.h_P);
+  Pc = Pn < sc.P_fs ? sc.P_fs : (Pn > kOneP ? kOneP : Pn);
+  const bool horizontal = fabsf(uz) < 1e-9f;
+  float dtau;
+  if (sc.expo) {
+    // Eq. 20 in closed form: with x = beta (v - v_fs) / v_fs the mass
+    // fraction between two heights is exp(-x0) (1 - exp(-(x1 - x0))) / E
+    const float e0 = expf(-sc.b_vfs * p_to_v(P, vP32));
+    if (horizontal) {
+      dtau = sc.tau_f * sc.b_vfs * e0 * sc.invE * sc.h_v;
+    } else {
+      const float dx = sc.b_vfs * ((float)(int)((Pc - P) >> sc.shift_d) * vPd);
+      dtau = sc.tau_f * e0 * fabsf(expm1_small(-dx)) * sc.invE / fabsf(uz);
+    }
+  } else if (horizontal) {
+    float d = 0.0f;
+    if (P > 0 && P < kOneP) {
+      const int j = (int)__umul64hi((unsigned long long)P << 2, (unsigned long long)n_v);
+      d = u64_to_f(Sq[j + 1] - Sq[j]);
+    }
+    dtau = d * sc.tau_hv_dv;
+  } else {
+    const long long dS = mass_at(Sq, n_v, Pc) - mass_at(Sq, n_v, P);
+    dtau = u64_to_f((unsigned long long)(dS < 0 ? -dS : dS)) * sc.tau_S / fabsf(uz);
+  }
+  return u23f(rx) < expf(-dtau);
+}
+
+// A run of passed layers, 32 steps at a time: lane i evaluates step
+// k + adv + i of one photon, and the first lane whose step would end the run
+// (a stop, the top, the free surface, or a step at or past k_lim) bounds the
+// advance. Every lane of the warp calls it with the same arguments; the
+// result is the number of steps the photon passes before the one that ends
+// its run, which the photon's own lane then takes as usual. Positions stay
+// within 33 steps of the cloud: inside the 64-bit range for steps h_P <= 2^56.
+__device__ __forceinline__ unsigned long long fast_forward(const StepConst& sc, const unsigned long long* Sq,
+                                           int n_v, float vP32, float vPd, uint2 key,
+                                           unsigned sid, unsigned long long pk, unsigned k,
+                                           unsigned k_lim, long long P, float uz, int lane) {
+  const long long dP = step_P(uz, (unsigned long long)sc.h_P);
+  unsigned long long adv = 0;
+  for (;;) {
+    const unsigned long long kk = (unsigned long long)k + adv + (unsigned)lane;
+    bool cont = false;
+    if (kk < (unsigned long long)k_lim) {
+      const uint4 r = philox4x32_10(
+          make_uint4((unsigned)pk, (unsigned)(pk >> 32), (unsigned)kk, sid), key);
+      long long Pn, Pc;
+      const long long Pi = P + (long long)(adv + (unsigned)lane) * dP;
+      cont = step_passes(sc, Sq, n_v, vP32, vPd, Pi, uz, r.x, Pn, Pc) &&
+             Pn < kOneP - sc.eps_P && Pn > sc.P_fs + sc.eps_P;
+    }
+    const unsigned b = __ballot_sync(kFullS, !cont);
+    if (b) return adv + (unsigned)(__ffs(b) - 1);
+    adv += 32;
+  }
+}
+
+// A photon whose current run has passed this many layers is moved on by the
+// whole warp (fast_forward) until the run ends.
+constexpr unsigned kLongRun = 8;
+
 __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restrict__ set,
                                                         const float* __restrict__ pn_g,
                                                         StepConst sc,
@@ -195,10 +276,9 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
   unsigned long long pk = 0, W = 0, dmask = 0;
   long long P = 0;
   unsigned k = 0, nev = 0, nsca = 0, nsurf = 0;
+  unsigned npass = 0;          // layers passed since the last event (the current run)
   float vcur = 0.f, ux = 0.f, uy = 0.f, uz = -1.f, iuz = -1.f;
   float Xx = 0.f, Xy = 0.f, vapp = 0.f, vcomp = 0.f;
-  float e0 = 0.f, em1 = 0.f;
-  bool e0_ok = false;
 
   const int lane = threadIdx.x & 31;
   bool exhausted = false;
@@ -218,53 +298,54 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
         ux = 0.f; uy = 0.f; uz = -1.f; iuz = -1.f;
         Xx = 0.f; Xy = 0.f; vapp = 0.f; vcomp = 0.f;
         W = 1ull << 32;
-        k = 1; nev = 0; nsca = 0; nsurf = 0; dmask = 0;
-        e0_ok = false;
+        k = 1; nev = 0; nsca = 0; nsurf = 0; dmask = 0; npass = 0;
         ++st_launch;
       }
     }
     if (!__any_sync(kFullS, alive)) break;
+    if (sc.ff) {
+      // long runs of passed layers, one photon at a time by the whole warp
+      unsigned todo = __ballot_sync(kFullS, alive && npass >= kLongRun);
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const unsigned long long spk = __shfl_sync(kFullS, pk, src);
+        const unsigned sk = __shfl_sync(kFullS, k, src);
+        const long long sP = __shfl_sync(kFullS, P, src);
+        const float suz = __shfl_sync(kFullS, uz, src);
+        const unsigned long long adv = fast_forward(sc, Sq, sd.n_v, vP32, vPd, key, sid, spk, sk,
+                                                    sd.max_events, sP, suz, lane);
+        if (lane == src && adv) {
+          k += (unsigned)adv;
+          P += (long long)adv * step_P(uz, (unsigned long long)sc.h_P);
+          npass += (unsigned)adv;
+          st_steps += adv;
+        }
+      }
+    }
     unsigned fate = 0;
     bool need_ar = false;
     unsigned r_phi = 0;
     if (alive) {
       const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), k, sid), key);
-      // Step (3): one step along u and the optical depth of the layer crossed
-      const long long Pn = P + step_P(uz, (unsigned long long)sc.h_P);
-      const long long Pc = Pn < sc.P_fs ? sc.P_fs : (Pn > kOneP ? kOneP : Pn);
-      const bool horizontal = fabsf(uz) < 1e-9f;
-      float dtau;
-      em1 = 0.0f;
-      if (sc.expo) {
-        // Eq. 20 in closed form: with x = beta (v - v_fs) / v_fs the mass
-        // fraction between two heights is exp(-x0) (1 - exp(-(x1 - x0))) / E.
-        // exp(-x0) is carried from step to step (times exp(-dx)) and taken
-        // afresh after every event and every 64 steps.
-        if (!e0_ok || (k & 63u) == 0) {
-          e0 = expf(-sc.b_vfs * p_to_v(P, vP32));
-          e0_ok = true;
-        }
-        if (horizontal) {
-          dtau = sc.tau_f * sc.b_vfs * e0 * sc.invE * sc.h_v;
-        } else {
-          const float dx = sc.b_vfs * ((float)(int)((Pc - P) >> sc.shift_d) * vPd);
-          em1 = expm1_small(-dx);
-          dtau = sc.tau_f * e0 * fabsf(em1) * sc.invE / fabsf(uz);
-        }
-      } else if (horizontal) {
-        float d = 0.0f;
-        if (P > 0 && P < kOneP) {
-          const int j = (int)__umul64hi((unsigned long long)P << 2, (unsigned long long)sd.n_v);
-          d = u64_to_f(Sq[j + 1] - Sq[j]);
-        }
-        dtau = d * sc.tau_hv_dv;
-      } else {
-        const long long dS = mass_at(Sq, sd.n_v, Pc) - mass_at(Sq, sd.n_v, P);
-        dtau = u64_to_f((unsigned long long)(dS < 0 ? -dS : dS)) * sc.tau_S / fabsf(uz);
-      }
+      // Step (3): one step along u and the Bernoulli trial of the layer crossed
+      long long Pn, Pc;
+      const bool pass = step_passes(sc, Sq, sd.n_v, vP32, vPd, P, uz, r.x, Pn, Pc);
       ++st_steps;
-      if (u23f(r.x) < expf(-dtau)) {
-        if (Pn >= kOneP - sc.eps_P) {
+      if (pass && Pn < kOneP - sc.eps_P && Pn > sc.P_fs + sc.eps_P) {
+        P = Pn;                                           // Step (5): passed the layer
+        ++npass;
+      } else {
+        // The run ends. Its passed layers moved the photon npass steps of
+        // h along u: lateral displacement and height, taken here at once.
+        if (npass) {
+          const float len = (float)npass * sc.h_v;
+          Xx = fmaf(ux, len, Xx);
+          Xy = fmaf(uy, len, Xy);
+          vcur = p_to_v(P, vP32) + sd.v_bot_f;
+          npass = 0;
+        }
+        if (pass && Pn >= kOneP - sc.eps_P) {
           // Step (6): out through the top; vacuum flight to the probe plane
           const float d = sd.v_top_f - vcur;
           Xx = fmaf(ux * iuz, d, Xx);
@@ -290,14 +371,13 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
           atomicAdd(&s_cnt[C_ESCAPES], 1ull);
           atomicAdd(&s_cnt[C_W_ESCAPED], W);
           fate = 1;
-        } else if (Pn <= sc.P_fs + sc.eps_P) {
+        } else if (pass) {
           // Step (6): the free surface; reflectivity in 2^32 fixed point
           const float d = sd.v_fs_f - vcur;
           Xx = fmaf(ux * iuz, d, Xx);
           Xy = fmaf(uy * iuz, d, Xy);
           P = sc.P_fs;
           vcur = sd.v_fs_f;
-          e0_ok = false;
           ++nev; ++nsurf; ++st_events; ++st_surf;
           const unsigned long long Wn =
               sd.R_q >= (1ull << 32) ? W : ((W * sd.R_q + (1ull << 31)) >> 32);
@@ -325,34 +405,26 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
           iuz = rcp_approx(nz);
           if (W == 0) fate = 3;
         } else {
-          // Step (5): passed the layer
-          P = Pn;
-          e0 = fmaf(e0, em1, e0);                                       // exp(-x) at Pn
-          vcur = p_to_v(Pn, vP32) + sd.v_bot_f;
-          Xx = fmaf(ux, sc.h_v, Xx);
-          Xy = fmaf(uy, sc.h_v, Xy);
-        }
-      } else {
-        // stopped in the layer: the interaction is at the end of the step
-        const float vn = Pc == sc.P_fs ? sd.v_fs_f : p_to_v(Pc, vP32) + sd.v_bot_f;
-        if (horizontal) {
-          Xx = fmaf(ux, sc.h_v, Xx);
-          Xy = fmaf(uy, sc.h_v, Xy);
-        } else {
-          const float d = vn - vcur;
-          Xx = fmaf(ux * iuz, d, Xx);
-          Xy = fmaf(uy * iuz, d, Xy);
-        }
-        P = Pc;
-        vcur = vn;
-        e0_ok = false;
-        ++nev; ++st_events;
-        if ((r.y >> 8) < sd.omega_q) {
-          need_ar = true;                                                 // Step (4): scattered
-          r_phi = r.w;
-        } else {
-          atomicAdd(&s_cnt[C_W_ABS_PARTICLE], W);                         // Eq. 11: absorbed
-          fate = 2;
+          // stopped in the layer: the interaction is at the end of the step
+          const float vn = Pc == sc.P_fs ? sd.v_fs_f : p_to_v(Pc, vP32) + sd.v_bot_f;
+          if (fabsf(uz) < 1e-9f) {
+            Xx = fmaf(ux, sc.h_v, Xx);
+            Xy = fmaf(uy, sc.h_v, Xy);
+          } else {
+            const float d = vn - vcur;
+            Xx = fmaf(ux * iuz, d, Xx);
+            Xy = fmaf(uy * iuz, d, Xy);
+          }
+          P = Pc;
+          vcur = vn;
+          ++nev; ++st_events;
+          if ((r.y >> 8) < sd.omega_q) {
+            need_ar = true;                                               // Step (4): scattered
+            r_phi = r.w;
+          } else {
+            atomicAdd(&s_cnt[C_W_ABS_PARTICLE], W);                       // Eq. 11: absorbed
+            fate = 2;
+          }
         }
       }
     }   // alive

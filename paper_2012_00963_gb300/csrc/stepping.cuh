@@ -27,6 +27,8 @@ struct StepConst {
   float invE;              // 1 / (1 - exp(-beta (v_top / v_fs - 1)))
   float tau_f;             // tau_tot
   int shift_d;             // dP >> shift_d fits 31 bits for a whole step
+  int ff;                  // warp fast-forward of long runs allowed (h_P <= 2^56, so
+                           // 33 steps past the cloud stay inside the 64-bit range)
 };
 
 // Shared-memory bytes of the stepping kernel for a set.
