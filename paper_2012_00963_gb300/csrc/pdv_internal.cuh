@@ -116,18 +116,14 @@ __device__ __forceinline__ double u23d(unsigned r) {
   return ((double)(r >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
-// x * 2^62 truncated towards zero for |x| < 1 (binary32 -> 64-bit integer with
-// integer instructions only).
+// x * 2^62 truncated towards zero for |x| < 1, exactly: with a = x 2^31
+// (exact), x 2^62 = trunc(a) 2^31 + (a - trunc(a)) 2^31, and both parts are
+// exact 32-bit conversions (the fractional part keeps at most 24 bits).
 __device__ __forceinline__ long long fix62(float x) {
-  const unsigned b = __float_as_uint(x);
-  const int e = (int)((b >> 23) & 0xffu);
-  const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
-  const int sh = e - 88;                       // value = m * 2^(e - 150) * 2^62
-  long long v;
-  if (sh >= 0) v = m << sh;
-  else v = (sh > -40) ? (m >> (-sh)) : 0ll;
-  if (e == 0) v = 0;
-  return (b >> 31) ? -v : v;
+  const float a = x * 2147483648.0f;
+  const int hi = __float2int_rz(a);
+  const int lo = __float2int_rz((a - truncf(a)) * 2147483648.0f);
+  return ((long long)hi << 31) + (long long)lo;
 }
 
 // Reciprocal on the special-function unit (about 1 ulp; used for geometry

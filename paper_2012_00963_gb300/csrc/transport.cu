@@ -8,8 +8,10 @@
 // absorption, surface loss, event limit) launches the next packet of the
 // warp's chunk in the same iteration. Packet state: 62-bit fixed-point mass
 // fraction S (optical depth T = tau_tot S above the free surface), binary32
-// direction and lateral displacement, 2^32 fixed-point weight. Tallies are
-// 64-bit integer atomics, so results do not depend on scheduling.
+// direction and lateral displacement, 2^32 fixed-point weight. Histogram
+// tallies are 64-bit integer atomics; the per-set sums (events, escapes,
+// escaped and absorbed weight) are integers held per lane and added to the
+// set's counters once per set. Results do not depend on scheduling.
 //
 // k_transport_f64: the plain FP64 path, one packet per thread at a time,
 // tables read from global memory, FP64 throughout.
@@ -210,11 +212,12 @@ __global__ void __launch_bounds__(256, 5) k_transport_f32(const SetDesc* __restr
     bool exhausted = false, alive = false;
     unsigned long long pk = 0, W = 0;
     long long Sq = 0;
-    unsigned kev = 0, nev = 0, nsca = 0, nsurf = 0;
+    unsigned kev = 0, nev = 0, nsca = 0, nsurf = 0;   // nev: events left before the limit
     unsigned long long dmask = 0;
     float vcur = 0.f, ux = 0.f, uy = 0.f, uz = -1.f, iuz = -1.f;
     float Xx = 0.f, Xy = 0.f, vapp = 0.f, vcomp = 0.f;
-    unsigned st_launch = 0, st_events = 0, st_scat = 0, st_surf = 0;
+    unsigned st_launch = 0, st_events = 0, st_scat = 0, st_surf = 0, st_esc = 0;
+    unsigned long long st_wesc = 0, st_wabs = 0;     // escaped / absorbed weight
 
     for (;;) {
       // refill dead lanes from the warp's chunk of packets
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(256, 5) k_transport_f32(const SetDesc* __restr
           vcur = sd.v_top_f;
           Xx = 0.f; Xy = 0.f; vapp = 0.f; vcomp = 0.f;
           W = 1ull << 32;
-          kev = 1; nev = 0;
+          kev = 1; nev = sd.max_events;
           if (DUMP) { nsca = 0; nsurf = 0; dmask = 0; }
           ++st_launch;
           alive = true;
@@ -350,13 +353,13 @@ __global__ void __launch_bounds__(256, 5) k_transport_f32(const SetDesc* __restr
             }
           }
         }
-        atomicAdd(&s_cnt[C_ESCAPES], 1ull);
-        atomicAdd(&s_cnt[C_W_ESCAPED], W);
+        ++st_esc;
+        st_wesc += W;
         fate = 1;
       } else {
         Sq = Sn;
         vcur = vn;
-        ++nev;
+        --nev;
         ++st_events;
         const bool surf = what == 2;
         if (surf) {
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(256, 5) k_transport_f32(const SetDesc* __restr
           if (Wn != W) atomicAdd(&s_cnt[C_W_ABS_SURFACE], W - Wn);
           W = Wn;
         } else if ((r.y >> 8) >= sd.omega_q) {
-          atomicAdd(&s_cnt[C_W_ABS_PARTICLE], W);             // Eq. 11: absorbed
+          st_wabs += W;                                       // Eq. 11: absorbed
           fate = 2;
         }
         if (fate == 0) {
@@ -435,7 +438,7 @@ __global__ void __launch_bounds__(256, 5) k_transport_f32(const SetDesc* __restr
           if (W == 0) fate = 3;      // the surface absorbed all of the weight
         }
       }
-      if (fate == 0 && nev >= sd.max_events) {
+      if (fate == 0 && nev == 0u) {
         atomicAdd(&s_cnt[C_W_TRUNCATED], W);
         atomicAdd(&s_cnt[C_TRUNCATED], 1ull);
         fate = 4;
@@ -443,7 +446,7 @@ __global__ void __launch_bounds__(256, 5) k_transport_f32(const SetDesc* __restr
       if (fate) {
         if (DUMP && sd.packets) {
           pdv_packet_record rec;
-          rec.n_events = nev;
+          rec.n_events = sd.max_events - nev;
           rec.n_scatters = nsca;
           rec.n_surface = nsurf;
           rec.fate = fate;
@@ -458,18 +461,25 @@ __global__ void __launch_bounds__(256, 5) k_transport_f32(const SetDesc* __restr
 
     // ---- flush this set's tallies
     {
-      unsigned a = st_launch, b = st_events, c = st_scat, d = st_surf;
+      unsigned a = st_launch, b = st_events, c = st_scat, d = st_surf, e = st_esc;
+      unsigned long long we = st_wesc, wa = st_wabs;
       for (int o = 16; o; o >>= 1) {
         a += __shfl_xor_sync(kFull, a, o);
         b += __shfl_xor_sync(kFull, b, o);
         c += __shfl_xor_sync(kFull, c, o);
         d += __shfl_xor_sync(kFull, d, o);
+        e += __shfl_xor_sync(kFull, e, o);
+        we += __shfl_xor_sync(kFull, we, o);
+        wa += __shfl_xor_sync(kFull, wa, o);
       }
       if (lane == 0) {
         atomicAdd(&s_cnt[C_LAUNCHED], (unsigned long long)a);
         atomicAdd(&s_cnt[C_EVENTS], (unsigned long long)b);
         atomicAdd(&s_cnt[C_SCATTERS], (unsigned long long)c);
         atomicAdd(&s_cnt[C_SURFACE_HITS], (unsigned long long)d);
+        atomicAdd(&s_cnt[C_ESCAPES], (unsigned long long)e);
+        atomicAdd(&s_cnt[C_W_ESCAPED], we);
+        atomicAdd(&s_cnt[C_W_ABS_PARTICLE], wa);
       }
     }
     __syncthreads();
