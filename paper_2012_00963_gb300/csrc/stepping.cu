@@ -162,15 +162,38 @@ __device__ __forceinline__ void kahan(float& sum, float& comp, float term) {
   sum = t;
 }
 
+// What a step depends on through the direction alone: its length in P, the
+// layer term exp(-dx) - 1 of an unclipped step (Eq. 20 closed form), and
+// 1 / |u_z|. Taken once per direction; both the per-lane loop and the warp's
+// fast-forward read the same values.
+struct StepDir {
+  long long dP;            // signed step in P
+  float em1;               // exp(-dx) - 1 for a step of dP (exponential law)
+  float iauz;              // 1 / |u_z| (unused for a horizontal photon)
+};
+
+__device__ __forceinline__ StepDir step_dir(const StepConst& sc, float vPd, float uz) {
+  StepDir d;
+  d.dP = step_P(uz, (unsigned long long)sc.h_P);
+  d.em1 = sc.expo ? expm1_small(-(sc.b_vfs * ((float)(int)(d.dP >> sc.shift_d) * vPd))) : 0.0f;
+  d.iauz = 1.0f / fabsf(uz);
+  return d;
+}
+
 // Section II.B steps (2)-(3) for one step of a photon at height P moving with
 // u_z: the step's end Pn, that end inside the cloud Pc, and whether the photon
 // passes the layer it crossed (the Bernoulli trial on word rx of its draw).
-// A pure function of (P, u_z, rx), so the per-lane loop and the warp's
-// fast-forward below take identical decisions from it.
+// A pure function of (P, direction, rx), so the per-lane loop and the warp's
+// fast-forward below take identical decisions from it. `clip` says whether a
+// step clipped at the cloud's ends takes its own layer term (the per-lane
+// loop); the fast-forward skips that, since a clipped step ends the run
+// whatever its trial gives.
+template <bool CLIP>
 __device__ __forceinline__ bool step_passes(const StepConst& sc, const unsigned long long* Sq,
                                             int n_v, float vP32, float vPd, long long P, float uz,
-                                            unsigned rx, long long& Pn, long long& Pc) {
-  Pn = P + step_P(uz, (unsigned long long)sc.h_P);
+                                            const StepDir& dir, unsigned rx, long long& Pn,
+                                            long long& Pc) {
+  Pn = P + dir.dP;
   Pc = Pn < sc.P_fs ? sc.P_fs : (Pn > kOneP ? kOneP : Pn);
   const bool horizontal = fabsf(uz) < 1e-9f;
   float dtau;
@@ -181,8 +204,10 @@ __device__ __forceinline__ bool step_passes(const StepConst& sc, const unsigned 
     if (horizontal) {
       dtau = sc.tau_f * sc.b_vfs * e0 * sc.invE * sc.h_v;
     } else {
-      const float dx = sc.b_vfs * ((float)(int)((Pc - P) >> sc.shift_d) * vPd);
-      dtau = sc.tau_f * e0 * fabsf(expm1_small(-dx)) * sc.invE / fabsf(uz);
+      float em1 = dir.em1;
+      if (CLIP && Pc != Pn)
+        em1 = expm1_small(-(sc.b_vfs * ((float)(int)((Pc - P) >> sc.shift_d) * vPd)));
+      dtau = sc.tau_f * e0 * fabsf(em1) * sc.invE * dir.iauz;
     }
   } else if (horizontal) {
     float d = 0.0f;
@@ -193,7 +218,7 @@ __device__ __forceinline__ bool step_passes(const StepConst& sc, const unsigned 
     dtau = d * sc.tau_hv_dv;
   } else {
     const long long dS = mass_at(Sq, n_v, Pc) - mass_at(Sq, n_v, P);
-    dtau = u64_to_f((unsigned long long)(dS < 0 ? -dS : dS)) * sc.tau_S / fabsf(uz);
+    dtau = u64_to_f((unsigned long long)(dS < 0 ? -dS : dS)) * sc.tau_S * dir.iauz;
   }
   return u23f(rx) < expf(-dtau);
 }
@@ -209,7 +234,8 @@ __device__ __forceinline__ unsigned long long fast_forward(const StepConst& sc, 
                                            int n_v, float vP32, float vPd, uint2 key,
                                            unsigned sid, unsigned long long pk, unsigned k,
                                            unsigned k_lim, long long P, float uz, int lane) {
-  const long long dP = step_P(uz, (unsigned long long)sc.h_P);
+  const StepDir dir = step_dir(sc, vPd, uz);
+  const long long top = kOneP - sc.eps_P, bottom = sc.P_fs + sc.eps_P;
   unsigned long long adv = 0;
   for (;;) {
     const unsigned long long kk = (unsigned long long)k + adv + (unsigned)lane;
@@ -218,9 +244,9 @@ __device__ __forceinline__ unsigned long long fast_forward(const StepConst& sc, 
       const uint4 r = philox4x32_10(
           make_uint4((unsigned)pk, (unsigned)(pk >> 32), (unsigned)kk, sid), key);
       long long Pn, Pc;
-      const long long Pi = P + (long long)(adv + (unsigned)lane) * dP;
-      cont = step_passes(sc, Sq, n_v, vP32, vPd, Pi, uz, r.x, Pn, Pc) &&
-             Pn < kOneP - sc.eps_P && Pn > sc.P_fs + sc.eps_P;
+      const long long Pi = P + (long long)(adv + (unsigned)lane) * dir.dP;
+      cont = step_passes<false>(sc, Sq, n_v, vP32, vPd, Pi, uz, dir, r.x, Pn, Pc) && Pn < top &&
+             Pn > bottom;
     }
     const unsigned b = __ballot_sync(kFullS, !cont);
     if (b) return adv + (unsigned)(__ffs(b) - 1);
@@ -330,7 +356,8 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
       const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), k, sid), key);
       // Step (3): one step along u and the Bernoulli trial of the layer crossed
       long long Pn, Pc;
-      const bool pass = step_passes(sc, Sq, sd.n_v, vP32, vPd, P, uz, r.x, Pn, Pc);
+      const bool pass = step_passes<true>(sc, Sq, sd.n_v, vP32, vPd, P, uz,
+                                          step_dir(sc, vPd, uz), r.x, Pn, Pc);
       ++st_steps;
       if (pass && Pn < kOneP - sc.eps_P && Pn > sc.P_fs + sc.eps_P) {
         P = Pn;                                           // Step (5): passed the layer
