@@ -450,7 +450,7 @@ __global__ void k_peak_mats(int n, int k_c, int n_p, int k2p, int j_lo, int n_w,
 // acc[4][6] += A[rows ty*4..+3] x B[cols tx*6..+5] over `len` reduction steps.
 __device__ __forceinline__ void tile_fma(const float* A, const float* B, int len, int ty, int tx,
                                          float (&acc)[4][6]) {
-#pragma unroll 2
+#pragma unroll 8
   for (int q = 0; q < len; ++q) {
     const float4 a = *reinterpret_cast<const float4*>(A + q * kAS + ty * 4);
     const float2 b0 = *reinterpret_cast<const float2*>(B + q * kNT + tx * 6);
