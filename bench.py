@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mode", default="default",
                     choices=["default", "serve", "batch", "precision", "model", "extract-mc",
-                             "stepping", "spectrogram"])
+                             "stepping", "spectrogram", "cpu-baseline"])
     ap.add_argument("--times", type=int, default=512, help="snapshot times of the spectrogram mode")
     ap.add_argument("--out", default="", help="spectrogram mode: write the v-t image (PGM) here")
     ap.add_argument("--model-sets", type=int, default=100_000,
@@ -312,6 +312,7 @@ def our_arm(args):
     peak = SMS * SCHEDULERS * LANES * F_MAX_HZ / 1e9
     prof = profile_counters()
     traffic = prof["dram_bytes_per_event"] * ev_per_launch if prof else None
+    issue_meas = pdv.pdv_measure_issue_rate(ctx.handle, 0.2) / 1e9   # after the timed region
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
@@ -341,7 +342,10 @@ def our_arm(args):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_transport_f32", "kernel_ms": kern_ms,
                      "algo_inst_per_event": ALGO_INST_PER_EVENT,
-                     "peak_basis": "152 SM x 4 schedulers x 32 lanes x 2070 MHz (issue rate)"},
+                     "peak_basis": "152 SM x 4 schedulers x 32 lanes x 2070 MHz (issue rate)",
+                     "peak_measured": issue_meas, "frac_of_measured": achieved / issue_meas,
+                     "peak_measured_basis": "independent FP32 FMA chains, 64 warps per SM "
+                                            "(pdv_measure_issue_rate)"},
         "clocks": clk,
     }
     if rank == 0 and world == 1 and args.serve_seconds > 0:
@@ -771,6 +775,7 @@ def stepping_mode(args):
             out[name]["steps"] = st["last_steps"]
             out[name]["steps_per_s"] = st["last_steps"] / (statistics.mean(kms) / 1e3)
     clk = clocks.stop()
+    issue_meas = pdv.pdv_measure_issue_rate(ctx.handle, 0.2)        # after the timed region
     info = cloud.info()
     cloud.close()
     ctx.close()
@@ -811,7 +816,8 @@ def stepping_mode(args):
                      "unit": "Ginst/s", "frac": achieved / issue_peak,
                      "traffic": prof["dram_bytes_per_step"] * out["stepping"]["steps"] if prof else None,
                      "kernel": "k_transport_step", "algo_inst_per_step": a_step,
-                     "peak_basis": "%d SM x 4 schedulers x 32 lanes x 2070 MHz (issue rate)" % sm},
+                     "peak_basis": "%d SM x 4 schedulers x 32 lanes x 2070 MHz (issue rate)" % sm,
+                     "peak_measured": issue_meas / 1e9, "frac_of_measured": achieved / issue_meas},
         "gpu_launches": 1,
         "tau_tot": info["tau_tot"], "dtype": "f32", "data": "synthetic (seeded)",
         "cpu_baseline": {"value": m / t_cpu, "unit": "photons/s", "cores": os.cpu_count(),
@@ -868,6 +874,38 @@ def spectrogram_mode(args):
     return 0
 
 
+def cpu_baseline_mode(args):
+    """The FP64 CPU oracle timed on this machine's host cores, with one thread
+    and with all of them: the cfg1 workload on 1e6 packets and the heavy
+    multiple-scattering cfg3 cloud (tau = 109) on 1e7 packets. Events/s,
+    scatter events/s and spectra/s per run; no GPU is used."""
+    from oracle import oracle as O
+    from paper_2012_00963_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    out = {}
+    for name, wl, n_all, n_one in (
+            ("cfg1", W.cfg1(), 1_000_000, 1_000_000),
+            ("cfg3", W.cfg3(r_ap=3.0 * W.MM, cone_alpha=0.5), 10_000_000, 10_000_000)):
+        table = O.phase_table(wl)
+        row = {"workload": wl.name, "snapshots": len(wl.t_snap)}
+        for key, threads, n in (("all_cores", cores, n_all), ("one_thread", 1, n_one)):
+            t0 = time.perf_counter()
+            r = O.simulate(wl, n_threads=threads, n_packets=n, table=table)
+            dt = time.perf_counter() - t0
+            c = r["counters"][0]
+            row[key] = {"threads": threads, "packets": n, "seconds": dt,
+                        "events_per_s": int(c[1]) / dt, "scatter_events_per_s": int(c[2]) / dt,
+                        "packets_per_s": n / dt,
+                        "spectra_per_s": len(wl.t_snap) * (n / wl.n_packets) / dt}
+        out[name] = row
+    line = {"mode": "cpu-baseline", "metric": "FP64 oracle events/s and spectra/s on the host cores",
+            "kind": "oracle", "cores": cores, "cfg1": out["cfg1"], "cfg3": out["cfg3"],
+            "note": "spectra/s counts whole spectra of each workload's full packet count "
+                    "(cfg1 1e6, cfg3 1e9 packets)"}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -884,6 +922,8 @@ def main():
         return extract_mc_mode(args)
     if args.mode == "stepping":
         return stepping_mode(args)
+    if args.mode == "cpu-baseline":
+        return cpu_baseline_mode(args)
     if args.mode == "spectrogram":
         return spectrogram_mode(args)
     return our_arm(args)

@@ -244,6 +244,18 @@ pdv_status pdv_simulate_batch(pdv_ctx* ctx, const pdv_request* reqs, int n);
  * the fastest in the context (and in *out if not NULL). */
 pdv_status pdv_autotune(pdv_ctx* ctx, const pdv_request* reqs, int n, pdv_tuning* out);
 
+/* Measured instruction-issue rate of the context's GPU, the denominator of
+ * the issue-rate roofline the transport kernels are reported against (their
+ * work is integer and FP32 instruction issue, not a contraction or memory
+ * traffic). Runs a kernel of independent FP32 fused multiply-adds, eight
+ * chains per thread and 64 warps per SM, for about `seconds` (0 < seconds
+ * <= 10) on the context's stream, waits for it, and writes FMA
+ * thread-instructions per second to *out. The loop's own three instructions
+ * per 64 FMAs are not counted, so the figure is a slight lower bound of the
+ * issue rate at the clock the GPU ran. Errors: PDV_EINVAL (NULL arguments,
+ * seconds out of range), PDV_ECUDA. */
+pdv_status pdv_measure_issue_rate(pdv_ctx* ctx, double seconds, double* out);
+
 /* The same FP32 spectrum as pdv_simulate_spectrum for callers that cannot
  * allocate device memory while they run (an allocator or memory plan that
  * forbids cudaMalloc after start-up). The paper has no counterpart: it is a

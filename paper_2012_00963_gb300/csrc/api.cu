@@ -1064,6 +1064,59 @@ extern "C" pdv_status pdv_simulate_batch(pdv_ctx* c, const pdv_request* rs, int 
   return run_batch_f32(c, f32.data(), (int)f32.size(), true, nullptr);
 }
 
+// ------------------------------------------------------------------ issue-rate probe
+namespace pdv {
+// Eight independent chains of FP32 fused multiply-adds per thread, 64 per loop
+// trip: with 64 warps per SM every scheduler has a ready instruction each
+// cycle, so the FMA count per second is the SM's sustained issue rate (one
+// warp instruction per scheduler per cycle) at the clock the GPU runs.
+__device__ float g_issue_sink[1];
+
+__global__ void __launch_bounds__(256) k_issue_probe(int iters, float m, float a) {
+  float x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = (float)(threadIdx.x + j) * 1e-3f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = fmaf(x[j], m, a);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += x[j];
+  if (s == -1.0f) g_issue_sink[0] = s;           // never true (x stays > 0): keeps the chains live
+}
+}  // namespace pdv
+
+extern "C" pdv_status pdv_measure_issue_rate(pdv_ctx* c, double seconds, double* out) {
+  if (!c || !out) return fail(PDV_EINVAL, "ctx and out must not be NULL");
+  if (!(seconds > 0.0) || seconds > 10.0) return fail(PDV_EINVAL, "seconds must be in (0, 10]");
+  std::lock_guard<std::mutex> lk(c->mu);
+  CK(cudaSetDevice(c->device));
+  const int grid = c->sm_count * 8, block = 256;
+  auto run = [&](int iters, float* ms) -> pdv_status {
+    CK(cudaEventRecord(c->ev0, c->stream));
+    k_issue_probe<<<grid, block, 0, c->stream>>>(iters, 0.999999f, 1e-7f);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(c->ev1, c->stream));
+    CK(cudaEventSynchronize(c->ev1));
+    CK(cudaEventElapsedTime(ms, c->ev0, c->ev1));
+    return PDV_OK;
+  };
+  float ms = 0.0f;
+  pdv_status s = run(64, &ms);                         // warm-up and calibration
+  if (s != PDV_OK) return s;
+  const double per_iter = std::max((double)ms, 1e-3) / 64.0;
+  const int iters = (int)std::min(2.0e6, std::max(256.0, seconds * 1e3 / per_iter));
+  s = run(iters, &ms);
+  if (s != PDV_OK) return s;
+  c->launches += 2;
+  const double fmas = (double)grid * block * (double)iters * 64.0;
+  *out = fmas / (ms * 1e-3);
+  return PDV_OK;
+}
+
 extern "C" pdv_status pdv_autotune(pdv_ctx* c, const pdv_request* rs, int n, pdv_tuning* out) {
   if (!c || !rs || n < 1) return fail(PDV_EINVAL, "need a context and n >= 1 requests");
   for (int i = 0; i < n; ++i) {

@@ -39,7 +39,7 @@ ABI_FUNCTIONS = [
     "pdv_create_cloud", "pdv_set_phase_table", "pdv_cloud_get_info", "pdv_destroy_cloud",
     "pdv_phase_hg", "pdv_mie_table", "pdv_simulate_spectrum", "pdv_simulate_batch",
     "pdv_autotune", "pdv_submit", "pdv_poll", "pdv_cancel", "pdv_simulate_spectrum_static",
-    "pdv_ss_spectrum", "pdv_extract_peaks",
+    "pdv_ss_spectrum", "pdv_extract_peaks", "pdv_measure_issue_rate",
 ]
 
 
@@ -172,6 +172,7 @@ def lib():
                 "pdv_ss_spectrum": ([vp, vp, ip, ip, C.c_double, C.c_double, C.c_uint32, vp], ip),
                 "pdv_extract_peaks": ([vp, vp, ip, ip, C.c_double, C.c_double, C.c_double,
                                        C.POINTER(pdv_peak_opts), C.c_uint32, vp], ip),
+                "pdv_measure_issue_rate": ([vp, C.c_double, dp], ip),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -282,6 +283,13 @@ def pdv_autotune(ctx: int, reqs: Sequence[pdv_request]) -> dict:
     t = pdv_tuning()
     _check(lib().pdv_autotune(C.c_void_p(ctx), arr, len(reqs), C.byref(t)))
     return {f: getattr(t, f) for f, _ in pdv_tuning._fields_}
+
+
+def pdv_measure_issue_rate(ctx: int, seconds: float = 0.2) -> float:
+    """Measured FP32 FMA issue rate of the GPU, thread-instructions per second."""
+    v = C.c_double()
+    _check(lib().pdv_measure_issue_rate(C.c_void_p(ctx), float(seconds), C.byref(v)))
+    return v.value
 
 
 def pdv_submit(ctx: int, req: pdv_request) -> int:
