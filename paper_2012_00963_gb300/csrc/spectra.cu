@@ -543,19 +543,25 @@ __global__ void __launch_bounds__(256, 3) k_extract_tiled(
 #pragma unroll
         for (int c = 0; c < 6; ++c) acc[i][c] = 0.0f;
       // the next chunk is in flight while this one is multiplied: F by
-      // cp.async into the other shared buffer, the spectra (converted to FP32
-      // on the way) through registers (lane = bin of the chunk, warp + 8 u =
-      // spectrum)
+      // cp.async into the other shared buffer, the spectra as raw FP64 words in
+      // registers (lane = bin of the chunk, warp + 8 u = spectrum), converted
+      // to FP32 only after the products, so their loads overlap them
+      double ra[kTS / 8];
       float pa[kTS / 8];
       auto fetch_a = [&](int j0) {
         const int gj = j0 + lane;
 #pragma unroll
         for (int u = 0; u < kTS / 8; ++u) {
           const int gs = s0 + warp + 8 * u;
-          pa[u] = (gs < n_spec && gj < n) ? f64_to_f32(spec[(size_t)gs * n + gj]) : 0.0f;
+          ra[u] = (gs < n_spec && gj < n) ? spec[(size_t)gs * n + gj] : 0.0;
         }
       };
+      auto convert_a = [&]() {
+#pragma unroll
+        for (int u = 0; u < kTS / 8; ++u) pa[u] = f64_to_f32(ra[u]);
+      };
       fetch_a(0);
+      convert_a();
       __syncthreads();                               // B buffers free (previous users done)
       load_chunk_async(Bs, F + cp, (size_t)k2p, tid);
       for (int j0 = 0, c = 0; j0 < n_p; j0 += kJC, ++c) {
@@ -571,6 +577,7 @@ __global__ void __launch_bounds__(256, 3) k_extract_tiled(
           fetch_a(j0 + kJC);
         }
         tile_fma(As, Bc, kJC, ty, tx, acc);
+        if (j0 + kJC < n_p) convert_a();
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
