@@ -345,7 +345,9 @@ extern "C" pdv_status pdv_create_cloud(pdv_ctx* c, const pdv_cloud_desc* d, pdv_
   cl->d_s = d->d_median_um * 1e-6 * std::exp(2.5 * d->sigma_ln * d->sigma_ln);
   cl->m0 = d->area_mass_mg_cm2 * 1e-2;
   const int n_v = d->table_nodes ? d->table_nodes : 2048;
-  const int n_g = std::min(next_pow2(n_v), kMaxTableNodes);
+  // two guide cells per node up to 4096 nodes (fewer search steps where the
+  // mass fraction crowds near the top of the cloud), one above
+  const int n_g = n_v <= 4096 ? 2 * next_pow2(n_v) : std::min(next_pow2(n_v), kMaxTableNodes);
   int lg = 0;
   while ((1 << lg) < n_g) ++lg;
   cl->t.n_v = n_v;

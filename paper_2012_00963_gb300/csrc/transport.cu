@@ -119,7 +119,7 @@ __device__ __forceinline__ void launch_position(unsigned long long pk, unsigned 
 }
 
 template <bool DUMP, int HMODE>
-__global__ void __launch_bounds__(256, 5) k_transport_f32(const SetDesc* __restrict__ sets,
+__global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restrict__ sets,
                                                           int n_sets,
                                                           unsigned long long* __restrict__ set_ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
