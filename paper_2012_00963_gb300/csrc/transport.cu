@@ -400,8 +400,8 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
             if (DUMP) ++nsca;
           }
           float st, ct, sp, cp;
-          sincospif(tpi, &st, &ct);
-          sincospif(2.0f * u23f(rphi), &sp, &cp);                        // azimuth, Eq. 15
+          sincospi_half_turns(tpi, &st, &ct);
+          sincospi_half_turns(2.0f * u23f(rphi), &sp, &cp);              // azimuth, Eq. 15
           if (surf && sd.surface_mode == PDV_SURFACE_LAMBERT) {
             const float a = u23f(r.y);
             ct = sqrtf(a);
