@@ -236,6 +236,8 @@ __device__ __forceinline__ unsigned long long fast_forward(const StepConst& sc, 
                                            unsigned k_lim, long long P, float uz, int lane) {
   const StepDir dir = step_dir(sc, vPd, uz);
   const long long top = kOneP - sc.eps_P, bottom = sc.P_fs + sc.eps_P;
+  const long long step32 = 32 * dir.dP;
+  long long Pi = P + (long long)lane * dir.dP;
   unsigned long long adv = 0;
   for (;;) {
     const unsigned long long kk = (unsigned long long)k + adv + (unsigned)lane;
@@ -244,19 +246,19 @@ __device__ __forceinline__ unsigned long long fast_forward(const StepConst& sc, 
       const uint4 r = philox4x32_10(
           make_uint4((unsigned)pk, (unsigned)(pk >> 32), (unsigned)kk, sid), key);
       long long Pn, Pc;
-      const long long Pi = P + (long long)(adv + (unsigned)lane) * dir.dP;
       cont = step_passes<false>(sc, Sq, n_v, vP32, vPd, Pi, uz, dir, r.x, Pn, Pc) && Pn < top &&
              Pn > bottom;
     }
     const unsigned b = __ballot_sync(kFullS, !cont);
     if (b) return adv + (unsigned)(__ffs(b) - 1);
     adv += 32;
+    Pi += step32;
   }
 }
 
 // A photon whose current run has passed this many layers is moved on by the
 // whole warp (fast_forward) until the run ends.
-constexpr unsigned kLongRun = 8;
+constexpr unsigned kLongRun = 4;
 
 __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restrict__ set,
                                                         const float* __restrict__ pn_g,
