@@ -689,7 +689,7 @@ static ReqBuffers plan_request(const pdv_request* r, bool device_out) {
 }
 
 static size_t set_smem(const SetDesc& d, int hm) {
-  return transport_f32_smem(d.n_v, d.n_g, d.n_p, d.n_snap, d.n_bins, hm, d.phase_uniform);
+  return transport_f32_smem(d.n_v, d.n_g, d.n_p, d.n_snap, d.n_bins, hm, d.phase_uniform, d.ap_all);
 }
 
 static int pick_hist_mode(const pdv_ctx* c, const SetDesc& d) {

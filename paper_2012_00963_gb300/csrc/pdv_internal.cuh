@@ -172,7 +172,7 @@ void launch_normalise(const SetDesc* d_sets, int n_sets, double* const* d_spec,
                       pdv_counters* const* d_cnt_out, unsigned long long* const* d_raw,
                       const unsigned* flags, int max_snap, cudaStream_t st);
 size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode,
-                          int phase_uniform);
+                          int phase_uniform, int ap_all);
 int transport_f32_max_smem();
 cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, int* blocks);
 

@@ -380,20 +380,28 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
           Xx = fmaf(ux * iuz, d, Xx);
           Xy = fmaf(uy * iuz, d, Xy);
           if (sd.cone_all || uz >= sd.cos_alpha_f) {
-            float x0, y0;
-            launch_xy(pk, sid, key, sd.r_beam_f, x0, y0);
-            const float tx = ux * iuz, ty = uy * iuz;
-            const float ax = fmaf(tx, sd.z_probe_f, x0), ay = fmaf(ty, sd.z_probe_f, y0);
-            const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
             const float fb = floorf((vapp - vcomp - sd.v_lo_f) * sd.inv_dbin_f);
             const int idx = fb < 0.0f ? 0 : (fb >= (float)n_bins ? n_bins + 1 : (int)fb + 1);
-            for (int s = 0; s < n_snap; ++s) {
-              const float t = ts[s];
-              const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
-              if (sd.ap_all || fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
-                atomicAdd(&sd.hist[(size_t)s * row + idx], W);             // Eq. 19
-                atomicAdd(&sd.hist[(size_t)s * row + n_bins + 2], 1ull);
-                if (s < 64) dmask |= 1ull << s;
+            if (sd.ap_all) {
+              // every snapshot time alike: one tally in row 0 (the
+              // normalisation reads it for each time)
+              atomicAdd(&sd.hist[idx], W);                                  // Eq. 19
+              atomicAdd(&sd.hist[n_bins + 2], 1ull);
+              dmask = n_snap >= 64 ? ~0ull : ((1ull << n_snap) - 1ull);
+            } else {
+              float x0, y0;
+              launch_xy(pk, sid, key, sd.r_beam_f, x0, y0);
+              const float tx = ux * iuz, ty = uy * iuz;
+              const float ax = fmaf(tx, sd.z_probe_f, x0), ay = fmaf(ty, sd.z_probe_f, y0);
+              const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
+              for (int s = 0; s < n_snap; ++s) {
+                const float t = ts[s];
+                const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
+                if (fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
+                  atomicAdd(&sd.hist[(size_t)s * row + idx], W);           // Eq. 19
+                  atomicAdd(&sd.hist[(size_t)s * row + n_bins + 2], 1ull);
+                  if (s < 64) dmask |= 1ull << s;
+                }
               }
             }
           }

@@ -46,8 +46,14 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 
 // Shared-memory bytes for one set's staged tables (and optional histogram).
 // A uniform theta grid needs no per-node angle arrays.
+// With an unlimited aperture every snapshot time detects an escaping packet
+// alike, so a set tallies one histogram row (row 0) and the normalisation
+// reads it for every snapshot.
+__host__ __device__ inline int tally_rows(int n_snap, int ap_all) { return ap_all ? 1 : n_snap; }
+
 __host__ __device__ inline size_t smem_layout(int n_v, int n_g, int n_p, int n_snap, int n_bins,
-                                              int hist_mode, int phase_uniform, size_t* off) {
+                                              int hist_mode, int phase_uniform, int ap_all,
+                                              size_t* off) {
   const size_t n_th = phase_uniform ? 0 : (size_t)n_p;
   size_t o = 0;
   off[0] = o; o = align16(o + sizeof(unsigned long long) * (size_t)(n_v + 1));   // Sq
@@ -60,14 +66,15 @@ __host__ __device__ inline size_t smem_layout(int n_v, int n_g, int n_p, int n_s
   off[7] = o; o = align16(o + sizeof(float) * (size_t)n_snap);                    // ts
   off[8] = o; o = align16(o + sizeof(unsigned short) * (size_t)n_snap);           // perm
   off[9] = o;
-  if (hist_mode == 2) o = align16(o + sizeof(unsigned long long) * (size_t)n_snap * hist_row(n_bins));
+  if (hist_mode == 2)
+    o = align16(o + sizeof(unsigned long long) * (size_t)tally_rows(n_snap, ap_all) * hist_row(n_bins));
   return o;
 }
 
 size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode,
-                          int phase_uniform) {
+                          int phase_uniform, int ap_all) {
   size_t off[10];
-  return smem_layout(n_v, n_g, n_p, n_snap, n_bins, hist_mode, phase_uniform, off);
+  return smem_layout(n_v, n_g, n_p, n_snap, n_bins, hist_mode, phase_uniform, ap_all, off);
 }
 
 __device__ __forceinline__ int search_mass(const unsigned long long* Sq, const unsigned short* G,
@@ -151,7 +158,7 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
     }
     __syncthreads();
     size_t off[10];
-    smem_layout(sd.n_v, sd.n_g, sd.n_p, sd.n_snap, sd.n_bins, HMODE, sd.phase_uniform, off);
+    smem_layout(sd.n_v, sd.n_g, sd.n_p, sd.n_snap, sd.n_bins, HMODE, sd.phase_uniform, sd.ap_all, off);
     SmemTables tb;
     tb.Sq = reinterpret_cast<const unsigned long long*>(smem + off[0]);
     tb.w = reinterpret_cast<const float*>(smem + off[1]);
@@ -190,7 +197,7 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
       }
       if (HMODE == 2) {
         unsigned long long* h = reinterpret_cast<unsigned long long*>(smem + off[9]);
-        const int nh = sd.n_snap * hist_row(sd.n_bins);
+        const int nh = tally_rows(sd.n_snap, sd.ap_all) * hist_row(sd.n_bins);
         for (int i = threadIdx.x; i < nh; i += blockDim.x) h[i] = 0ull;
       }
     }
@@ -304,18 +311,24 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
       if (what == 1) {
         // Step (6): out through the top, vacuum flight to the probe plane
         if (sd.cone_all || uz >= sd.cos_alpha_f) {
-          float x0, y0;
-          launch_position(pk, sid, key, sd.r_beam_f, x0, y0);
-          const float tx = ux * iuz, ty = uy * iuz;
-          const float ax = fmaf(tx, sd.z_probe_f, x0), ay = fmaf(ty, sd.z_probe_f, y0);
-          const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
           const float fb = floorf((vapp - vcomp - sd.v_lo_f) * sd.inv_dbin_f);
           const int idx = fb < 0.0f ? 0 : (fb >= (float)n_bins ? n_bins + 1 : (int)fb + 1);
-          // |a + t b|^2 <= R^2 holds on one interval of t: visit the ascending
-          // snapshot times inside it, plus one on each side, each re-tested
-          // exactly as below (the interval only narrows the search)
-          int s0 = 0, s1 = n_snap;
-          if (!sd.ap_all) {
+          if (sd.ap_all) {
+            // Eq. 19 at every snapshot time alike (unlimited aperture): one
+            // tally in row 0, which the normalisation reads for each time
+            atomicAdd(&tb.hist[idx], W);
+            atomicAdd(&tb.hist[n_bins + 2], 1ull);
+            if (DUMP) dmask = n_snap >= 64 ? ~0ull : ((1ull << n_snap) - 1ull);
+          } else {
+            float x0, y0;
+            launch_position(pk, sid, key, sd.r_beam_f, x0, y0);
+            const float tx = ux * iuz, ty = uy * iuz;
+            const float ax = fmaf(tx, sd.z_probe_f, x0), ay = fmaf(ty, sd.z_probe_f, y0);
+            const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
+            // |a + t b|^2 <= R^2 holds on one interval of t: visit the ascending
+            // snapshot times inside it, plus one on each side, each re-tested
+            // exactly as below (the interval only narrows the search)
+            int s0 = 0, s1 = n_snap;
             const float A = fmaf(bx, bx, by * by);
             const float B = 2.0f * fmaf(ax, bx, ay * by);
             const float Cc = fmaf(ax, ax, fmaf(ay, ay, -sd.r_ap2_f));
@@ -340,16 +353,16 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
                 s1 = lo < n_snap ? lo + 1 : n_snap;
               }
             }
-          }
-          for (int s = s0; s < s1; ++s) {
-            const float t = tb.ts[s];
-            const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
-            if (sd.ap_all || fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
-              // Eq. 19: tally the out-photon at its frequency shift
-              const int sr = tb.perm[s];
-              atomicAdd(&tb.hist[(size_t)sr * row + idx], W);
-              atomicAdd(&tb.hist[(size_t)sr * row + n_bins + 2], 1ull);
-              if (DUMP && sr < 64) dmask |= 1ull << sr;
+            for (int s = s0; s < s1; ++s) {
+              const float t = tb.ts[s];
+              const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
+              if (fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
+                // Eq. 19: tally the out-photon at its frequency shift
+                const int sr = tb.perm[s];
+                atomicAdd(&tb.hist[(size_t)sr * row + idx], W);
+                atomicAdd(&tb.hist[(size_t)sr * row + n_bins + 2], 1ull);
+                if (DUMP && sr < 64) dmask |= 1ull << sr;
+              }
             }
           }
         }
@@ -486,7 +499,7 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
     if (threadIdx.x < C_NCOUNT && s_cnt[threadIdx.x])
       atomicAdd(&sd.cnt[threadIdx.x], s_cnt[threadIdx.x]);
     if (HMODE == 2) {
-      const int nh = n_snap * row;
+      const int nh = tally_rows(n_snap, sd.ap_all) * row;
       for (int i = threadIdx.x; i < nh; i += blockDim.x) {
         const unsigned long long v = tb.hist[i];
         if (v) atomicAdd(&sd.hist[i], v);
@@ -703,7 +716,8 @@ __global__ void k_normalise(const SetDesc* __restrict__ sets, double* const* spe
   const int s = blockIdx.x;
   if (s >= sd.n_snap) return;
   const int n_bins = sd.n_bins, row = hist_row(n_bins);
-  const unsigned long long* h = sd.hist + (size_t)s * row;
+  // unlimited aperture: every time's tallies are those of row 0
+  const unsigned long long* h = sd.hist + (size_t)(sd.ap_all ? 0 : s) * row;
   double scale = 1.0 / (kTwo32 * (double)sd.norm_packets);
   if (flags[blockIdx.y] & PDV_PER_DV) scale *= sd.inv_dbin;
   double* out = spec[blockIdx.y] + (size_t)s * n_bins;

@@ -111,8 +111,10 @@ def test_cfg3_heavy_multiple_scattering(ctx, precision):
     dict(phase=W.Phase(kind="mie_iso", m=3.0 + 9.0j, n_angle=1801, n_size=64), d_m=1.5e-6,
          sigma_ln=0.5, m0=2 * W.MG_CM2, v_max=0.0),
     dict(r_ap=0.0, cone_alpha=2.0),
+    dict(r_ap=0.0, cone_alpha=2.0, t_snap=(0.5e-6, 1.0e-6, 3.0e-6)),
+    dict(r_ap=0.0, cone_alpha=0.5, t_snap=(1.0e-6, 0.7e-6, 2.0e-6, 4.0e-6)),
 ], ids=["lambert", "specular", "R0", "albedo1", "albedo0", "tabulated", "steep", "maxev2",
-        "onebin", "isotropic", "detect_all"])
+        "onebin", "isotropic", "detect_all", "detect_all_3t", "open_aperture_cone_4t"])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_variants(ctx, precision, kw):
     wl = W.cfg1(n_packets=50000, **WIDE).replace(**kw)

@@ -58,11 +58,12 @@ def test_cfg1_paper_layers(ctx):
          prof_f=[3.0, 1.0, 2.0, 0.2], v_max=0.0, m0=1 * W.MG_CM2),
     dict(n_layers=400, t_snap=(0.5e-6, 1e-6, 1.7e-6, 3e-6)),
     dict(n_layers=400, r_ap=0.0, cone_alpha=2.0),
+    dict(n_layers=400, r_ap=0.0, cone_alpha=0.5, t_snap=(1.0e-6, 0.7e-6, 2.0e-6)),
     dict(n_layers=300, max_events=500),
     dict(n_layers=400, phase=W.Phase(kind="mie", m=3.0 + 9.0j, n_angle=1801, n_size=32),
          d_m=1.5e-6, sigma_ln=0.5, m0=2 * W.MG_CM2, v_max=0.0, n_packets=8000),
 ], ids=["coarse", "fine", "lambert", "specular", "R0", "albedo1", "albedo0", "tabulated",
-        "snapshots", "detect_all", "step_limit", "mie"])
+        "snapshots", "detect_all", "open_aperture_3t", "step_limit", "mie"])
 def test_variants(ctx, kw):
     wl = W.cfg1(n_packets=kw.pop("n_packets", 20000), **WIDE).replace(**kw)
     out, ref = run_pair(ctx, wl)
