@@ -40,7 +40,7 @@ UNIT = "scatter events/s"
 # FP32 path: Philox4x32-10 (~80), free path and fixed-point update (~30),
 # velocity-table inversion (~20), phase-table inversion and theta (~16),
 # sin/cos of theta and phi (~30), rotation and renormalisation (~25), lateral
-# move, albedo test, Doppler sum and bookkeeping (~20): 220 (see DESIGN.md).
+# move, albedo test, Doppler sum and bookkeeping (~20): 220.
 ALGO_INST_PER_EVENT = 220.0
 SMS, SCHEDULERS, LANES, F_MAX_HZ = 152, 4, 32, 2.070e9
 
