@@ -282,3 +282,15 @@ def test_full_size_cfg2_sampled_packets(ctx):
     cloud.close()
     del pk, dev
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("seed,stream", [(11, 0), (2**63 + 12345, 7), (0xFFFFFFFF00000001, 2**31 + 3)],
+                         ids=["small", "high_word", "both_words"])
+def test_seed_and_stream_words(ctx, seed, stream):
+    """Philox key = (seed_lo, seed_hi) and counter word 3 = stream id: seeds that
+    use the high key word and large stream ids give the oracle's packets too,
+    in the exact scheme and in the layer-stepping scheme."""
+    for extra in (dict(), dict(n_layers=300)):
+        wl = W.cfg1(n_packets=20000, seed=seed, stream_id=stream, **WIDE).replace(**extra)
+        out, ref = run_pair(ctx, wl, "fp32")
+        compare(out, ref, wl, "fp32")
