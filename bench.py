@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mode", default="default",
                     choices=["default", "serve", "batch", "precision", "model", "extract-mc",
-                             "stepping", "spectrogram", "cpu-baseline"])
+                             "stepping", "spectrogram", "cpu-baseline", "fig12"])
     ap.add_argument("--times", type=int, default=512, help="snapshot times of the spectrogram mode")
     ap.add_argument("--out", default="", help="spectrogram mode: write the v-t image (PGM) here")
     ap.add_argument("--model-sets", type=int, default=100_000,
@@ -731,6 +731,73 @@ def extract_mc_mode(args):
     return 0
 
 
+def fig12_mode(args):
+    """The single-scattering model beside the Monte Carlo (Section III.B,
+    Fig. 12): for each area mass, the Monte Carlo spectrum of the cloud and the
+    model spectrum of Eq. 28 with tau0 = g_back tau_ext (the cloud's extinction
+    depth; g_back the paper's 0.67, and Eq. 25 evaluated for this cloud's own
+    scattering law), compared by shape (L1 distance of the unit-area spectra:
+    0 equal, 2 disjoint) and by main-peak position (the extraction pipeline on
+    all of them, Eq. 31 beside them); and the time of one spectrum by each."""
+    import numpy as np
+    import torch
+    from paper_2012_00963_gb300 import pdv
+    from paper_2012_00963_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = pdv.Context(0, stream=stream.cuda_stream)
+    g_back, beta, rows = 0.67, 10.0, []
+    for m0 in W.FIG12_MASSES:
+        wl = W.fig12(m0, n_packets=int(args.packets) if args.packets != 1e8 else 10_000_000)
+        cloud = pdv.Cloud(ctx, wl)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mc = pdv.simulate_spectrum(ctx, cloud, wl, per_dv=True)["spectrum"][0]
+        b.record(stream)
+        b.synchronize()
+        mc_ms = a.elapsed_time(b)
+        tau_ext = cloud.info()["tau_tot"]
+        cloud.close()
+        # Eq. 25 for this cloud's own scattering law: g_back = (K_back + K_abs) / K_ext,
+        # with K_back the scattering into the backward hemisphere of the phase table
+        th, pt, _, albedo = pdv.phase_table(ctx, wl)
+        w = pt * np.sin(th)
+        cum = np.concatenate([[0.0], np.cumsum(0.5 * (w[1:] + w[:-1]) * np.diff(th))])
+        back = 1.0 - np.interp(0.5 * math.pi, th, cum) / cum[-1]
+        g_own = albedo * back + (1.0 - albedo)
+        models = {}
+        for name, g in (("paper_g_back", g_back), ("own_g_back", g_own)):
+            tau0 = g * tau_ext
+            a.record(stream)
+            ss = pdv.ss_spectrum(ctx, [(beta, tau0, wl.v_fs, 0.0, 1.0)], wl.n_bins, wl.v_lo,
+                                 wl.v_hi, per_dv=True)[0]
+            b.record(stream)
+            b.synchronize()
+            models[name] = (g, tau0, ss, a.elapsed_time(b))
+        span = (wl.v_hi - wl.v_lo) / wl.v_fs
+        k_c = min(int(math.ceil(1.25 * beta * span)), wl.n_bins // 2 - 1)
+        pk = pdv.extract_peaks(ctx, np.stack([mc] + [m[2] for m in models.values()]), wl.v_lo,
+                               wl.v_hi, wl.v_fs, k_c, 1.02, 3.5)
+        row = {"m0_mg_cm2": m0, "tau_ext": tau_ext, "x_peak_mc": float(pk[0]["x_peak"]),
+               "status_mc": int(pk[0]["status"]), "mc_ms": mc_ms}
+        for i, (name, (g, tau0, ss, ms)) in enumerate(models.items()):
+            l1 = float(np.abs(mc / mc.sum() - ss / ss.sum()).sum()) if mc.sum() > 0 and ss.sum() > 0 else None
+            row[name] = {"g_back": g, "tau0": tau0, "x_peak_eq31": 1.0 + math.log(tau0) / beta,
+                         "x_peak_model": float(pk[1 + i]["x_peak"]),
+                         "status_model": int(pk[1 + i]["status"]), "shape_l1": l1, "model_ms": ms}
+        rows.append(row)
+    ctx.close()
+    print(json.dumps({"mode": "fig12",
+                      "metric": "shape and main-peak position of the single-scattering model vs the "
+                                "Monte Carlo spectrum (Eq. 28, Eq. 31)",
+                      "config": {"workload": "Fig. 12 clouds: beta 10, d_m 1.5 um, sigma 0.5, Mie 3+9i, "
+                                             "m0 5-40 mg/cm^2, every upward photon, 1200 bins "
+                                             "0-8000 m/s, t = 1 us; model with g_back = 0.67 and with "
+                                             "the cloud's own Eq. 25 value"},
+                      "rows": rows}))
+    return 0
+
+
 def stepping_mode(args):
     """The paper's own scheme (1000 layers, acceptance-rejection angles) on the
     workload its timings are quoted on (Fig. 4: 1e7 photons), against the exact
@@ -922,6 +989,8 @@ def main():
         return extract_mc_mode(args)
     if args.mode == "stepping":
         return stepping_mode(args)
+    if args.mode == "fig12":
+        return fig12_mode(args)
     if args.mode == "cpu-baseline":
         return cpu_baseline_mode(args)
     if args.mode == "spectrogram":

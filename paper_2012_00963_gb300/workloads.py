@@ -243,6 +243,22 @@ def fig13(cloud: int, beta: float, **kw) -> Workload:
     return wl.replace(**kw)
 
 
+FIG12_MASSES = (5.0, 10.0, 20.0, 40.0)      # mg/cm^2
+
+
+def fig12(m0_mg: float, **kw) -> Workload:
+    """A Monte Carlo case of the comparison with the single-scattering model
+    (Section III.B, Fig. 12): beta = 10, log-normal d_m = 1.5 um, sigma = 0.5,
+    area mass m0_mg (mg/cm^2); Mie 3+9i at 1550 nm, every upward photon
+    counted, 1200 bins over 0-8000 m/s at 1 us, 1e7 packets."""
+    wl = Workload(
+        name="fig12-m0-%g" % m0_mg, m0=m0_mg * MG_CM2, beta=10.0, v_max=0.0, d_m=1.5 * UM,
+        sigma_ln=0.5, phase=Phase(kind="mie", m=3.0 + 9.0j, n_angle=1801, n_size=256),
+        r_ap=0.0, cone_alpha=math.pi / 2, t_snap=(1.0 * US,), n_bins=1200, v_lo=0.0,
+        v_hi=8000.0, n_packets=10_000_000, seed=12)
+    return wl.replace(**kw)
+
+
 def fig4(**kw) -> Workload:
     """The convergence and timing case of Section II.D (Fig. 4; the paper's
     CPU / GPU timings are quoted on it): tin, beta = 10, log-normal d_m = 1.5
