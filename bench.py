@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mode", default="default",
                     choices=["default", "serve", "batch", "precision", "model", "extract-mc",
-                             "stepping", "spectrogram", "cpu-baseline", "fig12"])
+                             "stepping", "spectrogram", "cpu-baseline", "fig12", "fig6"])
     ap.add_argument("--times", type=int, default=512, help="snapshot times of the spectrogram mode")
     ap.add_argument("--out", default="", help="spectrogram mode: write the v-t image (PGM) here")
     ap.add_argument("--model-sets", type=int, default=100_000,
@@ -731,6 +731,59 @@ def extract_mc_mode(args):
     return 0
 
 
+def fig6_mode(args):
+    """Section II.D, Fig. 6, cases 1 and 2: the same cloud scattering by its
+    Mie phase function and isotropically (with the same Mie extinction and
+    albedo), every upward photon counted. For each case: the main peak (the
+    extraction pipeline), the detected fraction and the mean apparent
+    velocity; between them: the L1 distance of the unit-area spectra, split at
+    the Mie case's peak into the part below (the low-velocity, dense part of
+    the cloud) and above."""
+    import numpy as np
+    import torch
+    from paper_2012_00963_gb300 import pdv
+    from paper_2012_00963_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = pdv.Context(0, stream=stream.cuda_stream)
+    out, spec = {}, {}
+    for case in (1, 2):
+        wl = W.fig6(case, n_packets=int(args.packets) if args.packets != 1e8 else 10_000_000)
+        cloud = pdv.Cloud(ctx, wl)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = pdv.simulate_spectrum(ctx, cloud, wl, per_dv=True)
+        b.record(stream)
+        b.synchronize()
+        cloud.close()
+        s = r["spectrum"][0]
+        vc = wl.v_lo + (np.arange(wl.n_bins) + 0.5) * (wl.v_hi - wl.v_lo) / wl.n_bins
+        span = (wl.v_hi - wl.v_lo) / wl.v_fs
+        k_c = min(int(math.ceil(1.25 * wl.beta * span)), wl.n_bins // 2 - 1)
+        pk = pdv.extract_peaks(ctx, s, wl.v_lo, wl.v_hi, wl.v_fs, k_c, 1.02, 3.5)[0]
+        c = pdv.counters_dict(r["counters"][0])
+        spec[case] = (s, vc)
+        out["case%d" % case] = {"phase": "Mie" if case == 1 else "isotropic (Mie extinction and albedo)",
+                                "x_peak": float(pk["x_peak"]), "status": int(pk["status"]),
+                                "detected_fraction": c["w_detected"] / 2.0**32 / wl.n_packets,
+                                "mean_v_app_detected": float((s * vc).sum() / s.sum()),
+                                "mc_ms": a.elapsed_time(b)}
+    (s1, vc), (s2, _) = spec[1], spec[2]
+    d = np.abs(s1 / s1.sum() - s2 / s2.sum())
+    v_split = out["case1"]["x_peak"] * W.fig6(1).v_fs
+    ctx.close()
+    print(json.dumps({"mode": "fig6",
+                      "metric": "Mie vs isotropic scattering on the Fig. 6 cloud: peaks, detected "
+                                "fraction, and where the unit-area spectra differ",
+                      "config": {"workload": "Fig. 6 cloud: tin, m0 10.7 mg/cm^2, d_m 1.5 um, sigma 0.5, "
+                                             "beta 8, Mie 3+9i vs isotropic, every upward photon, "
+                                             "600 bins 0-8000 m/s, t = 1 us, 1e7 packets"},
+                      "case1": out["case1"], "case2": out["case2"],
+                      "shape_l1": float(d.sum()), "shape_l1_below_case1_peak": float(d[vc < v_split].sum()),
+                      "shape_l1_above_case1_peak": float(d[vc >= v_split].sum())}))
+    return 0
+
+
 def fig12_mode(args):
     """The single-scattering model beside the Monte Carlo (Section III.B,
     Fig. 12): for each area mass, the Monte Carlo spectrum of the cloud and the
@@ -989,6 +1042,8 @@ def main():
         return extract_mc_mode(args)
     if args.mode == "stepping":
         return stepping_mode(args)
+    if args.mode == "fig6":
+        return fig6_mode(args)
     if args.mode == "fig12":
         return fig12_mode(args)
     if args.mode == "cpu-baseline":
