@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mode", default="default",
                     choices=["default", "serve", "batch", "precision", "model", "extract-mc",
-                             "stepping", "spectrogram", "cpu-baseline", "fig12", "fig6"])
+                             "stepping", "spectrogram", "cpu-baseline", "fig12", "fig6", "trends"])
     ap.add_argument("--times", type=int, default=512, help="snapshot times of the spectrogram mode")
     ap.add_argument("--out", default="", help="spectrogram mode: write the v-t image (PGM) here")
     ap.add_argument("--model-sets", type=int, default=100_000,
@@ -731,6 +731,52 @@ def extract_mc_mode(args):
     return 0
 
 
+def trends_mode(args):
+    """Section III.A on this Monte Carlo: one parameter at a time around a
+    base cloud (beta 8, d_m 1.5 um, sigma 0.5, 10 mg/cm^2, Mie 3+9i, every
+    upward photon), the main peak position (extraction pipeline, window
+    x >= 1.02) and the share of the detected weight below v_fs, where the
+    free-surface echo lands."""
+    import numpy as np
+    import torch
+    from paper_2012_00963_gb300 import pdv
+    from paper_2012_00963_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    ctx = pdv.Context(0, stream=torch.cuda.current_stream().cuda_stream)
+    n = int(args.packets) if args.packets != 1e8 else 10_000_000
+    base = W.fig6(1, n_packets=n, m0=10.0 * W.MG_CM2, n_bins=800, seed=31)
+    sweeps = {"beta": [("beta", v, {"beta": v}) for v in (4.0, 8.0, 12.0)],
+              "d_m_um": [("d_m_um", v, {"d_m": v * W.UM}) for v in (1.0, 2.0, 4.0)],
+              "m0_mg_cm2": [("m0_mg_cm2", v, {"m0": v * W.MG_CM2}) for v in (2.0, 5.0, 10.0, 20.0)]}
+    out = {}
+    for key, cases in sweeps.items():
+        rows = []
+        for _, v, kw in cases:
+            wl = base.replace(**kw)
+            cloud = pdv.Cloud(ctx, wl)
+            r = pdv.simulate_spectrum(ctx, cloud, wl, per_dv=True)
+            tau = cloud.info()["tau_tot"]
+            cloud.close()
+            sp = r["spectrum"][0]
+            vc = wl.v_lo + (np.arange(wl.n_bins) + 0.5) * (wl.v_hi - wl.v_lo) / wl.n_bins
+            span = (wl.v_hi - wl.v_lo) / wl.v_fs
+            k_c = min(int(math.ceil(1.25 * wl.beta * span)), wl.n_bins // 2 - 1)
+            pk = pdv.extract_peaks(ctx, sp, wl.v_lo, wl.v_hi, wl.v_fs, k_c, 1.02, 6.0)[0]
+            rows.append({key: v, "tau_ext": tau, "x_peak": float(pk["x_peak"]),
+                         "status": int(pk["status"]),
+                         "share_below_v_fs": float(sp[vc < wl.v_fs].sum() / sp.sum())})
+        out[key] = rows
+    ctx.close()
+    print(json.dumps({"mode": "trends",
+                      "metric": "main-peak position and free-surface share of Monte Carlo spectra "
+                                "against beta, particle size and area mass (Section III.A)",
+                      "config": {"workload": "base: tin, beta 8, d_m 1.5 um, sigma 0.5, 10 mg/cm^2, "
+                                             "Mie 3+9i, every upward photon, 800 bins 0-8000 m/s, "
+                                             "t = 1 us, %d packets per case" % n},
+                      "sweeps": out}))
+    return 0
+
+
 def fig6_mode(args):
     """Section II.D, Fig. 6, cases 1 and 2: the same cloud scattering by its
     Mie phase function and isotropically (with the same Mie extinction and
@@ -1042,6 +1088,8 @@ def main():
         return extract_mc_mode(args)
     if args.mode == "stepping":
         return stepping_mode(args)
+    if args.mode == "trends":
+        return trends_mode(args)
     if args.mode == "fig6":
         return fig6_mode(args)
     if args.mode == "fig12":
