@@ -19,7 +19,9 @@
 // Both kernels transport a packet once and test detection at every snapshot
 // time: the cloud is self-similar (z = v t, Section II.C), so event decisions
 // and the Doppler sum do not depend on t, and the lateral position at time t
-// is x0 + t X with X accumulated in velocity units.
+// is x0 + t X with X accumulated in velocity units. With an unlimited aperture
+// every time detects alike; the FP32 kernel then tallies one histogram row,
+// which the normalisation reads for every time.
 #include <math.h>
 
 #include "pdv_internal.cuh"
