@@ -53,6 +53,31 @@ def test_batch_with_mixed_precision_and_multi_snapshot(ctx):
         c.close()
 
 
+@pytest.mark.parametrize("hist_mode", [1, 2])
+def test_batch_mixes_open_and_finite_apertures(ctx, hist_mode):
+    """Sets with an unlimited aperture tally one histogram row for all their
+    snapshot times; in a batch beside aperture-limited sets, and with global
+    or privatised histograms, every set equals its run alone."""
+    wls = small_sets(4)
+    wls[0] = wls[0].replace(r_ap=0.0, t_snap=(1e-6, 2e-6, 3e-6))
+    wls[1] = wls[1].replace(r_ap=0.0, cone_alpha=2.0, t_snap=(3e-6, 1e-6))
+    wls[2] = wls[2].replace(t_snap=(1e-6, 2.5e-6))
+    clouds = [pdv.Cloud(ctx, w) for w in wls]
+    alone = [pdv.simulate_spectrum(ctx, c, w) for c, w in zip(clouds, wls)]
+    ctx.set_tuning(hist_mode=hist_mode)
+    try:
+        batch = pdv.simulate_batch(ctx, clouds, wls)
+    finally:
+        ctx.set_tuning()
+    for w, a, b in zip(wls, alone, batch):
+        assert np.array_equal(a["raw"], b["raw"])
+        assert np.array_equal(a["counters"], b["counters"])
+        if w.r_ap <= 0.0:
+            assert all(np.array_equal(a["raw"][0], row) for row in a["raw"][1:])
+    for c in clouds:
+        c.close()
+
+
 def test_autotune_keeps_results(ctx):
     wls = small_sets(6)
     clouds = [pdv.Cloud(ctx, w) for w in wls]
