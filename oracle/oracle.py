@@ -24,14 +24,14 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-NCOUNTERS = 14
+NCOUNTERS = 16
 NORDER = 5
 COUNTER_NAMES = [
     "launched", "events", "scatters", "surface_hits", "escapes", "detected",
     "w_detected", "w_under", "w_over", "w_escaped_undetected", "w_absorbed_particle",
-    "w_absorbed_surface", "w_truncated", "truncated",
+    "w_absorbed_surface", "w_truncated", "truncated", "w_roulette_dropped", "w_roulette_gained",
 ]
-FATE_ESCAPED, FATE_ABS_PARTICLE, FATE_ABS_SURFACE, FATE_TRUNCATED = 1, 2, 3, 4
+FATE_ESCAPED, FATE_ABS_PARTICLE, FATE_ABS_SURFACE, FATE_TRUNCATED, FATE_DROPPED = 1, 2, 3, 4, 5
 
 
 def build(force: bool = False) -> str:
@@ -63,6 +63,7 @@ class _Problem(C.Structure):
         ("n_bins", C.c_int), ("v_lo", C.c_double), ("v_hi", C.c_double),
         ("packet_begin", C.c_uint64), ("n_packets", C.c_uint64), ("seed", C.c_uint64),
         ("stream_id", C.c_uint32), ("max_events", C.c_uint32), ("n_layers", C.c_uint32),
+        ("implicit_capture", C.c_uint32),
     ]
 
 
@@ -270,6 +271,7 @@ class Problem:
         pb.stream_id = wl.stream_id
         pb.max_events = wl.max_events
         pb.n_layers = getattr(wl, "n_layers", 0)
+        pb.implicit_capture = int(bool(getattr(wl, "implicit_capture", False)))
         self.pb = pb
         self.q_ext = q_ext
         self.albedo = albedo

@@ -17,7 +17,9 @@
  *   - the apparent velocity is v_app = 1/2 sum_k (u_z,out - u_z,in) v_k over
  *     particle scatterings and free-surface reflections (Eq. 4 and Eq. 18 with
  *     the sign that makes an approaching scatterer blueshift);
- *   - the spectrum counts escaping packets by apparent velocity (Eq. 19).
+ *   - the spectrum counts escaping packets by apparent velocity (Eq. 19);
+ *   - optionally (implicit_capture) the absorption choice of Eq. 11 is
+ *     replaced by weight reduction with Russian roulette.
  * With n_layers > 0 the paper's own scheme runs instead (orc_transport_stepped:
  * steps of H / n_layers with a Bernoulli pass per layer, acceptance-rejection
  * angles), with the readings stated there.
@@ -608,8 +610,30 @@ static void orc_transport(const orc_setup* st, uint64_t pk, double t, orc_tally*
       vcur = vn;
       ++nev;
       ta->cnt[ORC_EVENTS] += 1;
-      /* Step (4), Eq. 11: scatter with probability K_sca/K_ext */
-      if (orc_m24(r[1]) < st->omega_q) {
+      /* Step (4), Eq. 11: scatter with probability K_sca/K_ext (analog), or
+       * always scatter carrying the fraction K_sca/K_ext of the weight
+       * (implicit capture, with the roulette on the same draw r1) */
+      int scatter;
+      if (!pb->implicit_capture) {
+        scatter = orc_m24(r[1]) < st->omega_q;
+      } else {
+        uint64_t Wn = (W * (uint64_t)st->omega_q + ((uint64_t)1 << 23)) >> 24;
+        ta->cnt[ORC_W_ABS_PARTICLE] += W - Wn;
+        W = Wn;
+        scatter = 1;
+        if (W < ORC_RR_W) {
+          if (W > 0 && orc_m24(r[1]) < (1u << 24) / ORC_RR_M) {
+            ta->cnt[ORC_W_RR_GAINED] += (ORC_RR_M - 1) * W;
+            W *= ORC_RR_M;
+          } else {
+            ta->cnt[ORC_W_RR_DROPPED] += W;
+            orc_trace_put(trace, max_v, &nv, x, y, z, vn, u, 4);
+            fate = ORC_FATE_DROPPED;
+            break;
+          }
+        }
+      }
+      if (scatter) {
         double th = orc_phase_sample(pb->n_phase, pb->theta, st->cq, orc_m24(r[2]));
         double ph = 2.0 * ORC_PI * orc_u01(r[3]);              /* Eq. 15 */
         double uz_old = u[2];
@@ -863,6 +887,7 @@ int orc_simulate(const orc_problem* pb, int n_threads, uint64_t* hist, uint64_t*
   if (orc_cloud_constants(pb, &st.tau_tot, NULL, NULL, &st.d_s) != 0) return -1;
   if (orc_setup_profile(&st, pb) != 0) { free(st.M); return -1; }
   if (!(pb->reflectivity >= 0.0 && pb->reflectivity <= 1.0) ||
+      (pb->implicit_capture && pb->n_layers > 0) ||
       !(pb->albedo >= 0.0 && pb->albedo <= 1.0) || pb->n_bins < 1 || !(pb->v_hi > pb->v_lo) ||
       pb->n_snap < 1 || !(pb->r_beam >= 0.0) || pb->surface_mode < 0 || pb->surface_mode > 2) {
     free(st.M);

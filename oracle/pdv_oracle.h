@@ -29,7 +29,11 @@
  *                          time invariance, Doppler = -1/2 dL/dt);
  *                          the full multiple-scattering spectrum beyond those
  *                          invariants is "parity unpinned" (the paper prints
- *                          no spectrum values).
+ *                          no spectrum values). Implicit capture is pinned
+ *                          by the reductions omega = 1 (the analog walk) and
+ *                          omega = 0 (the analog absorbed weight), the weight
+ *                          law W = 2^32 omega^k 16^j of the k-scatter escapes,
+ *                          its conservation identity and the analog means.
  */
 #ifndef PDV_ORACLE_H
 #define PDV_ORACLE_H
@@ -56,11 +60,21 @@ enum {
   ORC_W_ABS_SURFACE,     /* weight absorbed by the free surface (1 - R)       */
   ORC_W_TRUNCATED,       /* weight of packets stopped by the event limit      */
   ORC_TRUNCATED,         /* packets stopped by the event limit                */
+  ORC_W_RR_DROPPED,      /* implicit capture: weight dropped by the roulette  */
+  ORC_W_RR_GAINED,       /* implicit capture: weight survivors gained         */
   ORC_NCOUNTERS
 };
 
 enum { ORC_FATE_ESCAPED = 1, ORC_FATE_ABS_PARTICLE = 2, ORC_FATE_ABS_SURFACE = 3,
-       ORC_FATE_TRUNCATED = 4 };
+       ORC_FATE_TRUNCATED = 4, ORC_FATE_DROPPED = 5 };
+
+/* Implicit capture with Russian roulette (a variance-reduction variant of
+ * Section II.B step (4); the paper itself uses the analog choice of Eq. 11):
+ * the packet keeps round(W omega_q / 2^24) at each particle interaction and,
+ * below ORC_RR_W, survives with probability 1/ORC_RR_M at ORC_RR_M times
+ * its weight. */
+#define ORC_RR_W ((uint64_t)1 << 22)   /* threshold, 2^32 fixed point      */
+#define ORC_RR_M 16u                   /* survival 1 in 16, weight x 16    */
 
 #define ORC_NORDER 5   /* scattering-order histograms: orders 0..3 and 4+ */
 
@@ -104,6 +118,8 @@ typedef struct {
                             stepping it bounds the steps                       */
   uint32_t n_layers;     /* 0: exact free paths; > 0: the paper's synchronous
                             stepping, H / n_layers per step (Section II.B)     */
+  uint32_t implicit_capture; /* 1: implicit capture + roulette (exact free
+                            paths only); 0: the analog choice of Eq. 11        */
 } orc_problem;
 
 typedef struct {

@@ -84,6 +84,7 @@ class Workload:
     stream_id: int = 0
     max_events: int = 1_000_000       # with layer stepping: the step limit
     n_layers: int = 0                 # 0 exact free paths; > 0 the paper's H / n_layers steps
+    implicit_capture: bool = False    # weight omega per interaction + Russian roulette (exact paths)
     precision: str = "fp32"           # "fp32" | "fp64"
     name: str = "custom"
 
