@@ -228,6 +228,7 @@ def our_arm(args):
     stream = torch.cuda.current_stream(dev)
     wl = workload(args, rank)
     ns, nb = len(wl.t_snap), wl.n_bins
+    NC = len(pdv.COUNTER_NAMES)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -240,9 +241,9 @@ def our_arm(args):
     th_pin = torch.from_numpy(np.ascontiguousarray(table[0])).pin_memory()
     p_pin = torch.from_numpy(np.ascontiguousarray(table[1])).pin_memory()
     dev_out = {"spectrum": torch.zeros(ns * nb, dtype=torch.float64, device=dev),
-               "counters": torch.zeros(ns * 14, dtype=torch.int64, device=dev)}
+               "counters": torch.zeros(ns * NC, dtype=torch.int64, device=dev)}
     host_spec = torch.zeros(ns * nb, dtype=torch.float64).pin_memory()
-    host_cnt = torch.zeros(ns * 14, dtype=torch.int64).pin_memory()
+    host_cnt = torch.zeros(ns * NC, dtype=torch.int64).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     tbl = (th_pin.numpy(), p_pin.numpy(), table[2], table[3])
 
@@ -260,7 +261,7 @@ def our_arm(args):
         return ev, ctx.stats()["last_transport_ms"]
 
     def scat_per_step():
-        return int(dev_out["counters"].view(ns, 14)[0, 2].item())
+        return int(dev_out["counters"].view(ns, NC)[0, 2].item())
 
     def timed(precision, device_outputs, steps, warmup):
         for _ in range(warmup):

@@ -55,6 +55,19 @@ enum { PDV_PREC_FP32 = 0, PDV_PREC_FP64 = 1 };
 #define PDV_PER_DV     0x2u   /* spectrum divided by the bin width (per m/s)   */
 #define PDV_IN_DEVICE  0x4u   /* input arrays are device pointers (pdv_ss_spectrum,
                                  pdv_extract_peaks)                            */
+/* Implicit capture with Russian roulette, in place of the analog absorption
+ * of Eq. 11 (Section II.B step (4)); off by default, exact free paths only
+ * (n_layers == 0), both precisions. At every particle interaction the packet
+ * scatters and keeps W' = floor((W omega_q + 2^23) / 2^24) of its weight
+ * (omega_q = round(omega 2^24)); W - W' is absorbed by the particle. If
+ * W' < PDV_ROULETTE_W the packet survives when (r1 >> 8) < PDV_ROULETTE_Q
+ * (probability 1/16) with weight 16 W', else (and always when W' = 0) it is
+ * dropped (fate 5). The expectation of every tally is that of the analog
+ * scheme. */
+#define PDV_IMPLICIT_CAPTURE 0x8u
+#define PDV_ROULETTE_W (1ull << 22)  /* threshold, 2^32 fixed point (2^-10) */
+#define PDV_ROULETTE_Q (1u << 20)    /* survival bound on r1 >> 8 (1/16)   */
+#define PDV_ROULETTE_M 16u           /* survivor's weight factor           */
 
 /* Optional device allocator (NULL: cudaMallocAsync/cudaFreeAsync on the
  * context stream). Both callbacks are called from library threads. */
@@ -101,17 +114,21 @@ typedef struct {
 
 /* Per-snapshot tallies. Weights are 2^32 fixed point per launched packet;
  * w_detected + w_under + w_over + w_escaped_undetected + w_absorbed_particle
- * + w_absorbed_surface + w_truncated == launched * 2^32 exactly. */
+ * + w_absorbed_surface + w_truncated + w_roulette_dropped
+ * == launched * 2^32 + w_roulette_gained exactly (the last two are 0 unless
+ * PDV_IMPLICIT_CAPTURE is set: the weight of dropped packets, and the
+ * weight that survivors gained, (PDV_ROULETTE_M - 1) W' each). */
 typedef struct {
   uint64_t launched, events, scatters, surface_hits, escapes, detected;
   uint64_t w_detected, w_under, w_over, w_escaped_undetected;
   uint64_t w_absorbed_particle, w_absorbed_surface, w_truncated, truncated;
+  uint64_t w_roulette_dropped, w_roulette_gained;
 } pdv_counters;
 
 /* Per-packet record (debug / parity dumps; snapshot 0 unless stated). */
 typedef struct {
-  uint32_t n_events, n_scatters, n_surface, fate;  /* fate: 1 escaped, 2 absorbed by a particle, 3 absorbed at the surface, 4 truncated */
-  uint64_t weight;                                 /* final weight, 2^32 fixed point */
+  uint32_t n_events, n_scatters, n_surface, fate;  /* fate: 1 escaped, 2 absorbed by a particle, 3 absorbed at the surface, 4 truncated, 5 dropped by the roulette */
+  uint64_t weight;                                 /* weight when the fate was decided, 2^32 fixed point */
   double v_app;                                    /* apparent velocity, m/s */
   uint64_t detect_mask;                            /* bit s: detected at snapshot s < 64 */
 } pdv_packet_record;
@@ -135,7 +152,7 @@ typedef struct {
   int n_bins;                      /* 1..65536                           */
   double v_lo, v_hi;               /* m/s, v_hi > v_lo                   */
   int precision;                   /* PDV_PREC_FP32 | PDV_PREC_FP64      */
-  uint32_t flags;                  /* PDV_OUT_DEVICE | PDV_PER_DV        */
+  uint32_t flags;                  /* PDV_OUT_DEVICE | PDV_PER_DV | PDV_IMPLICIT_CAPTURE */
   double* out_spectrum;            /* [n_snap * n_bins], required        */
   uint64_t* out_raw;               /* optional [n_snap * (n_bins + 2)]: under, bins, over */
   pdv_counters* out_counters;      /* optional [n_snap]                  */

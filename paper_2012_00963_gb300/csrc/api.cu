@@ -581,10 +581,12 @@ static pdv_status validate_request(const pdv_request* r) {
   if (!r->out_spectrum) return fail(PDV_EINVAL, "out_spectrum is required");
   if (r->out_packets && r->n_packets > ((r->flags & PDV_OUT_DEVICE) ? (1ull << 28) : (1ull << 26)))
     return fail(PDV_EINVAL, "packet dumps need n_packets <= 2^26 (2^28 into device memory)");
-  if (r->flags & ~(PDV_OUT_DEVICE | PDV_PER_DV)) return fail(PDV_EINVAL, "unknown flags");
+  if (r->flags & ~(PDV_OUT_DEVICE | PDV_PER_DV | PDV_IMPLICIT_CAPTURE)) return fail(PDV_EINVAL, "unknown flags");
   if (r->reserved) return fail(PDV_EINVAL, "reserved must be 0");
   if (r->n_layers && r->precision != PDV_PREC_FP32)
     return fail(PDV_EINVAL, "the layer-stepping scheme runs in FP32");
+  if (r->n_layers && (r->flags & PDV_IMPLICIT_CAPTURE))
+    return fail(PDV_EINVAL, "implicit capture runs with exact free paths only (n_layers = 0)");
   const pdv_probe& pr = r->probe;
   if (!(pr.z_probe_mm > 0) || !(pr.beam_radius_mm >= 0) || !std::isfinite(pr.aperture_radius_mm) ||
       !(pr.cone_half_angle_rad > 0))
@@ -614,6 +616,8 @@ static SetDesc make_set(const pdv_request* r) {
   d.omega_q = (unsigned)std::floor(cl->albedo * 16777216.0 + 0.5);
   d.stream_id = r->stream_id;
   d.max_events = r->max_events ? r->max_events : 1000000u;
+  d.implicit = (r->flags & PDV_IMPLICIT_CAPTURE) ? 1u : 0u;
+  d.absorb_gate = d.implicit ? 0u : d.omega_q;
   d.R_q = (unsigned long long)std::floor(cl->desc.reflectivity * kTwo32 + 0.5);
   d.seed = r->seed;
   d.packet_begin = r->packet_begin;
@@ -702,11 +706,11 @@ static int pick_hist_mode(const pdv_ctx* c, const SetDesc& d) {
 }
 
 // Launch geometry of the persistent FP32 kernel for given shared memory.
-static pdv_status f32_geometry(pdv_ctx* c, size_t smem, int hist_mode, bool dump, int* grid,
-                               int* block) {
+static pdv_status f32_geometry(pdv_ctx* c, size_t smem, int hist_mode, bool dump, bool impl,
+                               int* grid, int* block) {
   const int bt = c->tuning.block_threads ? c->tuning.block_threads : 256;
   int occ = 0;
-  CK(transport_f32_occupancy(bt, smem, hist_mode, dump, &occ));
+  CK(transport_f32_occupancy(bt, smem, hist_mode, dump, impl, &occ));
   if (occ < 1) return fail(PDV_EINVAL, "tables need %zu bytes of shared memory, too many for one block", smem);
   int bps = c->tuning.blocks_per_sm ? std::min(c->tuning.blocks_per_sm, occ) : occ;
   *grid = c->sm_count * bps;
@@ -768,10 +772,11 @@ static pdv_status enqueue_transport(pdv_ctx* c, const pdv_request* r, const SetD
     const size_t smem = set_smem(d, hm);
     if (smem > (size_t)c->max_smem) return fail(PDV_EINVAL, "tables need %zu bytes of shared memory (max %d)", smem, c->max_smem);
     int grid = 0, block = 0;
-    pdv_status s = f32_geometry(c, smem, hm, dump, &grid, &block);
+    const bool impl = d.implicit != 0;
+    pdv_status s = f32_geometry(c, smem, hm, dump, impl, &grid, &block);
     if (s != PDV_OK) return s;
     launch_transport_f32((const SetDesc*)(base + b.o_set), 1,
-                         (unsigned long long*)(base + b.o_ctr), grid, block, smem, hm, dump, st);
+                         (unsigned long long*)(base + b.o_ctr), grid, block, smem, hm, dump, impl, st);
     c->last_grid = grid;
     c->last_block = block;
   } else {
@@ -921,11 +926,12 @@ static pdv_status run_batch_f32(pdv_ctx* c, const pdv_request* rs, int n, bool t
   std::vector<SetDesc> sets(n);
   size_t smem = 0;
   int hm = 2;
-  bool dump = false;
+  bool dump = false, impl = false;
   for (int i = 0; i < n; ++i) {
     sets[i] = make_set(&rs[i]);
     if (pick_hist_mode(c, sets[i]) == 1) hm = 1;
     dump = dump || rs[i].out_packets != nullptr;
+    impl = impl || sets[i].implicit != 0;
   }
   for (int i = 0; i < n; ++i) {
     const SetDesc& d = sets[i];
@@ -933,7 +939,7 @@ static pdv_status run_batch_f32(pdv_ctx* c, const pdv_request* rs, int n, bool t
   }
   if (smem > (size_t)c->max_smem) return fail(PDV_EINVAL, "batch tables need %zu bytes of shared memory", smem);
   int grid = 0, block = 0;
-  pdv_status s = f32_geometry(c, smem, hm, dump, &grid, &block);
+  pdv_status s = f32_geometry(c, smem, hm, dump, impl, &grid, &block);
   if (s != PDV_OK) return s;
   const std::string key = batch_key(c, rs, n, grid, block, smem, hm, dump);
   pdv_ctx::GraphEntry* ge = nullptr;
@@ -968,7 +974,7 @@ static pdv_status run_batch_f32(pdv_ctx* c, const pdv_request* rs, int n, bool t
       cudaMemsetAsync(base + B.o_hist, 0, sizeof(unsigned long long) * B.hist_words, cap);
       cudaEventRecordWithFlags(c->ev0, cap, cudaEventRecordExternal);
       launch_transport_f32((const SetDesc*)(base + B.o_sets), n,
-                           (unsigned long long*)(base + B.o_ctr), grid, block, smem, hm, dump, cap);
+                           (unsigned long long*)(base + B.o_ctr), grid, block, smem, hm, dump, impl, cap);
       cudaEventRecordWithFlags(c->ev1, cap, cudaEventRecordExternal);
       int max_snap = 1;
       for (int i = 0; i < n; ++i) max_snap = std::max(max_snap, rs[i].n_snap);
@@ -1337,12 +1343,14 @@ static void serving_loop(pdv_ctx* c) {
     const int n = (int)items.size();
     size_t smem = 0;
     int hm = 1;
+    bool impl = false;
     for (int k = 0; k < n; ++k) {
       const SetDesc& d = s.h_sets[k];
       smem = std::max(smem, set_smem(d, 1));
+      impl = impl || d.implicit != 0;
     }
     int grid = 0, block = 0;
-    if (f32_geometry(c, smem, hm, false, &grid, &block) != PDV_OK) {
+    if (f32_geometry(c, smem, hm, false, impl, &grid, &block) != PDV_OK) {
       std::lock_guard<std::mutex> lk(c->smu);
       for (auto& it : items) {
         it.first->state = 3;
@@ -1355,7 +1363,8 @@ static void serving_loop(pdv_ctx* c) {
     cudaMemcpyAsync(s.d_mem, s.h_sets, sizeof(SetDesc) * n, cudaMemcpyHostToDevice, c->serve_stream);
     unsigned long long* ctr = (unsigned long long*)(s.d_mem + sizeof(SetDesc) * kMaxLaunchSets);
     cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * n, c->serve_stream);
-    launch_transport_f32((const SetDesc*)s.d_mem, n, ctr, grid, block, smem, hm, false, c->serve_stream);
+    launch_transport_f32((const SetDesc*)s.d_mem, n, ctr, grid, block, smem, hm, false, impl,
+                         c->serve_stream);
     c->launches += 1;
     cudaEventRecord(s.ev, c->serve_stream);
     s.items = std::move(items);
@@ -1613,10 +1622,11 @@ extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request
   const size_t smem = set_smem(d, hm);
   if (smem > (size_t)c->max_smem) return fail(PDV_EINVAL, "tables need %zu bytes of shared memory", smem);
   int grid = 0, block = 0;
-  s = f32_geometry(c, smem, hm, dump, &grid, &block);
+  const bool impl = d.implicit != 0;
+  s = f32_geometry(c, smem, hm, dump, impl, &grid, &block);
   if (s != PDV_OK) return s;
   launch_transport_f32((const SetDesc*)(base + o_set), 1, (unsigned long long*)(base + o_ctr),
-                       grid, block, smem, hm, dump, st);
+                       grid, block, smem, hm, dump, impl, st);
   launch_normalise((const SetDesc*)(base + o_set), 1, (double* const*)(base + o_ptr),
                    (pdv_counters* const*)(base + o_ptr + sizeof(void*)),
                    (unsigned long long* const*)(base + o_ptr + 2 * sizeof(void*)),

@@ -39,6 +39,8 @@ enum Counter {
   C_W_ABS_SURFACE,
   C_W_TRUNCATED,
   C_TRUNCATED,
+  C_W_RR_DROPPED,       // weight of packets dropped by the roulette
+  C_W_RR_GAINED,        // weight the roulette's survivors gained
   C_NCOUNT
 };
 
@@ -81,7 +83,9 @@ struct SetDesc {
   int n_v, n_g, g_shift, n_p;
   int n_snap, n_bins;
   int surface_mode, cone_all, ap_all, phase_uniform;   // theta_i = pi i / (n_p - 1)
-  unsigned omega_q, stream_id, max_events, pad1;
+  unsigned omega_q, stream_id, max_events;
+  unsigned implicit;                  // PDV_IMPLICIT_CAPTURE: weight omega per interaction + roulette
+  unsigned absorb_gate;               // r1 >> 8 at or above it leaves the scatter path: omega_q, or 0 (implicit)
   unsigned long long R_q, seed, packet_begin, n_packets;
   unsigned long long norm_packets;    // packets of the whole request (normalisation)
   double tau_tot, inv_tau, v_bot, dv, v_top, v_fs;
@@ -164,8 +168,10 @@ __device__ __forceinline__ float u64_to_f(unsigned long long d) {
 }
 
 // Kernel entry points (defined in the .cu files).
+// impl: some set of the launch has PDV_IMPLICIT_CAPTURE (a kernel build that
+// holds the implicit-capture branch; the analog build leaves it out).
 void launch_transport_f32(const SetDesc* d_sets, int n_sets, unsigned long long* d_set_ctr,
-                          int grid, int block, size_t smem, int hist_mode, bool dump,
+                          int grid, int block, size_t smem, int hist_mode, bool dump, bool impl,
                           cudaStream_t st);
 void launch_transport_f64(const SetDesc* d_set, int grid, int block, cudaStream_t st);
 void launch_normalise(const SetDesc* d_sets, int n_sets, double* const* d_spec,
@@ -174,7 +180,8 @@ void launch_normalise(const SetDesc* d_sets, int n_sets, double* const* d_spec,
 size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode,
                           int phase_uniform, int ap_all);
 int transport_f32_max_smem();
-cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, int* blocks);
+cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, bool impl,
+                                    int* blocks);
 
 cudaError_t build_mass_table(int kind, double beta, double v_fs, double v_bot, double v_top,
                              const double* d_prof_v, const double* d_prof_f, int prof_n,

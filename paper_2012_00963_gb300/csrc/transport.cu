@@ -22,6 +22,12 @@
 // is x0 + t X with X accumulated in velocity units. With an unlimited aperture
 // every time detects alike; the FP32 kernel then tallies one histogram row,
 // which the normalisation reads for every time.
+//
+// With PDV_IMPLICIT_CAPTURE an interaction always scatters and scales the
+// weight by omega in 2^32 fixed point; a packet below PDV_ROULETTE_W survives
+// the roulette on the r1 draw (the analog scheme's Eq. 11 draw) with
+// probability 1/16 at 16 times the weight. The roulette's rare weight sums go
+// to shared atomics; the absorbed weight joins the per-lane sum.
 #include <math.h>
 
 #include "pdv_internal.cuh"
@@ -127,7 +133,7 @@ __device__ __forceinline__ void launch_position(unsigned long long pk, unsigned 
   y0 = rad * sp;
 }
 
-template <bool DUMP, int HMODE>
+template <bool DUMP, int HMODE, bool IMPL>
 __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restrict__ sets,
                                                           int n_sets,
                                                           unsigned long long* __restrict__ set_ctr) {
@@ -385,9 +391,28 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
               sd.R_q >= (1ull << 32) ? W : ((W * sd.R_q + (1ull << 31)) >> 32);
           if (Wn != W) atomicAdd(&s_cnt[C_W_ABS_SURFACE], W - Wn);
           W = Wn;
-        } else if ((r.y >> 8) >= sd.omega_q) {
-          st_wabs += W;                                       // Eq. 11: absorbed
-          fate = 2;
+        } else if ((r.y >> 8) >= (IMPL ? sd.absorb_gate : sd.omega_q)) {
+          // analog: Eq. 11 absorbs (the gate is omega_q). Implicit capture
+          // (gate 0, always here): the particle absorbs 1 - omega of the
+          // weight and the packet scatters; a light packet plays the roulette
+          // on r1. Launches without implicit sets compile this out.
+          if (!IMPL || !sd.implicit) {
+            st_wabs += W;
+            fate = 2;
+          } else {
+            const unsigned long long Wn = (W * sd.omega_q + (1ull << 23)) >> 24;
+            st_wabs += W - Wn;
+            W = Wn;
+            if (Wn < PDV_ROULETTE_W) {
+              if (Wn != 0 && (r.y >> 8) < PDV_ROULETTE_Q) {
+                atomicAdd(&s_cnt[C_W_RR_GAINED], (PDV_ROULETTE_M - 1) * Wn);
+                W = Wn * PDV_ROULETTE_M;
+              } else {
+                atomicAdd(&s_cnt[C_W_RR_DROPPED], Wn);
+                fate = 5;
+              }
+            }
+          }
         }
         if (fate == 0) {
           // New direction. Particle scattering (Eq. 13-17): polar angle from the
@@ -511,9 +536,15 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
   }
 }
 
-static const void* f32_kernel(int hist_mode, bool dump) {
-  if (dump) return hist_mode == 2 ? (const void*)k_transport_f32<true, 2> : (const void*)k_transport_f32<true, 1>;
-  return hist_mode == 2 ? (const void*)k_transport_f32<false, 2> : (const void*)k_transport_f32<false, 1>;
+template <bool IMPL>
+static const void* f32_kernel_impl(int hist_mode, bool dump) {
+  if (dump)
+    return hist_mode == 2 ? (const void*)k_transport_f32<true, 2, IMPL> : (const void*)k_transport_f32<true, 1, IMPL>;
+  return hist_mode == 2 ? (const void*)k_transport_f32<false, 2, IMPL> : (const void*)k_transport_f32<false, 1, IMPL>;
+}
+
+static const void* f32_kernel(int hist_mode, bool dump, bool impl) {
+  return impl ? f32_kernel_impl<true>(hist_mode, dump) : f32_kernel_impl<false>(hist_mode, dump);
 }
 
 int transport_f32_max_smem() {
@@ -523,17 +554,18 @@ int transport_f32_max_smem() {
   return v - (int)(sizeof(SetDesc) + sizeof(unsigned long long) * C_NCOUNT + 64);
 }
 
-cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, int* blocks) {
-  const void* k = f32_kernel(hist_mode, dump);
+cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, bool impl,
+                                    int* blocks) {
+  const void* k = f32_kernel(hist_mode, dump, impl);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, block, smem);
 }
 
 void launch_transport_f32(const SetDesc* d_sets, int n_sets, unsigned long long* d_set_ctr,
-                          int grid, int block, size_t smem, int hist_mode, bool dump,
+                          int grid, int block, size_t smem, int hist_mode, bool dump, bool impl,
                           cudaStream_t st) {
-  const void* k = f32_kernel(hist_mode, dump);
+  const void* k = f32_kernel(hist_mode, dump, impl);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   void* args[] = {(void*)&d_sets, (void*)&n_sets, (void*)&d_set_ctr};
   cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, st);
@@ -647,7 +679,31 @@ __global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict
         S = Sn;
         vcur = vn;
         ++nev; ++st_events;
-        if ((r.y >> 8) < sd.omega_q) {
+        bool scatter;
+        if (!sd.implicit) {
+          scatter = (r.y >> 8) < sd.omega_q;               // Eq. 11
+          if (!scatter) {
+            atomicAdd(&s_cnt[C_W_ABS_PARTICLE], W);
+            fate = 2;
+          }
+        } else {
+          // implicit capture with the roulette on r1 (as in the FP32 kernel)
+          const unsigned long long Wn = (W * sd.omega_q + (1ull << 23)) >> 24;
+          if (W != Wn) atomicAdd(&s_cnt[C_W_ABS_PARTICLE], W - Wn);
+          W = Wn;
+          scatter = true;
+          if (Wn < PDV_ROULETTE_W) {
+            if (Wn != 0 && (r.y >> 8) < PDV_ROULETTE_Q) {
+              atomicAdd(&s_cnt[C_W_RR_GAINED], (PDV_ROULETTE_M - 1) * Wn);
+              W = Wn * PDV_ROULETTE_M;
+            } else {
+              atomicAdd(&s_cnt[C_W_RR_DROPPED], Wn);
+              fate = 5;
+              scatter = false;
+            }
+          }
+        }
+        if (scatter) {
           const unsigned m2 = r.z >> 8;
           int lo = 0, hi = sd.n_p - 2;
           while (lo < hi) {
@@ -673,9 +729,6 @@ __global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict
           vapp += 0.5 * (nz - uz) * vn;
           ux = nx; uy = ny; uz = nz;
           ++nsca; ++st_scat;
-        } else {
-          atomicAdd(&s_cnt[C_W_ABS_PARTICLE], W);
-          fate = 2;
         }
       }
       if (fate == 0 && nev >= sd.max_events) {
@@ -757,6 +810,8 @@ __global__ void k_normalise(const SetDesc* __restrict__ sets, double* const* spe
       c.w_absorbed_surface = sd.cnt[C_W_ABS_SURFACE];
       c.w_truncated = sd.cnt[C_W_TRUNCATED];
       c.truncated = sd.cnt[C_TRUNCATED];
+      c.w_roulette_dropped = sd.cnt[C_W_RR_DROPPED];
+      c.w_roulette_gained = sd.cnt[C_W_RR_GAINED];
       co[s] = c;
     }
   }

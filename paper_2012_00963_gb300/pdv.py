@@ -24,7 +24,7 @@ from . import build as _build
 
 PDV_OK, PDV_EINVAL, PDV_ENOMEM, PDV_ECUDA, PDV_EAGAIN = 0, -1, -2, -3, -4
 PDV_ENOTREADY, PDV_ETIMEOUT, PDV_ECANCELLED = -5, -6, -7
-PDV_OUT_DEVICE, PDV_PER_DV, PDV_IN_DEVICE = 0x1, 0x2, 0x4
+PDV_OUT_DEVICE, PDV_PER_DV, PDV_IN_DEVICE, PDV_IMPLICIT_CAPTURE = 0x1, 0x2, 0x4, 0x8
 PDV_PEAK_OK, PDV_PEAK_NO_PEAK, PDV_PEAK_NOT_MAX, PDV_PEAK_EDGE = 0, 1, 2, 3
 PDV_PREC_FP32, PDV_PREC_FP64 = 0, 1
 STATUS_NAMES = {0: "PDV_OK", -1: "PDV_EINVAL", -2: "PDV_ENOMEM", -3: "PDV_ECUDA",
@@ -32,7 +32,7 @@ STATUS_NAMES = {0: "PDV_OK", -1: "PDV_EINVAL", -2: "PDV_ENOMEM", -3: "PDV_ECUDA"
 COUNTER_NAMES = [
     "launched", "events", "scatters", "surface_hits", "escapes", "detected",
     "w_detected", "w_under", "w_over", "w_escaped_undetected", "w_absorbed_particle",
-    "w_absorbed_surface", "w_truncated", "truncated",
+    "w_absorbed_surface", "w_truncated", "truncated", "w_roulette_dropped", "w_roulette_gained",
 ]
 ABI_FUNCTIONS = [
     "pdv_ctx_create", "pdv_ctx_destroy", "pdv_last_error", "pdv_get_stats", "pdv_set_tuning",
@@ -489,6 +489,8 @@ class Request:
         prec = precision or wl.precision
         r.precision = PDV_PREC_FP64 if prec in ("fp64", PDV_PREC_FP64) else PDV_PREC_FP32
         r.flags = PDV_PER_DV if per_dv else 0
+        if getattr(wl, "implicit_capture", False):
+            r.flags |= PDV_IMPLICIT_CAPTURE
         ns, nb = r.n_snap, r.n_bins
         self.device_out = device_out
         if device_out is not None:

@@ -24,16 +24,31 @@ W_KEYS = ("w_detected", "w_under", "w_over", "w_escaped_undetected", "w_absorbed
 
 
 def conserved(cnt_row) -> bool:
+    """Every launched weight is accounted for; the roulette of implicit capture
+    drops weight and gives survivors more (both 0 in the analog scheme)."""
     c = pdv.counters_dict(cnt_row)
-    return sum(c[k] for k in W_KEYS) == c["launched"] << 32
+    return (sum(c[k] for k in W_KEYS) + c["w_roulette_dropped"]
+            == (c["launched"] << 32) + c["w_roulette_gained"])
 
 
-def compare(out, ref, wl, precision, min_same=0.999, rel=1e-5):
+def compare(out, ref, wl, precision, min_same=0.999, rel=1e-5, n_scat_ref=None,
+            min_frac_v=0.999, max_err=None):
+    """Packet-level parity. ``n_scat_ref``: the v_app bound grows in proportion
+    to the packet's scatterings beyond this many. A binary32 rotation leaves a
+    direction error of about 2e-7 that every later direction inherits, so the
+    error of u_z after k scatterings is a random walk of k such steps, and the
+    Doppler sum adds one of them per scattering: the v_app error grows about
+    linearly with the scattering count. 1e-5 covers the tens of scatterings of
+    an analog walk; implicit capture keeps walks alive for hundreds.
+    ``min_frac_v``: the share of detected packets within the bound (FP32).
+    ``max_err``: a bound on every matching packet's (scaled) error."""
     a, b = out["packets"], ref["packets"]
     assert len(a) == len(b)
     same = a["n_events"] == b["n_events"]
     frac_same = float(same.mean())
     scale = np.maximum(np.abs(b["v_app"]), wl.v_fs)
+    if n_scat_ref:
+        scale = scale * np.maximum(1.0, b["n_scatters"] / float(n_scat_ref))
     err = np.abs(a["v_app"] - b["v_app"]) / scale
     det = (a["detect_mask"] != 0) & (b["detect_mask"] != 0)
     ok_v = err[same & det] <= rel
@@ -53,8 +68,10 @@ def compare(out, ref, wl, precision, min_same=0.999, rel=1e-5):
         assert ok_v.all(), rep
         assert frac_v_all == 1.0, rep
     else:
-        assert frac_v >= 0.999, rep
+        assert frac_v >= min_frac_v, rep
         assert frac_v_all >= 0.998, rep
+    if max_err is not None:
+        assert rep["max_err_v"] <= max_err, rep
     assert z.max() <= 4.0, rep
     for do, dg in zip(det_o, det_g):
         assert abs(do - dg) <= max(1e-3 * do, 1.0), rep

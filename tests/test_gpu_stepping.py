@@ -144,7 +144,7 @@ def test_full_size_fig4_sampled_packets(ctx):
     try:
         dev = {"spectrum": torch.zeros(wl.n_bins, dtype=torch.float64, device="cuda"),
                "raw": torch.zeros(wl.n_bins + 2, dtype=torch.int64, device="cuda"),
-               "counters": torch.zeros(14, dtype=torch.int64, device="cuda"),
+               "counters": torch.zeros(len(pdv.COUNTER_NAMES), dtype=torch.int64, device="cuda"),
                "packets": torch.zeros(n * pdv.PACKET_DTYPE.itemsize, dtype=torch.uint8,
                                       device="cuda")}
         req = pdv.Request(cloud, wl, device_out=dev)

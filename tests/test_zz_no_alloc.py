@@ -29,7 +29,7 @@ def _device_outputs(torch, wl):
     ns, nb = len(wl.t_snap), wl.n_bins
     return {"spectrum": torch.full((ns * nb,), -1.0, dtype=torch.float64, device="cuda"),
             "raw": torch.full((ns * (nb + 2),), -1, dtype=torch.int64, device="cuda"),
-            "counters": torch.full((ns * 14,), -1, dtype=torch.int64, device="cuda")}
+            "counters": torch.full((ns * len(pdv.COUNTER_NAMES),), -1, dtype=torch.int64, device="cuda")}
 
 
 def _run(ctx, cloud, wl, torch, static):
@@ -59,7 +59,7 @@ def test_static_scratch_matches_allocating_call():
             assert np.array_equal(a["raw"], b["raw"])
             assert np.array_equal(a["counters"], b["counters"])
             assert np.array_equal(a["spectrum"], b["spectrum"])
-            assert a["counters"].reshape(-1, 14)[0, 0] == wl.n_packets
+            assert a["counters"].reshape(-1, len(pdv.COUNTER_NAMES))[0, 0] == wl.n_packets
         # a request larger than the fixed scratch is refused
         huge = big.replace(n_bins=65536, t_snap=tuple(np.linspace(1e-6, 5e-6, 64)))
         req = pdv.Request(clouds[id(big)], huge, device_out=_device_outputs(torch, huge))
