@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mode", default="default",
                     choices=["default", "serve", "batch", "precision", "model", "extract-mc",
-                             "stepping", "spectrogram", "cpu-baseline", "fig12", "fig6", "trends"])
+                             "stepping", "spectrogram", "cpu-baseline", "fig12", "fig6", "trends",
+                             "implicit"])
     ap.add_argument("--times", type=int, default=512, help="snapshot times of the spectrogram mode")
     ap.add_argument("--out", default="", help="spectrogram mode: write the v-t image (PGM) here")
     ap.add_argument("--model-sets", type=int, default=100_000,
@@ -831,6 +832,62 @@ def fig6_mode(args):
     return 0
 
 
+def implicit_mode(args):
+    """Analog absorption (Eq. 11) against implicit capture with Russian
+    roulette on the 50-snapshot log-normal Mie cloud: K independent seeds per
+    scheme give each bin's mean and variance; the figure of merit is the
+    spectrum's squared signal-to-noise per second of transport,
+    (sum_b mean_b^2 / sum_b var_b) / T. chi2_per_bin compares the two schemes'
+    means (about 1 when they estimate the same spectrum)."""
+    import numpy as np
+    import torch
+    from paper_2012_00963_gb300 import pdv
+    from paper_2012_00963_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    ctx = pdv.Context(0)
+    n = int(args.packets) if args.packets != 1e8 else 10_000_000
+    K = max(int(args.steps), 4)
+    base = W.cfg2(n_packets=n)
+    cloud = pdv.Cloud(ctx, base)
+    res = {}
+    for name, imp in (("analog", False), ("implicit", True)):
+        wl0 = base.replace(implicit_capture=imp)
+        pdv.simulate_spectrum(ctx, cloud, wl0.replace(seed=999, n_packets=min(n, 1_000_000)))
+        specs, ms, ev, det = [], [], [], []
+        for k in range(K):
+            r = pdv.simulate_spectrum(ctx, cloud, wl0.replace(seed=1000 + k))
+            st = ctx.stats()
+            specs.append(r["spectrum"])
+            ms.append(st["last_transport_ms"])
+            c = pdv.counters_dict(r["counters"][0])
+            ev.append(c["events"])
+            det.append(c["w_detected"] / 2.0**32 / n)
+        S = np.array(specs)
+        mean, var = S.mean(axis=0), S.var(axis=0, ddof=1)
+        t = float(np.median(ms))
+        snr2 = float((mean**2).sum() / var.sum())
+        res[name] = {"transport_ms": t, "events_per_packet": float(np.mean(ev)) / n,
+                     "detected_fraction_t0": float(np.mean(det)),
+                     "relative_noise": float(np.sqrt(1.0 / snr2)), "fom_per_s": snr2 / (t * 1e-3),
+                     "mean": mean, "var": var}
+    a, b = res["analog"], res["implicit"]
+    chi2 = float(((a["mean"] - b["mean"])**2 / ((a["var"] + b["var"]) / K + 1e-300))[
+        (a["var"] + b["var"]) > 0].mean())
+    cloud.close()
+    ctx.close()
+    for v in res.values():
+        del v["mean"], v["var"]
+    print(json.dumps({"mode": "implicit",
+                      "metric": "squared signal-to-noise of the spectrum per second of transport, "
+                                "analog (Eq. 11) vs implicit capture + Russian roulette",
+                      "config": {"workload": "cfg2: log-normal Mie cloud d_m=3um sigma=0.5 m=3+9i, "
+                                             "5 mg/cm^2 tin, beta=5, 50 snapshots 0.5-5us, %d packets, "
+                                             "%d seeds per scheme, 600 bins" % (n, K)},
+                      "analog": a, "implicit": b, "fom_ratio_implicit_over_analog":
+                      b["fom_per_s"] / a["fom_per_s"], "chi2_per_bin_between_means": chi2}))
+    return 0
+
+
 def fig12_mode(args):
     """The single-scattering model beside the Monte Carlo (Section III.B,
     Fig. 12): for each area mass, the Monte Carlo spectrum of the cloud and the
@@ -1095,6 +1152,8 @@ def main():
         return fig6_mode(args)
     if args.mode == "fig12":
         return fig12_mode(args)
+    if args.mode == "implicit":
+        return implicit_mode(args)
     if args.mode == "cpu-baseline":
         return cpu_baseline_mode(args)
     if args.mode == "spectrogram":
