@@ -178,6 +178,15 @@ def oracle_sample(wl, seconds, threads):
                 events_per_s=int(r["counters"][0][1]) / dt)
 
 
+def workload_config(wl, world):
+    """The benchmark workload as both arms report it."""
+    return {"workload": "cfg2: log-normal Mie cloud d_m=3um sigma=0.5 m=3+9i lambda=1550nm, "
+                        "5 mg/cm^2 tin, beta=5, %d snapshots 0.5-5us, %.0e packets per snapshot, "
+                        "%d bins 0-8000 m/s" % (len(wl.t_snap), wl.n_packets, wl.n_bins),
+            "packets_per_snapshot": wl.n_packets, "snapshots": len(wl.t_snap), "bins": wl.n_bins,
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def reference_arm(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -199,9 +208,7 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": wl.name + " (FP64 CPU oracle)",
-                                        "packets_per_snapshot": wl.n_packets,
-                                        "snapshots": len(wl.t_snap), "bins": wl.n_bins},
+        "data": "synthetic", "config": workload_config(wl, world),
         "spectra_per_s": statistics.median(sp),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "%d packets x %d snapshots per step (of %d packets)" % (
@@ -321,14 +328,7 @@ def our_arm(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded cloud of the paper's workload shape; no dataset)",
-        "config": {
-            "workload": "cfg2: log-normal Mie cloud d_m=3um sigma=0.5 m=3+9i lambda=1550nm, "
-                        "5 mg/cm^2 tin, beta=5, %d snapshots 0.5-5us, %.0e packets per snapshot, "
-                        "%d bins 0-8000 m/s, FP32 transport" % (ns, wl.n_packets, nb),
-            "packets_per_snapshot": wl.n_packets, "snapshots": ns, "bins": nb,
-            "parallelism": "replicas" if world > 1 else "single GPU",
-            "l2": "flushed between steps (256 MiB write)",
-        },
+        "config": dict(workload_config(wl, world), l2="flushed between steps (256 MiB write)"),
         "spectra_per_s": spectra,
         "events_per_s": world * (events / steps) * steps / total_s,
         "packet_histories_per_s": world * wl.n_packets * steps / total_s,
