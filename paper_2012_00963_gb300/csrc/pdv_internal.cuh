@@ -112,6 +112,25 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
+// The same block with the ten round keys of one key read from memory (one
+// shared-memory load a round in place of two additions): rk[i] is the key
+// after i Weyl increments, staged once per set by philox_round_key.
+__device__ __forceinline__ uint2 philox_round_key(uint2 k, unsigned i) {
+  return make_uint2(k.x + i * 0x9E3779B9u, k.y + i * 0xBB67AE85u);
+}
+
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint2* rk) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint2 k = rk[i];
+    const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53u;
+    const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57u;
+    c = make_uint4((unsigned)(p1 >> 32) ^ c.y ^ k.x, (unsigned)p1,
+                   (unsigned)(p0 >> 32) ^ c.w ^ k.y, (unsigned)p0);
+  }
+  return c;
+}
+
 // Uniform in (0, 1): ((r >> 9) + 1/2) 2^-23, exact in binary32 and binary64.
 __device__ __forceinline__ float u23f(unsigned r) {
   return fmaf(__uint2float_rn(r >> 9), 1.0f / 8388608.0f, 1.0f / 16777216.0f);

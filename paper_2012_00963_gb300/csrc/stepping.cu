@@ -36,7 +36,8 @@
 // Bernoulli trial, word 1 scatter/absorb (24-bit) or the surface polar angle,
 // word 2 the surface azimuth, word 3 the scattering azimuth. The
 // acceptance-rejection draws use a second key (seed ^ 0xA4093822, seed_hi ^
-// stream) and counter (p, k, attempt pair), two attempts per call.
+// stream) and counter (p, k, attempt pair), two attempts per call. Both keys'
+// ten round keys are computed once per launch and read from shared memory.
 #include <cmath>
 
 #include "stepping.cuh"
@@ -103,13 +104,13 @@ __device__ __forceinline__ float phase_ratio(float mu, const float* pn, const fl
 // warp for one lane's packet. Attempt pairs are independent Philox counters,
 // so lane i tries pair base + i; the first acceptance in counter order (lowest
 // lane, then the pair's first attempt) is the one a sequential loop would take.
-__device__ __forceinline__ float ar_cos_warp(unsigned long long pk, unsigned step, uint2 key2,
+__device__ __forceinline__ float ar_cos_warp(unsigned long long pk, unsigned step, const uint2* rk2,
                                              const float* pn, const float* thpi, int n_p,
                                              int uniform, float inv_nm1, int lane) {
   float last = 0.0f;
   for (unsigned base = 0; base < (1u << 24); base += 32) {
-    const uint4 r = philox4x32_10(
-        make_uint4((unsigned)pk, (unsigned)(pk >> 32), step, base + (unsigned)lane), key2);
+    const uint4 r = philox4x32_10_rk(
+        make_uint4((unsigned)pk, (unsigned)(pk >> 32), step, base + (unsigned)lane), rk2);
     const float mu0 = fmaf(2.0f, u23f(r.x), -1.0f);                   // exact
     const float mu1 = fmaf(2.0f, u23f(r.z), -1.0f);
     const bool acc0 = u23f(r.y) < phase_ratio(mu0, pn, thpi, n_p, uniform, inv_nm1);
@@ -231,7 +232,7 @@ __device__ __forceinline__ bool step_passes(const StepConst& sc, const unsigned 
 // its run, which the photon's own lane then takes as usual. Positions stay
 // within 33 steps of the cloud: inside the 64-bit range for steps h_P <= 2^56.
 __device__ __forceinline__ unsigned long long fast_forward(const StepConst& sc, const unsigned long long* Sq,
-                                           int n_v, float vP32, float vPd, uint2 key,
+                                           int n_v, float vP32, float vPd, const uint2* rk,
                                            unsigned sid, unsigned long long pk, unsigned k,
                                            unsigned k_lim, long long P, float uz, int lane) {
   const StepDir dir = step_dir(sc, vPd, uz);
@@ -243,8 +244,8 @@ __device__ __forceinline__ unsigned long long fast_forward(const StepConst& sc, 
     const unsigned long long kk = (unsigned long long)k + adv + (unsigned)lane;
     bool cont = false;
     if (kk < (unsigned long long)k_lim) {
-      const uint4 r = philox4x32_10(
-          make_uint4((unsigned)pk, (unsigned)(pk >> 32), (unsigned)kk, sid), key);
+      const uint4 r = philox4x32_10_rk(
+          make_uint4((unsigned)pk, (unsigned)(pk >> 32), (unsigned)kk, sid), rk);
       long long Pn, Pc;
       cont = step_passes<false>(sc, Sq, n_v, vP32, vPd, Pi, uz, dir, r.x, Pn, Pc) && Pn < top &&
              Pn > bottom;
@@ -269,6 +270,7 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
   __shared__ SetDesc sd;
   __shared__ unsigned long long s_cnt[C_NCOUNT];
   __shared__ unsigned long long s_steps;
+  __shared__ uint2 s_rk[10], s_rk2[10];          // Philox round keys: steps, angles
   {
     const int* src = reinterpret_cast<const int*>(set);
     int* dst = reinterpret_cast<int*>(&sd);
@@ -278,6 +280,11 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
     if (threadIdx.x == 0) s_steps = 0ull;
   }
   __syncthreads();
+  if (threadIdx.x < 10) {
+    s_rk[threadIdx.x] = philox_round_key(make_uint2((unsigned)sd.seed, (unsigned)(sd.seed >> 32)),
+                                         threadIdx.x);
+    s_rk2[threadIdx.x] = philox_round_key(make_uint2(sc.key2x, sc.key2y), threadIdx.x);
+  }
   const StepSmem L = step_layout(sd.n_v, sd.n_p, sd.n_snap, sd.phase_uniform);
   unsigned long long* Sq = reinterpret_cast<unsigned long long*>(smem + L.o_sq);
   float* pn = reinterpret_cast<float*>(smem + L.o_pn);
@@ -292,7 +299,6 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
   __syncthreads();
 
   const uint2 key = make_uint2((unsigned)sd.seed, (unsigned)(sd.seed >> 32));
-  const uint2 key2 = make_uint2(sc.key2x, sc.key2y);
   const unsigned sid = sd.stream_id;
   const int n_bins = sd.n_bins, row = hist_row(sd.n_bins), n_snap = sd.n_snap;
   const float vP32 = sc.v_per_P * 4294967296.0f;           // m/s per unit of P >> 32
@@ -341,7 +347,7 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
         const unsigned sk = __shfl_sync(kFullS, k, src);
         const long long sP = __shfl_sync(kFullS, P, src);
         const float suz = __shfl_sync(kFullS, uz, src);
-        const unsigned long long adv = fast_forward(sc, Sq, sd.n_v, vP32, vPd, key, sid, spk, sk,
+        const unsigned long long adv = fast_forward(sc, Sq, sd.n_v, vP32, vPd, s_rk, sid, spk, sk,
                                                     sd.max_events, sP, suz, lane);
         if (lane == src && adv) {
           k += (unsigned)adv;
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
     bool need_ar = false;
     unsigned r_phi = 0;
     if (alive) {
-      const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), k, sid), key);
+      const uint4 r = philox4x32_10_rk(make_uint4((unsigned)pk, (unsigned)(pk >> 32), k, sid), s_rk);
       // Step (3): one step along u and the Bernoulli trial of the layer crossed
       long long Pn, Pc;
       const bool pass = step_passes<true>(sc, Sq, sd.n_v, vP32, vPd, P, uz,
@@ -473,7 +479,7 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
       want &= want - 1;
       const unsigned long long spk = __shfl_sync(kFullS, pk, src);
       const unsigned sk = __shfl_sync(kFullS, k, src);
-      const float c = ar_cos_warp(spk, sk, key2, pn, thpi, sd.n_p, sd.phase_uniform, sd.inv_nm1,
+      const float c = ar_cos_warp(spk, sk, s_rk2, pn, thpi, sd.n_p, sd.phase_uniform, sd.inv_nm1,
                                   lane);
       if (lane == src) my_ct = c;
     }

@@ -11,7 +11,8 @@
 // direction and lateral displacement, 2^32 fixed-point weight. Histogram
 // tallies are 64-bit integer atomics; the per-set sums (events, escapes,
 // escaped and absorbed weight) are integers held per lane and added to the
-// set's counters once per set. Results do not depend on scheduling.
+// set's counters once per set. The set's ten Philox round keys are staged in
+// shared memory with its tables. Results do not depend on scheduling.
 //
 // k_transport_f64: the plain FP64 path, one packet per thread at a time,
 // tables read from global memory, FP64 throughout.
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
   __shared__ SetDesc sd;
   __shared__ unsigned long long s_cnt[C_NCOUNT];
   __shared__ int s_go;
+  __shared__ uint2 s_rk[10];                       // the set's Philox round keys
 
   const int lane = threadIdx.x & 31;
   const int start = (int)(((long long)blockIdx.x * n_sets) / gridDim.x);
@@ -203,6 +205,9 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
         ts[i] = (float)sd.t_snap[sd.n_snap + i];
         perm[i] = (unsigned short)sd.t_snap[2 * sd.n_snap + i];
       }
+      if (threadIdx.x < 10)
+        s_rk[threadIdx.x] = philox_round_key(
+            make_uint2((unsigned)sd.seed, (unsigned)(sd.seed >> 32)), threadIdx.x);
       if (HMODE == 2) {
         unsigned long long* h = reinterpret_cast<unsigned long long*>(smem + off[9]);
         const int nh = tally_rows(sd.n_snap, sd.ap_all) * hist_row(sd.n_bins);
@@ -274,7 +279,7 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
       if (!alive) continue;
 
       // ---- one flight and what ends it
-      const uint4 r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), kev, sid), key);
+      const uint4 r = philox4x32_10_rk(make_uint4((unsigned)pk, (unsigned)(pk >> 32), kev, sid), s_rk);
       ++kev;
       const float tau = -logf(u23f(r.x));                // Step (3): Beer–Lambert
       // 0 interaction, 1 escape through the top, 2 free surface, 3 horizontal
