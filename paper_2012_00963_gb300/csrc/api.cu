@@ -640,6 +640,15 @@ static SetDesc make_set(const pdv_request* r) {
   d.v_bot_f = (float)d.v_bot; d.dv_f = (float)d.dv; d.v_top_f = (float)d.v_top; d.v_fs_f = (float)d.v_fs;
   d.z_probe_f = (float)d.z_probe; d.r_beam_f = (float)d.r_beam; d.r_ap2_f = (float)d.r_ap2;
   d.cos_alpha_f = (float)d.cos_alpha; d.v_lo_f = (float)d.v_lo; d.inv_dbin_f = (float)d.inv_dbin;
+  d.expo = cl->desc.profile_kind == PDV_PROFILE_EXPONENTIAL ? 1 : 0;
+  if (d.expo) {
+    // Eq. 20 cut at v_top and renormalised: S(v) = (1 - exp(-beta (v/v_fs - 1))) / E, so
+    // 1 - S E = (1 - S) + S eps with eps = 1 - E, and v = v_fs (1 - ln(1 - S E) / beta)
+    const double x = cl->desc.beta * (cl->v_top / cl->desc.v_fs - 1.0);
+    d.eps_f = (float)std::exp(-x);
+    d.lg_c_f = (float)(cl->desc.v_fs * M_LN2 / cl->desc.beta);
+    d.dvds_c_f = (float)(cl->desc.v_fs * -std::expm1(-x) / cl->desc.beta);
+  }
   return d;
 }
 
@@ -693,7 +702,8 @@ static ReqBuffers plan_request(const pdv_request* r, bool device_out) {
 }
 
 static size_t set_smem(const SetDesc& d, int hm) {
-  return transport_f32_smem(d.n_v, d.n_g, d.n_p, d.n_snap, d.n_bins, hm, d.phase_uniform, d.ap_all);
+  return transport_f32_smem(d.n_v, d.n_g, d.n_p, d.n_snap, d.n_bins, hm, d.phase_uniform, d.ap_all,
+                            d.expo);
 }
 
 static int pick_hist_mode(const pdv_ctx* c, const SetDesc& d) {

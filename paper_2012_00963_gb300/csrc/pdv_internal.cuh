@@ -83,6 +83,7 @@ struct SetDesc {
   int n_v, n_g, g_shift, n_p;
   int n_snap, n_bins;
   int surface_mode, cone_all, ap_all, phase_uniform;   // theta_i = pi i / (n_p - 1)
+  int expo;                           // exponential law (Eq. 20): velocities by its closed-form inverse
   unsigned omega_q, stream_id, max_events;
   unsigned implicit;                  // PDV_IMPLICIT_CAPTURE: weight omega per interaction + roulette
   unsigned absorb_gate;               // r1 >> 8 at or above it leaves the scatter path: omega_q, or 0 (implicit)
@@ -92,6 +93,8 @@ struct SetDesc {
   double z_probe, r_beam, r_ap2, cos_alpha, v_lo, inv_dbin;
   float inv_tau_f, v_bot_f, dv_f, v_top_f, v_fs_f, z_probe_f, r_beam_f, r_ap2_f;
   float cos_alpha_f, v_lo_f, inv_dbin_f, inv_nm1;      // 1 / (n_p - 1)
+  // exponential law: v(S) = v_fs - lg_c log2((1 - S) + S eps), dv/dS = dvds_c / ((1 - S) + S eps)
+  float lg_c_f, eps_f, dvds_c_f;      // v_fs ln2 / beta, exp(-beta (v_top/v_fs - 1)), v_fs E / beta
 };
 
 // ------------------------------------------------------------- Philox4x32-10
@@ -197,7 +200,7 @@ void launch_normalise(const SetDesc* d_sets, int n_sets, double* const* d_spec,
                       pdv_counters* const* d_cnt_out, unsigned long long* const* d_raw,
                       const unsigned* flags, int max_snap, cudaStream_t st);
 size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode,
-                          int phase_uniform, int ap_all);
+                          int phase_uniform, int ap_all, int expo);
 int transport_f32_max_smem();
 cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, bool impl,
                                     int* blocks);

@@ -37,6 +37,7 @@ namespace pdv {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kChunk = 64;          // packets claimed per warp refill
+constexpr float kTwoM62f = 2.168404344971009e-19f;   // 2^-62
 
 struct SmemTables {
   const unsigned long long* Sq;
@@ -61,13 +62,15 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 __host__ __device__ inline int tally_rows(int n_snap, int ap_all) { return ap_all ? 1 : n_snap; }
 
 __host__ __device__ inline size_t smem_layout(int n_v, int n_g, int n_p, int n_snap, int n_bins,
-                                              int hist_mode, int phase_uniform, int ap_all,
+                                              int hist_mode, int phase_uniform, int ap_all, int expo,
                                               size_t* off) {
+  // the exponential law inverts in closed form: its velocity table is not staged
+  const size_t n_m = expo ? 0 : (size_t)n_v + 1, n_mg = expo ? 0 : (size_t)n_g + 1;
   const size_t n_th = phase_uniform ? 0 : (size_t)n_p;
   size_t o = 0;
-  off[0] = o; o = align16(o + sizeof(unsigned long long) * (size_t)(n_v + 1));   // Sq
-  off[1] = o; o = align16(o + sizeof(float) * (size_t)n_v);                       // w
-  off[2] = o; o = align16(o + sizeof(unsigned short) * (size_t)(n_g + 1));        // G
+  off[0] = o; o = align16(o + sizeof(unsigned long long) * n_m);                  // Sq
+  off[1] = o; o = align16(o + sizeof(float) * n_m);                               // w
+  off[2] = o; o = align16(o + sizeof(unsigned short) * n_mg);                     // G
   off[3] = o; o = align16(o + sizeof(unsigned) * (size_t)n_p);                    // Cq
   off[4] = o; o = align16(o + sizeof(float) * n_th);                              // thpi
   off[5] = o; o = align16(o + sizeof(float) * n_th);                              // dthpi
@@ -81,9 +84,9 @@ __host__ __device__ inline size_t smem_layout(int n_v, int n_g, int n_p, int n_s
 }
 
 size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode,
-                          int phase_uniform, int ap_all) {
+                          int phase_uniform, int ap_all, int expo) {
   size_t off[10];
-  return smem_layout(n_v, n_g, n_p, n_snap, n_bins, hist_mode, phase_uniform, ap_all, off);
+  return smem_layout(n_v, n_g, n_p, n_snap, n_bins, hist_mode, phase_uniform, ap_all, expo, off);
 }
 
 __device__ __forceinline__ int search_mass(const unsigned long long* Sq, const unsigned short* G,
@@ -168,7 +171,8 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
     }
     __syncthreads();
     size_t off[10];
-    smem_layout(sd.n_v, sd.n_g, sd.n_p, sd.n_snap, sd.n_bins, HMODE, sd.phase_uniform, sd.ap_all, off);
+    smem_layout(sd.n_v, sd.n_g, sd.n_p, sd.n_snap, sd.n_bins, HMODE, sd.phase_uniform, sd.ap_all,
+                sd.expo, off);
     SmemTables tb;
     tb.Sq = reinterpret_cast<const unsigned long long*>(smem + off[0]);
     tb.w = reinterpret_cast<const float*>(smem + off[1]);
@@ -181,12 +185,14 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
     tb.perm = reinterpret_cast<const unsigned short*>(smem + off[8]);
     tb.hist = HMODE == 2 ? reinterpret_cast<unsigned long long*>(smem + off[9]) : sd.hist;
     {
-      unsigned long long* Sq = reinterpret_cast<unsigned long long*>(smem + off[0]);
-      for (int i = threadIdx.x; i <= sd.n_v; i += blockDim.x) Sq[i] = sd.Sq[i];
-      float* w = reinterpret_cast<float*>(smem + off[1]);
-      for (int i = threadIdx.x; i < sd.n_v; i += blockDim.x) w[i] = sd.w[i];
-      unsigned short* G = reinterpret_cast<unsigned short*>(smem + off[2]);
-      for (int i = threadIdx.x; i <= sd.n_g; i += blockDim.x) G[i] = sd.G[i];
+      if (!sd.expo) {
+        unsigned long long* Sq = reinterpret_cast<unsigned long long*>(smem + off[0]);
+        for (int i = threadIdx.x; i <= sd.n_v; i += blockDim.x) Sq[i] = sd.Sq[i];
+        float* w = reinterpret_cast<float*>(smem + off[1]);
+        for (int i = threadIdx.x; i < sd.n_v; i += blockDim.x) w[i] = sd.w[i];
+        unsigned short* G = reinterpret_cast<unsigned short*>(smem + off[2]);
+        for (int i = threadIdx.x; i <= sd.n_g; i += blockDim.x) G[i] = sd.G[i];
+      }
       unsigned* Cq = reinterpret_cast<unsigned*>(smem + off[3]);
       float* thpi = reinterpret_cast<float*>(smem + off[4]);
       float* dthpi = reinterpret_cast<float*>(smem + off[5]);
@@ -219,7 +225,8 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
     // ---- per-set constants in registers
     const uint2 key = make_uint2((unsigned)sd.seed, (unsigned)(sd.seed >> 32));
     const unsigned sid = sd.stream_id;
-    const unsigned long long n_pk = sd.n_packets, base_pk = sd.packet_begin;
+    const unsigned long long base_pk = sd.packet_begin;
+    const unsigned n_pk = (unsigned)sd.n_packets;    // at most 4e9 packets per set
     const float inv_tau = sd.inv_tau_f;
     const int n_bins = sd.n_bins, row = hist_row(sd.n_bins), n_snap = sd.n_snap;
 
@@ -227,7 +234,8 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
     // The warp owns a chunk [pool_next, pool_end) of packet offsets and has the
     // next chunk's claim already in flight (lane 0's `pre`), so the global
     // atomic's latency is hidden behind a chunk's worth of events.
-    unsigned long long pool_next = 0, pool_end = 0, pre = 0;
+    unsigned pool_next = 0, pool_end = 0;
+    unsigned long long pre = 0;
     if (lane == 0) pre = atomicAdd(&set_ctr[si], (unsigned long long)kChunk);
     bool exhausted = false, alive = false;
     unsigned long long pk = 0, W = 0;
@@ -243,25 +251,25 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
       // refill dead lanes from the warp's chunk of packets
       unsigned need = __ballot_sync(kFull, !alive);
       while (need) {
-        const unsigned long long avail = pool_end - pool_next;
+        const unsigned avail = pool_end - pool_next;
         if (avail == 0) {
           if (exhausted) break;
           const unsigned long long b = __shfl_sync(kFull, pre, 0);
-          if (b >= n_pk) {
+          if (b >= (unsigned long long)n_pk) {
             exhausted = true;
             break;
           }
           if (lane == 0) pre = atomicAdd(&set_ctr[si], (unsigned long long)kChunk);
-          pool_next = b;
-          pool_end = b + kChunk < n_pk ? b + kChunk : n_pk;
+          pool_next = (unsigned)b;
+          pool_end = n_pk - pool_next > kChunk ? pool_next + kChunk : n_pk;
           continue;
         }
         const unsigned cnt = __popc(need);
-        const unsigned take = (unsigned)(avail < cnt ? avail : cnt);
+        const unsigned take = avail < cnt ? avail : cnt;
         const unsigned rank = __popc(need & lanemask_lt());
         if (!alive && rank < take) {
           // Step (1): a new packet at the top of the cloud moving along -z
-          pk = base_pk + pool_next + rank;
+          pk = base_pk + (pool_next + rank);
           ux = 0.f; uy = 0.f; uz = -1.f; iuz = -1.f;
           Sq = (long long)kOneQ;
           vcur = sd.v_top_f;
@@ -299,9 +307,17 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
       // velocity coordinate z/t where the flight ends
       float vn = vcur;
       if (what == 0) {
-        const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sn);
-        const float fd = u64_to_f((unsigned long long)Sn - tb.Sq[j]);
-        vn = fmaf(fd, tb.w[j], fmaf((float)j, sd.dv_f, sd.v_bot_f));
+        if (sd.expo) {
+          // Eq. 20 inverted in closed form: v = v_fs (1 - ln((1 - S) + S eps) / beta); 1 - S is
+          // exact in the fixed-point state, so the top of the cloud keeps its relative precision
+          const float q = fmaf(__ull2float_rn((unsigned long long)Sn) * kTwoM62f, sd.eps_f,
+                               __ull2float_rn(kOneQ - (unsigned long long)Sn) * kTwoM62f);
+          vn = fmaf(-sd.lg_c_f, __log2f(q), sd.v_fs_f);
+        } else {
+          const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sn);
+          const float fd = u64_to_f((unsigned long long)Sn - tb.Sq[j]);
+          vn = fmaf(fd, tb.w[j], fmaf((float)j, sd.dv_f, sd.v_bot_f));
+        }
       } else if (what == 1) {
         vn = sd.v_top_f;
       } else if (what == 2) {
@@ -314,9 +330,16 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
         Xx = fmaf(ux * iuz, d, Xx);
         Xy = fmaf(uy * iuz, d, Xy);
       } else {
-        // horizontal packet: lateral path tau / mu(z)
-        const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sq);
-        const float len = tau * inv_tau * tb.w[j] * 4.611686018427388e18f;
+        // horizontal packet: lateral path tau / mu(z), in velocity units tau / tau_tot dv/dS
+        float dvds;
+        if (sd.expo) {
+          dvds = sd.dvds_c_f / fmaf(__ull2float_rn((unsigned long long)Sq) * kTwoM62f, sd.eps_f,
+                                    __ull2float_rn(kOneQ - (unsigned long long)Sq) * kTwoM62f);
+        } else {
+          const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sq);
+          dvds = tb.w[j] * 4.611686018427388e18f;
+        }
+        const float len = tau * inv_tau * dvds;
         Xx = fmaf(ux, len, Xx);
         Xy = fmaf(uy, len, Xy);
       }
