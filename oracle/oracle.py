@@ -63,15 +63,27 @@ class _Problem(C.Structure):
         ("n_bins", C.c_int), ("v_lo", C.c_double), ("v_hi", C.c_double),
         ("packet_begin", C.c_uint64), ("n_packets", C.c_uint64), ("seed", C.c_uint64),
         ("stream_id", C.c_uint32), ("max_events", C.c_uint32), ("n_layers", C.c_uint32),
-        ("implicit_capture", C.c_uint32),
+        ("implicit_capture", C.c_uint32), ("test_horizontal_launch", C.c_uint32),
+        ("spread_runs", C.c_uint32),
+        ("spread_flight", C.c_double), ("spread_turn", C.c_double), ("spread_store", C.c_double),
     ]
 
 
 PACKET_DTYPE = np.dtype([
     ("n_events", np.uint32), ("n_scatters", np.uint32), ("n_surface", np.uint32),
     ("fate", np.uint32), ("weight", np.uint64), ("v_app", np.float64),
-    ("detect_mask", np.uint64),
+    ("detect_mask", np.uint64), ("v_app_spread", np.float64), ("n_unstable", np.uint32),
+    ("_pad", np.uint32),
 ])
+
+# Rounding sensitivity of v_app (packet records only): perturbed FP64 re-runs
+# with random errors of the size of a binary32 walk's roundings, as standard
+# deviations in units of u = 2^-24: a flight's optical length (logarithm and two
+# products, relative), each new direction component (polar angle, sin/cos,
+# rotation and renormalisation, absolute), and the storage of each component
+# (relative). Derived in DESIGN from the FP32 kernel's operations.
+SPREAD_RUNS = 8
+SPREAD_SD = (2.0, 3.0, 1.0)
 VERTEX_DTYPE = np.dtype([
     ("x", np.float64), ("y", np.float64), ("z", np.float64), ("v", np.float64),
     ("ux", np.float64), ("uy", np.float64), ("uz", np.float64), ("kind", np.int32),
@@ -272,6 +284,9 @@ class Problem:
         pb.max_events = wl.max_events
         pb.n_layers = getattr(wl, "n_layers", 0)
         pb.implicit_capture = int(bool(getattr(wl, "implicit_capture", False)))
+        pb.test_horizontal_launch = int(bool(getattr(wl, "horizontal_launch", False)))
+        pb.spread_runs = 0
+        pb.spread_flight, pb.spread_turn, pb.spread_store = SPREAD_SD
         self.pb = pb
         self.q_ext = q_ext
         self.albedo = albedo
@@ -292,13 +307,20 @@ class Problem:
 
 
 def simulate(wl, n_threads=None, n_packets=None, packet_begin=0, snapshots=None, order=False,
-             packets=False, n_trace=0, max_vertices=64, table=None):
+             packets=False, n_trace=0, max_vertices=64, table=None, spread_runs=None,
+             spread_sd=None):
     """Run the oracle. Returns a dict with ``hist`` [n_snap, n_bins] (uint64, 2^32
     weight units), ``counters`` [n_snap, NCOUNTERS], optionally ``order``
-    [n_snap, NORDER, n_bins], ``packets`` (PACKET_DTYPE) and ``trace``."""
+    [n_snap, NORDER, n_bins], ``packets`` (PACKET_DTYPE) and ``trace``. With
+    packet records, ``spread_runs`` perturbed re-runs (default SPREAD_RUNS)
+    give each packet's ``v_app_spread``; ``spread_sd`` overrides SPREAD_SD."""
     pr = Problem(wl, n_packets=n_packets, packet_begin=packet_begin, snapshots=snapshots,
                  table=table)
     pb = pr.pb
+    if packets:
+        pb.spread_runs = SPREAD_RUNS if spread_runs is None else int(spread_runs)
+        if spread_sd is not None:
+            pb.spread_flight, pb.spread_turn, pb.spread_store = spread_sd
     ns, nb = pb.n_snap, pb.n_bins
     hist = np.zeros((ns, nb), np.uint64)
     cnt = np.zeros((ns, NCOUNTERS), np.uint64)

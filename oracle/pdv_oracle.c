@@ -413,16 +413,21 @@ double orc_phase_sample(int n, const double* theta, const uint32_t* cq, uint32_t
 }
 
 /* Eq. 16 (standard form; the printed Eq. 16 has typos in its u_x and u_y
- * rows) and Eq. 17 for |u_z| close to 1 (threshold 1 - 1e-6, which the paper
- * does not give). The result is renormalised. */
+ * rows), with the horizontal norm s = sqrt(u_x^2 + u_y^2) taken from the
+ * horizontal components, and Eq. 17 for a vertical direction. The paper says
+ * only "u_z close to 1" for Eq. 17; it is read as vertical to within
+ * s < 1e-15: a wider threshold makes the new direction jump (by up to
+ * sqrt(2 (1 - |u_z|)) at the switch), and walks whose u_z is rounded to one
+ * side of it or the other would part there. The result is renormalised. */
 void orc_rotate(double u[3], double ct, double st, double cp, double sp) {
   double ux = u[0], uy = u[1], uz = u[2], nx, ny, nz;
-  if (fabs(uz) > 1.0 - 1e-6) {
+  double h2 = ux * ux + uy * uy;
+  if (h2 < 1e-30) {
     nx = st * cp;
     ny = st * sp;
     nz = uz >= 0.0 ? ct : -ct;
   } else {
-    double s = sqrt(1.0 - uz * uz);
+    double s = sqrt(h2);
     nx = st * (ux * uz * cp - uy * sp) / s + ux * ct;
     ny = st * (uy * uz * cp + ux * sp) / s + uy * ct;
     nz = -st * cp * s + uz * ct;
@@ -455,6 +460,71 @@ static void orc_trace_put(orc_vertex* tr, int max_v, int* nv, double x, double y
   e->ux = u[0]; e->uy = u[1]; e->uz = u[2];
   e->kind = kind;
   ++*nv;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rounding sensitivity of a packet's apparent velocity (test support).       */
+/* A binary32 walk rounds every flight's optical length and every new         */
+/* direction, and stores each direction component to 24 bits. Re-running the  */
+/* packet in FP64 with random errors of those sizes injected at those points  */
+/* (stochastic arithmetic in the manner of Vignes' CESTAC method) shows how    */
+/* far such roundings move v_app, whatever amplifies them: a steep dv/dS in    */
+/* the thin top of the cloud, or a near-vertical direction whose azimuth      */
+/* frame (Eq. 16) or Eq. 17 switch turns a 1e-7 error into a large one. The    */
+/* errors are drawn from Philox under a key of their own, so the walk's own    */
+/* random numbers (and with them its decisions) are unchanged.                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  uint32_t run;          /* 1, 2, ...: which perturbed re-run               */
+  double sd_flight, sd_turn, sd_store;   /* already scaled by 2^-24          */
+} orc_pert;
+
+/* standard normal from two 24-bit uniforms (Box–Muller) */
+static double orc_gauss(uint32_t a, uint32_t b) {
+  double u1 = ((double)(a >> 8) + 0.5) / 16777216.0;
+  double u2 = ((double)(b >> 8) + 0.5) / 16777216.0;
+  return sqrt(-2.0 * log(u1)) * cos(2.0 * ORC_PI * u2);
+}
+
+/* two standard normals for (packet, event, slot) of re-run pe->run */
+static void orc_pert_normals(const orc_problem* pb, const orc_pert* pe, uint64_t pk, uint32_t k,
+                             uint32_t slot, double g[2]) {
+  uint32_t key[2] = {(uint32_t)pb->seed ^ 0x3C6EF372u,
+                     (uint32_t)(pb->seed >> 32) ^ (0x85EBCA6Bu * pe->run)};
+  uint32_t ctr[4] = {(uint32_t)pk, (uint32_t)(pk >> 32), k, slot};
+  uint32_t r[4];
+  orc_philox4x32_10(ctr, key, r);
+  g[0] = orc_gauss(r[0], r[1]);
+  g[1] = orc_gauss(r[2], r[3]);
+}
+
+/* relative error factor of flight k's optical length */
+static double orc_pert_flight(const orc_problem* pb, const orc_pert* pe, uint64_t pk, uint32_t k) {
+  double g[2];
+  orc_pert_normals(pb, pe, pk, k, 0u, g);
+  return 1.0 + pe->sd_flight * g[0];
+}
+
+/* the new direction of event k as a binary32 walk would hold it: a fresh
+ * error on each component, renormalised, then each component stored */
+static void orc_pert_turn(const orc_problem* pb, const orc_pert* pe, uint64_t pk, uint32_t k,
+                          double u[3]) {
+  double a[2], b[2], c[2];
+  orc_pert_normals(pb, pe, pk, k, 1u, a);
+  orc_pert_normals(pb, pe, pk, k, 2u, b);
+  orc_pert_normals(pb, pe, pk, k, 3u, c);
+  if (pe->sd_turn != 0.0) {
+    u[0] += pe->sd_turn * a[0];
+    u[1] += pe->sd_turn * a[1];
+    u[2] += pe->sd_turn * b[0];
+    double n = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    u[0] /= n;
+    u[1] /= n;
+    u[2] /= n;
+  }
+  u[0] *= 1.0 + pe->sd_store * b[1];
+  u[1] *= 1.0 + pe->sd_store * c[0];
+  u[2] *= 1.0 + pe->sd_store * c[1];
 }
 
 /* Step (6) at the top of the cloud: vacuum flight from (x, y, z_top) to the
@@ -495,7 +565,7 @@ static int orc_escape(const orc_setup* st, orc_tally* ta, double x, double y, do
  * paper has none), the new direction by the surface law from r[1], r[2], and
  * the Doppler shift of the moving wall. Returns 1 when no weight is left. */
 static int orc_surface(const orc_setup* st, orc_tally* ta, const uint32_t r[4], double u[3],
-                       uint64_t* Wp, double* vapp) {
+                       uint64_t* Wp, double* vapp, const orc_pert* pe, uint64_t pk, uint32_t k) {
   const orc_problem* pb = st->pb;
   uint64_t W = *Wp;
   ta->cnt[ORC_EVENTS] += 1;
@@ -524,13 +594,14 @@ static int orc_surface(const orc_setup* st, orc_tally* ta, const uint32_t r[4], 
     u[1] = stt * sin(ph);
     u[2] = ct;
   }
+  if (pe) orc_pert_turn(pb, pe, pk, k, u);
   /* the moving wall shifts the frequency like a particle at v_fs */
   *vapp += 0.5 * (u[2] - uz_old) * pb->v_fs;
   return Wn == 0;
 }
 
 static void orc_transport(const orc_setup* st, uint64_t pk, double t, orc_tally* ta,
-                          orc_result* res, orc_vertex* trace, int max_v) {
+                          orc_result* res, orc_vertex* trace, int max_v, const orc_pert* pe) {
   const orc_problem* pb = st->pb;
   uint32_t key[2] = {(uint32_t)pb->seed, (uint32_t)(pb->seed >> 32)};
   uint32_t ctr[4] = {(uint32_t)pk, (uint32_t)(pk >> 32), 0u, pb->stream_id};
@@ -545,6 +616,10 @@ static void orc_transport(const orc_setup* st, uint64_t pk, double t, orc_tally*
   double psi = 2.0 * ORC_PI * orc_u01(r[1]);
   double x = rad * cos(psi), y = rad * sin(psi);
   double u[3] = {0.0, 0.0, -1.0};
+  if (pb->test_horizontal_launch) {  /* test of the horizontal-flight rule */
+    u[0] = 1.0;
+    u[2] = 0.0;
+  }
   orc_trace_put(trace, max_v, &nv, x, y, pb->z_probe, 0.0, u, 0);
   double z = st->v_top * t;          /* particles at z = v t (vacuum flight) */
   double vcur = st->v_top;
@@ -572,7 +647,9 @@ static void orc_transport(const orc_setup* st, uint64_t pk, double t, orc_tally*
       vn = vcur;
       interact = 1;
     } else {
-      Tn = T + tau * u[2];
+      double dT = tau * u[2];
+      if (pe) dT *= orc_pert_flight(pb, pe, pk, k);
+      Tn = T + dT;
       if (Tn >= st->tau_tot) {
         /* Step (6): leaves through the top */
         double z_top = st->v_top * t;
@@ -590,7 +667,7 @@ static void orc_transport(const orc_setup* st, uint64_t pk, double t, orc_tally*
         vcur = pb->v_fs;
         ++nev;
         ++nsurf;
-        if (orc_surface(st, ta, r, u, &W, &vapp)) {
+        if (orc_surface(st, ta, r, u, &W, &vapp, pe, pk, k)) {
           orc_trace_put(trace, max_v, &nv, x, y, z, pb->v_fs, u, 2);
           fate = ORC_FATE_ABS_SURFACE;
           break;
@@ -638,6 +715,7 @@ static void orc_transport(const orc_setup* st, uint64_t pk, double t, orc_tally*
         double ph = 2.0 * ORC_PI * orc_u01(r[3]);              /* Eq. 15 */
         double uz_old = u[2];
         orc_rotate(u, cos(th), sin(th), cos(ph), sin(ph));    /* Eq. 16-17 */
+        if (pe) orc_pert_turn(pb, pe, pk, k, u);
         vapp += 0.5 * (u[2] - uz_old) * vn;                    /* Eq. 4, 18 */
         ++nsca;
         ta->cnt[ORC_SCATTERS] += 1;
@@ -719,7 +797,8 @@ double orc_phase_ar_cos(const orc_problem* pb, uint64_t pk, uint32_t step) {
 }
 
 static void orc_transport_stepped(const orc_setup* st, uint64_t pk, double t, orc_tally* ta,
-                                  orc_result* res, orc_vertex* trace, int max_v) {
+                                  orc_result* res, orc_vertex* trace, int max_v,
+                                  const orc_pert* pe) {
   const orc_problem* pb = st->pb;
   uint32_t key[2] = {(uint32_t)pb->seed, (uint32_t)(pb->seed >> 32)};
   uint32_t ctr[4] = {(uint32_t)pk, (uint32_t)(pk >> 32), 0u, pb->stream_id};
@@ -772,7 +851,7 @@ static void orc_transport_stepped(const orc_setup* st, uint64_t pk, double t, or
         z = z_fs;
         ++nev;
         ++nsurf;
-        int dead = orc_surface(st, ta, r, u, &W, &vapp);
+        int dead = orc_surface(st, ta, r, u, &W, &vapp, pe, pk, k);
         orc_trace_put(trace, max_v, &nv, x, y, z, pb->v_fs, u, 2);
         if (dead) {
           fate = ORC_FATE_ABS_SURFACE;
@@ -798,6 +877,7 @@ static void orc_transport_stepped(const orc_setup* st, uint64_t pk, double t, or
         double ph = 2.0 * ORC_PI * orc_u01(r[3]);              /* Eq. 15 */
         double uz_old = u[2];
         orc_rotate(u, ct, sqrt(1.0 - ct * ct), cos(ph), sin(ph));   /* Eq. 16-17 */
+        if (pe) orc_pert_turn(pb, pe, pk, k, u);
         vapp += 0.5 * (u[2] - uz_old) * vn;                    /* Eq. 4, 18 */
         ++nsca;
         ta->cnt[ORC_SCATTERS] += 1;
@@ -839,6 +919,8 @@ typedef struct {
   orc_packet* packets;
   int n_trace, max_v;
   orc_vertex* trace;
+  uint64_t* scratch_hist;  /* [n_bins], tallies of the perturbed re-runs */
+  uint64_t* scratch_cnt;   /* [ORC_NCOUNTERS] */
 } orc_job;
 
 static void* orc_worker(void* arg) {
@@ -860,9 +942,9 @@ static void* orc_worker(void* arg) {
       if (s == 0 && jb->trace && i < (uint64_t)jb->n_trace)
         tr = jb->trace + (size_t)i * (size_t)jb->max_v;
       if (pb->n_layers)
-        orc_transport_stepped(st, pk, pb->t_snap[s], &ta, &res, tr, jb->max_v);
+        orc_transport_stepped(st, pk, pb->t_snap[s], &ta, &res, tr, jb->max_v, NULL);
       else
-        orc_transport(st, pk, pb->t_snap[s], &ta, &res, tr, jb->max_v);
+        orc_transport(st, pk, pb->t_snap[s], &ta, &res, tr, jb->max_v, NULL);
       if (res.detected && s < 64) mask |= (uint64_t)1 << s;
       if (s == 0 && jb->packets) {
         orc_packet* o = &jb->packets[i];
@@ -872,6 +954,31 @@ static void* orc_worker(void* arg) {
         o->fate = res.fate;
         o->weight = res.weight;
         o->v_app = res.v_app;
+        o->v_app_spread = 0.0;
+        o->n_unstable = 0;
+        o->pad_ = 0;
+        /* rounding sensitivity: perturbed re-runs into a scratch tally */
+        for (uint32_t q = 1; q <= pb->spread_runs; ++q) {
+          const double unit = 1.0 / 16777216.0;
+          orc_pert pe = {q, pb->spread_flight * unit, pb->spread_turn * unit,
+                         pb->spread_store * unit};
+          orc_tally sc;
+          memset(jb->scratch_cnt, 0, sizeof(uint64_t) * ORC_NCOUNTERS);
+          sc.hist = jb->scratch_hist;
+          sc.cnt = jb->scratch_cnt;
+          sc.order = NULL;
+          orc_result rq;
+          if (pb->n_layers)
+            orc_transport_stepped(st, pk, pb->t_snap[0], &sc, &rq, NULL, 0, &pe);
+          else
+            orc_transport(st, pk, pb->t_snap[0], &sc, &rq, NULL, 0, &pe);
+          if (rq.n_events != res.n_events) {
+            o->n_unstable += 1;
+          } else {
+            double d = fabs(rq.v_app - res.v_app);
+            if (d > o->v_app_spread) o->v_app_spread = d;
+          }
+        }
       }
     }
     if (jb->packets) jb->packets[i].detect_mask = mask;
@@ -888,6 +995,7 @@ int orc_simulate(const orc_problem* pb, int n_threads, uint64_t* hist, uint64_t*
   if (orc_setup_profile(&st, pb) != 0) { free(st.M); return -1; }
   if (!(pb->reflectivity >= 0.0 && pb->reflectivity <= 1.0) ||
       (pb->implicit_capture && pb->n_layers > 0) ||
+      (pb->test_horizontal_launch && pb->n_layers > 0) ||
       !(pb->albedo >= 0.0 && pb->albedo <= 1.0) || pb->n_bins < 1 || !(pb->v_hi > pb->v_lo) ||
       pb->n_snap < 1 || !(pb->r_beam >= 0.0) || pb->surface_mode < 0 || pb->surface_mode > 2) {
     free(st.M);
@@ -928,6 +1036,8 @@ int orc_simulate(const orc_problem* pb, int n_threads, uint64_t* hist, uint64_t*
     jb->n_trace = trace ? n_trace : 0;
     jb->max_v = max_vertices;
     jb->trace = trace;
+    jb->scratch_hist = (uint64_t*)calloc(nb, sizeof(uint64_t));
+    jb->scratch_cnt = (uint64_t*)calloc(ORC_NCOUNTERS, sizeof(uint64_t));
   }
   if (trace)
     for (size_t i = 0; i < (size_t)n_trace * (size_t)max_vertices; ++i) trace[i].kind = -1;
@@ -944,6 +1054,7 @@ int orc_simulate(const orc_problem* pb, int n_threads, uint64_t* hist, uint64_t*
     if (order_hist)
       for (size_t i = 0; i < ns * ORC_NORDER * nb; ++i) order_hist[i] += jobs[j].order[i];
     free(jobs[j].hist); free(jobs[j].cnt); free(jobs[j].order);
+    free(jobs[j].scratch_hist); free(jobs[j].scratch_cnt);
   }
   free(jobs); free(th); free(st.M); free(st.cq);
   return 0;

@@ -34,6 +34,9 @@
  *                          omega = 0 (the analog absorbed weight), the weight
  *                          law W = 2^32 omega^k 16^j of the k-scatter escapes,
  *                          its conservation identity and the analog means.
+ *   v_app_spread           pinned (zero at zero perturbation, linear in the
+ *                          perturbation size, zero for the exact specular
+ *                          echo, thread-count invariant)
  */
 #ifndef PDV_ORACLE_H
 #define PDV_ORACLE_H
@@ -120,6 +123,17 @@ typedef struct {
                             stepping, H / n_layers per step (Section II.B)     */
   uint32_t implicit_capture; /* 1: implicit capture + roulette (exact free
                             paths only); 0: the analog choice of Eq. 11        */
+  /* Rounding sensitivity of each packet's v_app (test support, only with a
+   * packets array): spread_runs perturbed FP64 re-runs of snapshot 0 in which
+   * every flight's optical length, every new direction and every stored
+   * direction component carry a random error the size of a binary32 rounding
+   * (standard deviations in units of u = 2^-24). 0 runs: none. */
+  uint32_t test_horizontal_launch; /* 1: packets enter moving along +x (a test
+                            of the horizontal-flight rule; exact paths only)   */
+  uint32_t spread_runs;
+  double spread_flight;  /* relative, per flight                             */
+  double spread_turn;    /* absolute, per direction component at each turn   */
+  double spread_store;   /* relative, per stored direction component         */
 } orc_problem;
 
 typedef struct {
@@ -127,6 +141,10 @@ typedef struct {
   uint64_t weight;       /* final weight (2^32 fixed point)                  */
   double v_app;          /* apparent velocity accumulated (snapshot 0)       */
   uint64_t detect_mask;  /* bit s: detected at snapshot s (s < 64)           */
+  double v_app_spread;   /* largest |v_app' - v_app| over the perturbed re-runs
+                            that kept the event count (0 without re-runs)      */
+  uint32_t n_unstable;   /* perturbed re-runs whose event count changed      */
+  uint32_t pad_;
 } orc_packet;
 
 typedef struct {

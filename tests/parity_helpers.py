@@ -2,14 +2,20 @@
 
 Criteria (the reading of the parity bar; tolerances fixed here):
   * identical per-packet event counts for >= 99.9% of packets;
-  * on detected packets (detected at some snapshot by both paths) with
-    identical event counts, |v_app,gpu - v_app,oracle| <= 1e-5
-    max(|v_app,oracle|, v_fs): relative 1e-5, with the free-surface velocity
-    as the scale where multiple scattering cancels v_app towards 0; every such
-    packet for the FP64 path, >= 99.9% of them for the FP32 path (binary32
-    direction rounding is amplified where the profile is steepest);
+  * on every packet with identical event counts (detected or not),
+    |v_app,gpu - v_app,oracle| <= 1e-5 max(|v_app,oracle|, v_fs) + K s, where
+    the free-surface velocity is the scale where multiple scattering cancels
+    v_app towards 0, and s is the packet's rounding sensitivity: the largest
+    deviation of v_app over the oracle's FP64 re-runs of the packet with
+    random errors the size of a binary32 walk's roundings (oracle.SPREAD_SD).
+    K = 4 for the FP32 path; the FP64 path must meet 1e-5 alone (K = 0).
+    Packets whose event count changed in every perturbed re-run are decided by
+    rounding; they are counted against the same 0.1% budget as the event
+    counts and held to no v_app bound;
   * every histogram bin within 4 sigma of the combined Monte Carlo error
-    (weights <= 1 packet, so sigma^2 <= tallied weight on each side);
+    (weights <= 1 packet, so sigma^2 <= tallied weight on each side), both as
+    integer tallies and as the normalised FP64 spectrum S_b = W_b / (2^32 N)
+    (Eq. 19), which must also equal the GPU's own tallies so normalised;
   * total detected weight (in range and out of range) within 1e-3 relative;
   * exact integer weight conservation on the GPU side.
 """
@@ -31,51 +37,59 @@ def conserved(cnt_row) -> bool:
             == (c["launched"] << 32) + c["w_roulette_gained"])
 
 
-def compare(out, ref, wl, precision, min_same=0.999, rel=1e-5, n_scat_ref=None,
-            min_frac_v=0.999, max_err=None):
-    """Packet-level parity. ``n_scat_ref``: the v_app bound grows in proportion
-    to the packet's scatterings beyond this many. A binary32 rotation leaves a
-    direction error of about 2e-7 that every later direction inherits, so the
-    error of u_z after k scatterings is a random walk of k such steps, and the
-    Doppler sum adds one of them per scattering: the v_app error grows about
-    linearly with the scattering count. 1e-5 covers the tens of scatterings of
-    an analog walk; implicit capture keeps walks alive for hundreds.
-    ``min_frac_v``: the share of detected packets within the bound (FP32).
-    ``max_err``: a bound on every matching packet's (scaled) error."""
+SPREAD_K = 4.0
+
+
+def v_app_check(a, b, v_fs, precision, rel=1e-5):
+    """Per-packet v_app bar on packets with identical event counts. Returns
+    (ok mask over the compared packets, compared mask, report)."""
+    same = a["n_events"] == b["n_events"]
+    scale = np.maximum(np.abs(b["v_app"]), v_fs)
+    err = np.abs(a["v_app"] - b["v_app"])
+    k = SPREAD_K if precision == "fp32" else 0.0
+    bound = rel * scale + k * b["v_app_spread"]
+    undecided = same & (b["n_unstable"] >= O.SPREAD_RUNS) & (precision == "fp32")
+    checked = same & ~undecided
+    ok = err <= bound
+    det = (a["detect_mask"] != 0) & (b["detect_mask"] != 0)
+    rep = dict(n_same=int(same.sum()), n_checked=int(checked.sum()), n_undecided=int(undecided.sum()),
+               n_det=int((checked & det).sum()), n_fail=int((checked & ~ok).sum()),
+               frac_within_1e5=float((err[checked] <= rel * scale[checked]).mean()) if checked.any() else 1.0,
+               n_widened=int((checked & (err > rel * scale) & ok).sum()),
+               max_err_rel=float((err / scale)[checked].max()) if checked.any() else 0.0,
+               max_err_over_bound=float((err / bound)[checked].max()) if checked.any() else 0.0)
+    return ok, checked, rep
+
+
+def compare(out, ref, wl, precision, min_same=0.999, rel=1e-5):
+    """Packet-level parity (criteria in the module docstring)."""
     a, b = out["packets"], ref["packets"]
     assert len(a) == len(b)
     same = a["n_events"] == b["n_events"]
     frac_same = float(same.mean())
-    scale = np.maximum(np.abs(b["v_app"]), wl.v_fs)
-    if n_scat_ref:
-        scale = scale * np.maximum(1.0, b["n_scatters"] / float(n_scat_ref))
-    err = np.abs(a["v_app"] - b["v_app"]) / scale
-    det = (a["detect_mask"] != 0) & (b["detect_mask"] != 0)
-    ok_v = err[same & det] <= rel
-    frac_v = float(ok_v.mean()) if ok_v.size else 1.0
-    frac_v_all = float((err[same] <= rel).mean())
+    ok, checked, vrep = v_app_check(a, b, wl.v_fs, precision, rel)
     hist_o = ref["hist"].astype(np.float64) / TWO32
     hist_g = out["hist"].astype(np.float64) / TWO32
     z = np.abs(hist_g - hist_o) / np.sqrt(hist_g + hist_o + 1.0)
     det_o = (ref["hist"].astype(np.float64).sum(axis=1) + ref["counters"][:, 7] + ref["counters"][:, 8]) / TWO32
     det_g = out["raw"].astype(np.float64).sum(axis=1) / TWO32
-    rep = dict(frac_same=frac_same, frac_v=frac_v, frac_v_all=frac_v_all, n_det=int(det.sum()),
-               max_err_v_det=float(err[same & det].max()) if (same & det).any() else 0.0,
-               max_err_v=float(err[same].max()) if same.any() else 0.0,
-               max_z=float(z.max()), det_o=det_o.tolist(), det_g=det_g.tolist())
+    # Eq. 19 normalisation (a14): every bin of the FP64 spectrum is the integer
+    # tally over 2^32 N, and lies within 4 sigma of the oracle's W_b / (2^32 N)
+    n = float(len(a))
+    spec = out["spectrum"]
+    exact = np.array_equal(spec, out["hist"].astype(np.float64) * (1.0 / (TWO32 * n)))
+    z_spec = np.abs(spec * n - hist_o) / np.sqrt(spec * n + hist_o + 1.0)
+    rep = dict(frac_same=frac_same, max_z=float(z.max()), max_z_spec=float(z_spec.max()),
+               spec_exact=bool(exact), det_o=det_o.tolist(), det_g=det_g.tolist(), **vrep)
     assert frac_same >= min_same, rep
-    if precision == "fp64":
-        assert ok_v.all(), rep
-        assert frac_v_all == 1.0, rep
-    else:
-        assert frac_v >= min_frac_v, rep
-        assert frac_v_all >= 0.998, rep
-    if max_err is not None:
-        assert rep["max_err_v"] <= max_err, rep
+    assert (len(a) - vrep["n_checked"]) <= (1.0 - min_same) * len(a), rep
+    assert ok[checked].all(), rep
     assert z.max() <= 4.0, rep
+    assert exact and z_spec.max() <= 4.0, rep
     for do, dg in zip(det_o, det_g):
         assert abs(do - dg) <= max(1e-3 * do, 1.0), rep
     for row in out["counters"]:
         assert conserved(row), rep
-    print("parity", precision, rep["frac_same"], rep["frac_v"], rep["frac_v_all"], rep["n_det"], rep["max_err_v_det"], rep["max_z"])
+    print("parity", precision, rep["frac_same"], rep["n_checked"], rep["frac_within_1e5"],
+          rep["n_widened"], rep["max_err_rel"], rep["max_err_over_bound"], rep["max_z"])
     return rep

@@ -18,13 +18,10 @@ WIDE = dict(r_ap=3e-3, cone_alpha=0.5)
 
 
 def compare(out, ref, wl, precision):
-    """The packet-level bar for long walks: the v_app bound grows in proportion
-    to the scatterings beyond 50 (see parity_helpers.compare). A scattering in
-    the thin top of the cloud, where dv/dS is steepest, amplifies the FP32
-    error of the flight's mass step; walks that scatter more often meet the
-    top more often, so FP32 keeps 99.8 % of detected packets (not 99.9 %)
-    within the bound, and every matching packet within 1e-3."""
-    return _compare(out, ref, wl, precision, n_scat_ref=50, min_frac_v=0.998, max_err=1e-3)
+    """The packet-level bar of parity_helpers.compare. Long walks need no bar of
+    their own: the oracle's perturbed re-runs follow every scattering of the
+    walk, so each packet's rounding sensitivity grows with its walk."""
+    return _compare(out, ref, wl, precision)
 
 
 @pytest.fixture(scope="module")

@@ -243,3 +243,20 @@ def test_rotation_geometry():
     # Eq. 17 branch for a vertical packet keeps the sign of u_z
     v = O.rotate([0, 0, -1.0], np.cos(0.3), np.sin(0.3), 1.0, 0.0)
     assert v[2] == pytest.approx(-np.cos(0.3)) and v[0] == pytest.approx(np.sin(0.3))
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1.4e-3, 1e-6, 1e-9, 1e-13])
+def test_rotation_is_continuous_at_the_pole(eps):
+    """Near the pole the rotation keeps the exact scattering angle, and the
+    new direction tends to the vertical packet's as the tilt goes to zero, with
+    the azimuth measured from the tilt's own direction alpha (the limit of the
+    Eq. 16 frame): no jump at any tilt (the tilt eps = 1.4e-3 is the old
+    switch to Eq. 17 at 1 - |u_z| = 1e-6)."""
+    alpha, th, ph = 0.7, 0.9, 2.1
+    u = np.array([eps * np.cos(alpha), eps * np.sin(alpha), -np.sqrt(1.0 - eps * eps)])
+    v = O.rotate(u, np.cos(th), np.sin(th), np.cos(ph), np.sin(ph))
+    assert np.dot(u, v) == pytest.approx(np.cos(th), abs=1e-12)
+    e1 = np.array([-np.cos(alpha), -np.sin(alpha), 0.0])   # limit of (u_x u_z, u_y u_z, -s^2) / s
+    e2 = np.array([-np.sin(alpha), np.cos(alpha), 0.0])
+    lim = np.sin(th) * (np.cos(ph) * e1 + np.sin(ph) * e2) + np.cos(th) * np.array([0, 0, -1.0])
+    assert np.allclose(v, lim, atol=3.0 * eps + 1e-12)

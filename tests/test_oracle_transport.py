@@ -288,3 +288,49 @@ def test_spectrum_error_falls_as_inverse_square_root_of_packets():
     assert -0.6 < slope < -0.4, (slope, err)
     for a, b in zip(err, err[1:]):
         assert 0.5 / 1.2 < b / a < 0.5 * 1.2, err
+
+
+def _first_tau(wl, pk):
+    """tau* of a packet's first flight from its Philox block (event 1):
+    -ln u with u = ((r0 >> 9) + 1/2) 2^-23."""
+    ctr = np.array([pk & 0xFFFFFFFF, pk >> 32, 1, wl.stream_id], np.uint32)
+    key = np.array([wl.seed & 0xFFFFFFFF, wl.seed >> 32], np.uint32)
+    r0 = int(O.philox4x32_10(ctr, key)[0])
+    return -math.log(((r0 >> 9) + 0.5) * 2.0**-23)
+
+
+@pytest.mark.parametrize("profile", ["flat", "exponential"])
+def test_horizontal_flight_rule(profile):
+    """Packets launched along +x (the test hook of the |u_z| < 1e-9 rule) keep
+    their height at the top of the cloud, z = v_top t, and interact after a
+    lateral path tau* / mu with mu = tau_tot (ds/dv) / t the extinction per
+    unit length there. Flat profile: ds/dv = 1 / (v_top - v_bot) exactly;
+    exponential law: ds/dv from a central difference of the pinned cumulative
+    mass fraction."""
+    t = 1e-6
+    if profile == "flat":
+        wl = W.cfg1(n_packets=300, profile_kind="tabulated", prof_v=[2500.0, 4500.0],
+                    prof_f=[1.0, 1.0], v_max=0.0, m0=2 * W.MG_CM2, horizontal_launch=True,
+                    r_ap=0.0, cone_alpha=2.0)
+        dsdv = 1.0 / 2000.0
+    else:
+        wl = W.cfg1(n_packets=300, m0=2 * W.MG_CM2, horizontal_launch=True, r_ap=0.0,
+                    cone_alpha=2.0)
+        pr = O.Problem(wl)
+        h = 1e-3   # the difference is centred 2h below the top: relative offset 2 h beta / v_fs
+        dsdv = (pr.cdf(wl.v_max - h) - pr.cdf(wl.v_max - 3 * h)) / (2 * h)
+    r = O.simulate(wl, packets=True, n_trace=300, max_vertices=4)
+    tau = r["tau_tot"]
+    v_top = r["v_top"]
+    n = 0
+    for pk in range(300):
+        v0, v1 = r["trace"][pk][0], r["trace"][pk][1]
+        assert v0["kind"] == 0 and v1["kind"] in (1, 4)
+        assert v1["z"] == pytest.approx(v_top * t, rel=1e-15)
+        assert v1["v"] == pytest.approx(v_top, rel=1e-15)
+        assert v1["y"] == v0["y"]
+        expect = _first_tau(wl, pk) * t / (tau * dsdv)
+        assert v1["x"] - v0["x"] == pytest.approx(expect, rel=1e-12 if profile == "flat" else 2e-5)
+        n += 1
+    assert n == 300
+    assert r["packets"]["n_events"].min() >= 1
