@@ -69,6 +69,14 @@ enum { PDV_PREC_FP32 = 0, PDV_PREC_FP64 = 1 };
 #define PDV_ROULETTE_Q (1u << 20)    /* survival bound on r1 >> 8 (1/16)   */
 #define PDV_ROULETTE_M 16u           /* survivor's weight factor           */
 
+/* Test hook for the horizontal-flight rule: every packet enters at the top of
+ * the cloud moving along +x, u = (1, 0, 0), instead of along -z. A flight with
+ * |u_z| < 1e-9 keeps its height and runs tau* / mu(z) sideways, where mu is the
+ * extinction per unit length at that height; the paper is silent on this case,
+ * and random directions reach it with a probability of about 1e-9, so this flag
+ * is how tests exercise it. Exact free paths only (n_layers == 0). */
+#define PDV_TEST_HORIZONTAL_LAUNCH 0x10u
+
 /* Optional device allocator (NULL: cudaMallocAsync/cudaFreeAsync on the
  * context stream). Both callbacks are called from library threads. */
 typedef struct {
@@ -152,7 +160,8 @@ typedef struct {
   int n_bins;                      /* 1..65536                           */
   double v_lo, v_hi;               /* m/s, v_hi > v_lo                   */
   int precision;                   /* PDV_PREC_FP32 | PDV_PREC_FP64      */
-  uint32_t flags;                  /* PDV_OUT_DEVICE | PDV_PER_DV | PDV_IMPLICIT_CAPTURE */
+  uint32_t flags;                  /* PDV_OUT_DEVICE | PDV_PER_DV | PDV_IMPLICIT_CAPTURE
+                                      | PDV_TEST_HORIZONTAL_LAUNCH */
   double* out_spectrum;            /* [n_snap * n_bins], required        */
   uint64_t* out_raw;               /* optional [n_snap * (n_bins + 2)]: under, bins, over */
   pdv_counters* out_counters;      /* optional [n_snap]                  */
@@ -173,7 +182,8 @@ typedef struct {
 typedef struct {
   int block_threads;               /* 128, 256, 512 (0 = 256)            */
   int blocks_per_sm;               /* 0 = occupancy maximum              */
-  int tile_packets;                /* packets per work tile (0 = auto)   */
+  int tile_packets;                /* packets a warp claims at a time from its
+                                      request's counter: 0 (64) or 16..65536 */
   int hist_mode;                   /* 0 auto, 1 global atomics, 2 shared-memory privatised */
 } pdv_tuning;
 
@@ -257,9 +267,20 @@ pdv_status pdv_simulate_spectrum(pdv_ctx* ctx, const pdv_request* req);
  * batch shape. Outputs as for pdv_simulate_spectrum. */
 pdv_status pdv_simulate_batch(pdv_ctx* ctx, const pdv_request* reqs, int n);
 
-/* Time candidate launch parameters on a short version of the batch and keep
- * the fastest in the context (and in *out if not NULL). */
+/* Time candidate launch parameters on a short version of the batch (1/16 of
+ * each request's packets, at least 65536) and keep the fastest in the context
+ * (and in *out if not NULL). The search covers block_threads {128, 256},
+ * hist_mode {1, 2} (global or block-private histograms), blocks_per_sm
+ * {0 (as many as fit), 2} and tile_packets {32, 64, 256}. With a cache file set
+ * (pdv_set_autotune_cache), a choice already recorded there for this device
+ * and batch shape is taken without timing, and a new choice is added to the
+ * file. A deployment tool with no counterpart in the paper. */
 pdv_status pdv_autotune(pdv_ctx* ctx, const pdv_request* reqs, int n, pdv_tuning* out);
+
+/* Keep pdv_autotune's choices in a JSON file (NULL: no cache). The file maps
+ * "device|sms|sets|packets|snapshots|bins|flags" keys, one per device name
+ * and batch shape, to the chosen pdv_tuning fields. Errors: PDV_EINVAL. */
+pdv_status pdv_set_autotune_cache(pdv_ctx* ctx, const char* path);
 
 /* Measured instruction-issue rate of the context's GPU, the denominator of
  * the issue-rate roofline the transport kernels are reported against (their
@@ -277,23 +298,36 @@ pdv_status pdv_measure_issue_rate(pdv_ctx* ctx, double seconds, double* out);
  * allocate device memory while they run (an allocator or memory plan that
  * forbids cudaMalloc after start-up). The paper has no counterpart: it is a
  * deployment variant. Its scratch is a fixed 4 MiB array in device memory that
- * every GPU loading the library keeps until the process exits; a request must
- * fit in it (about n_snap * (n_bins + 4) * 8 bytes + 1 KiB), else PDV_EINVAL.
- * Outputs must be device buffers (PDV_OUT_DEVICE); precision must be FP32.
- * The cloud's tables are made beforehand by pdv_create_cloud and
- * pdv_set_phase_table. The first call on a device looks the array's device
- * address up, so make that first call before any stream capture. All calls
- * share the array and it keeps the last call's contents (cleared at the start
- * of each call); calls that overlap on the GPU race. Blocking. Errors:
- * PDV_EINVAL, PDV_ECUDA. */
+ * every GPU loading the library keeps until the process exits. A request must
+ * fit in it: 2048 + ceil256(8 n_snap (n_bins + 3)) + ceil256(24 n_snap) bytes
+ * at most 4 MiB, where ceil256 rounds up to a multiple of 256 (roughly
+ * n_snap (n_bins + 6) * 8 + 2.5 KiB), else PDV_EINVAL. Outputs must be device
+ * buffers (PDV_OUT_DEVICE); precision must be FP32. The cloud's tables are
+ * made beforehand by pdv_create_cloud and pdv_set_phase_table. pdv_ctx_create
+ * does all the set-up this call needs: it looks the array's device address up
+ * (which maps the array on the context's device), loads the kernels the call
+ * launches and reserves host buffers for the snapshot times, so the call
+ * itself allocates neither device nor host memory. Do not reset the device
+ * (cudaDeviceReset) while a context lives. All calls share the array and it
+ * keeps the last call's contents (cleared at the start of each call); calls
+ * that overlap on the GPU race. Blocking. Errors: PDV_EINVAL, PDV_ECUDA. */
 pdv_status pdv_simulate_spectrum_static(pdv_ctx* ctx, const pdv_request* req);
 
 /* ---------------------------------------------------------------- serving */
 
 /* Admit a request into the context's continuous-batching loop. The request's
  * cloud and output buffers must stay valid until pdv_poll reports completion.
- * Returns PDV_EAGAIN when device memory or request slots do not allow it now. */
+ * Returns PDV_EAGAIN when device memory or request slots do not allow it now:
+ * at most max_requests submitted requests may be held (running, or finished
+ * and not yet returned by pdv_poll), and the request's device buffers must fit
+ * in the device's free memory less reserve_bytes (pdv_set_serving_limits). */
 pdv_status pdv_submit(pdv_ctx* ctx, const pdv_request* req, pdv_ticket* out);
+
+/* Admission limits of pdv_submit: max_requests in [1, 65536] (default 1024)
+ * and reserve_bytes of device memory kept free (default 256 MiB). A deployment
+ * variant with no counterpart in the paper. Takes effect at the next submit.
+ * Errors: PDV_EINVAL. */
+pdv_status pdv_set_serving_limits(pdv_ctx* ctx, int max_requests, uint64_t reserve_bytes);
 
 /* Wait up to timeout_us for a ticket: PDV_OK (done, outputs written, ticket
  * released), PDV_ENOTREADY (still running), or the request's error. */

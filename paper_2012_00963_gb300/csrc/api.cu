@@ -75,6 +75,8 @@ struct pdv_ctx {
   int sm_count = 0;
   int max_smem = 0;
   pdv_tuning tuning{};
+  std::string tune_cache;              // pdv_autotune's JSON cache file (empty: none)
+  std::string device_name;
   std::mutex mu;                      // serialises synchronous calls on the stream
   std::atomic<unsigned long long> launches{0};
   double last_transport_ms = 0.0;
@@ -103,7 +105,8 @@ struct pdv_ctx {
   std::deque<std::shared_ptr<Request>> active;
   pdv_ticket next_ticket = 1;
   cudaStream_t serve_stream = nullptr;
-  int max_slots = 1024;
+  int max_slots = 1024;                     // admitted requests not yet polled
+  uint64_t mem_reserve = 256ull << 20;     // device memory admission keeps free
   unsigned long long quantum = 1ull << 21;   // packets per request per serving launch
   // pinned staging buffers for served outputs, reused by size class (page-
   // locking memory per request would cost milliseconds of latency)
@@ -111,6 +114,12 @@ struct pdv_ctx {
   std::map<size_t, std::vector<void*>> pinned_free;
   size_t mem_free = 0;
   std::chrono::steady_clock::time_point mem_checked{};
+  // fixed-scratch entry point: the device address of the file-scope scratch
+  // array on this context's device, and host buffers for the snapshot times,
+  // all set up when the context is made (the call itself allocates nothing)
+  char* static_scratch = nullptr;
+  std::vector<double> static_ts;
+  std::vector<int> static_idx;
 };
 
 static size_t pin_class(size_t bytes) {
@@ -187,6 +196,8 @@ struct Layout {
 };
 
 // ------------------------------------------------------------------ context
+static cudaError_t static_scratch_lookup(char** out);
+
 extern "C" pdv_status pdv_ctx_create(int device, void* cuda_stream, const pdv_allocator* alloc,
                                      pdv_ctx** out) {
   if (!out) return fail(PDV_EINVAL, "out is NULL");
@@ -229,10 +240,29 @@ extern "C" pdv_status pdv_ctx_create(int device, void* cuda_stream, const pdv_al
     }
   }
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) c->device_name = prop.name;
+    cudaGetLastError();
+  }
   c->max_smem = transport_f32_max_smem();
   c->tuning.block_threads = 256;
   cudaEventCreate(&c->ev0);
   cudaEventCreate(&c->ev1);
+  // Everything pdv_simulate_spectrum_static needs is made here, so that the
+  // call itself allocates nothing: the scratch array's device address (which
+  // loads this file's module and maps the array on this device), the
+  // transport and normalisation kernels (loaded now, not at their first
+  // launch, under the runtime's lazy module loading), and host buffers for
+  // the snapshot times.
+  cudaError_t e = static_scratch_lookup(&c->static_scratch);
+  if (e == cudaSuccess) e = transport_preload();
+  if (e != cudaSuccess) {
+    pdv_ctx_destroy(c);
+    return fail(PDV_ECUDA, "context set-up failed: %s", cudaGetErrorString(e));
+  }
+  c->static_ts.assign(3 * (size_t)kMaxSnap, 0.0);
+  c->static_idx.assign((size_t)kMaxSnap, 0);
   *out = c;
   return PDV_OK;
 }
@@ -279,7 +309,9 @@ extern "C" pdv_status pdv_set_tuning(pdv_ctx* c, const pdv_tuning* t) {
       t->block_threads != 256)
     return fail(PDV_EINVAL, "block_threads must be 64, 128 or 256");
   if (t->hist_mode < 0 || t->hist_mode > 2) return fail(PDV_EINVAL, "hist_mode must be 0..2");
-  if (t->blocks_per_sm < 0 || t->tile_packets < 0) return fail(PDV_EINVAL, "negative tuning");
+  if (t->blocks_per_sm < 0) return fail(PDV_EINVAL, "negative blocks_per_sm");
+  if (t->tile_packets && (t->tile_packets < 16 || t->tile_packets > 65536))
+    return fail(PDV_EINVAL, "tile_packets must be 0 or in [16, 65536]");
   c->tuning = *t;
   if (!c->tuning.block_threads) c->tuning.block_threads = 256;
   return PDV_OK;
@@ -581,7 +613,10 @@ static pdv_status validate_request(const pdv_request* r) {
   if (!r->out_spectrum) return fail(PDV_EINVAL, "out_spectrum is required");
   if (r->out_packets && r->n_packets > ((r->flags & PDV_OUT_DEVICE) ? (1ull << 28) : (1ull << 26)))
     return fail(PDV_EINVAL, "packet dumps need n_packets <= 2^26 (2^28 into device memory)");
-  if (r->flags & ~(PDV_OUT_DEVICE | PDV_PER_DV | PDV_IMPLICIT_CAPTURE)) return fail(PDV_EINVAL, "unknown flags");
+  if (r->flags & ~(PDV_OUT_DEVICE | PDV_PER_DV | PDV_IMPLICIT_CAPTURE | PDV_TEST_HORIZONTAL_LAUNCH))
+    return fail(PDV_EINVAL, "unknown flags");
+  if (r->n_layers && (r->flags & PDV_TEST_HORIZONTAL_LAUNCH))
+    return fail(PDV_EINVAL, "the horizontal launch runs with exact free paths only (n_layers = 0)");
   if (r->reserved) return fail(PDV_EINVAL, "reserved must be 0");
   if (r->n_layers && r->precision != PDV_PREC_FP32)
     return fail(PDV_EINVAL, "the layer-stepping scheme runs in FP32");
@@ -617,6 +652,7 @@ static SetDesc make_set(const pdv_request* r) {
   d.stream_id = r->stream_id;
   d.max_events = r->max_events ? r->max_events : 1000000u;
   d.implicit = (r->flags & PDV_IMPLICIT_CAPTURE) ? 1u : 0u;
+  d.launch_horizontal = (r->flags & PDV_TEST_HORIZONTAL_LAUNCH) ? 1 : 0;
   d.absorb_gate = d.implicit ? 0u : d.omega_q;
   d.R_q = (unsigned long long)std::floor(cl->desc.reflectivity * kTwo32 + 0.5);
   d.seed = r->seed;
@@ -658,9 +694,8 @@ static SetDesc make_set(const pdv_request* r) {
 // visit only the times at which an escaping packet is inside the aperture.
 static size_t time_words(int n_snap) { return 3 * (size_t)n_snap; }
 
-static void fill_times(const pdv_request* r, double* out) {
+static void fill_times_into(const pdv_request* r, double* out, int* idx) {
   const int n = r->n_snap;
-  int idx[kMaxSnap];
   for (int i = 0; i < n; ++i) idx[i] = i;
   const double* t = r->t_snap_us;
   std::sort(idx, idx + n, [t](int a, int b) { return t[a] < t[b] || (t[a] == t[b] && a < b); });
@@ -669,6 +704,11 @@ static void fill_times(const pdv_request* r, double* out) {
     out[n + i] = t[idx[i]] * 1e-6;
     out[2 * n + i] = (double)idx[i];
   }
+}
+
+static void fill_times(const pdv_request* r, double* out) {
+  int idx[kMaxSnap];
+  fill_times_into(r, out, idx);
 }
 
 // Device buffers of one request: set descriptor, counters, histogram,
@@ -786,7 +826,8 @@ static pdv_status enqueue_transport(pdv_ctx* c, const pdv_request* r, const SetD
     pdv_status s = f32_geometry(c, smem, hm, dump, impl, &grid, &block);
     if (s != PDV_OK) return s;
     launch_transport_f32((const SetDesc*)(base + b.o_set), 1,
-                         (unsigned long long*)(base + b.o_ctr), grid, block, smem, hm, dump, impl, st);
+                         (unsigned long long*)(base + b.o_ctr), grid, block, smem, hm, dump, impl,
+                         (unsigned)c->tuning.tile_packets, st);
     c->last_grid = grid;
     c->last_block = block;
   } else {
@@ -916,7 +957,8 @@ static std::string batch_key(const pdv_ctx* c, const pdv_request* rs, int n, int
                              size_t smem, int hm, bool dump) {
   std::string k;
   char buf[128];
-  snprintf(buf, sizeof buf, "%d|%d|%d|%zu|%d|%d|", n, grid, block, smem, hm, (int)dump);
+  snprintf(buf, sizeof buf, "%d|%d|%d|%zu|%d|%d|%d|", n, grid, block, smem, hm, (int)dump,
+           c->tuning.tile_packets);
   k += buf;
   for (int i = 0; i < n; ++i) {
     const pdv_request& r = rs[i];
@@ -925,7 +967,6 @@ static std::string batch_key(const pdv_ctx* c, const pdv_request* rs, int n, int
              r.out_packets ? (unsigned long long)r.n_packets : 0ull);
     k += buf;
   }
-  (void)c;
   return k;
 }
 
@@ -984,7 +1025,8 @@ static pdv_status run_batch_f32(pdv_ctx* c, const pdv_request* rs, int n, bool t
       cudaMemsetAsync(base + B.o_hist, 0, sizeof(unsigned long long) * B.hist_words, cap);
       cudaEventRecordWithFlags(c->ev0, cap, cudaEventRecordExternal);
       launch_transport_f32((const SetDesc*)(base + B.o_sets), n,
-                           (unsigned long long*)(base + B.o_ctr), grid, block, smem, hm, dump, impl, cap);
+                           (unsigned long long*)(base + B.o_ctr), grid, block, smem, hm, dump, impl,
+                           (unsigned)c->tuning.tile_packets, cap);
       cudaEventRecordWithFlags(c->ev1, cap, cudaEventRecordExternal);
       int max_snap = 1;
       for (int i = 0; i < n; ++i) max_snap = std::max(max_snap, rs[i].n_snap);
@@ -1135,6 +1177,69 @@ extern "C" pdv_status pdv_measure_issue_rate(pdv_ctx* c, double seconds, double*
   return PDV_OK;
 }
 
+// Autotune cache: a flat JSON object {"key": {"block_threads": b, "blocks_per_sm": s,
+// "tile_packets": t, "hist_mode": h, "ms": m}, ...}, written and read only here.
+static std::string tune_key(const pdv_ctx* c, const pdv_request* rs, int n) {
+  unsigned long long pk = 0;
+  int snap = 0, bins = 0;
+  unsigned flags = 0;
+  for (int i = 0; i < n; ++i) {
+    pk += rs[i].n_packets;
+    snap = std::max(snap, rs[i].n_snap);
+    bins = std::max(bins, rs[i].n_bins);
+    flags |= rs[i].flags & PDV_IMPLICIT_CAPTURE;
+    if (rs[i].probe.aperture_radius_mm <= 0) flags |= 0x100u;
+  }
+  std::string name = c->device_name;
+  for (char& ch : name)
+    if (ch == '"' || ch == '\\' || ch == '|') ch = '_';
+  char buf[320];
+  snprintf(buf, sizeof buf, "%s|%d|%d|%.1e|%d|%d|%x", name.c_str(), c->sm_count, n, (double)pk,
+           snap, bins, flags);
+  return buf;
+}
+
+static bool tune_cache_find(const std::string& text, const std::string& key, pdv_tuning* t) {
+  const std::string q = "\"" + key + "\"";
+  const size_t at = text.find(q);
+  if (at == std::string::npos) return false;
+  const size_t open = text.find('{', at + q.size()), close = text.find('}', at + q.size());
+  if (open == std::string::npos || close == std::string::npos || close < open) return false;
+  const std::string body = text.substr(open, close - open);
+  auto field = [&](const char* f, int* v) {
+    const size_t p = body.find(std::string("\"") + f + "\"");
+    if (p == std::string::npos) return false;
+    const size_t colon = body.find(':', p);
+    return colon != std::string::npos && sscanf(body.c_str() + colon + 1, "%d", v) == 1;
+  };
+  pdv_tuning r{};
+  if (!field("block_threads", &r.block_threads) || !field("blocks_per_sm", &r.blocks_per_sm) ||
+      !field("tile_packets", &r.tile_packets) || !field("hist_mode", &r.hist_mode))
+    return false;
+  *t = r;
+  return true;
+}
+
+static std::string read_file(const std::string& path) {
+  std::string out;
+  FILE* f = fopen(path.c_str(), "rb");
+  if (!f) return out;
+  char buf[4096];
+  size_t k;
+  while ((k = fread(buf, 1, sizeof buf, f)) > 0) out.append(buf, k);
+  fclose(f);
+  return out;
+}
+
+static std::mutex g_tune_file_mu;
+
+extern "C" pdv_status pdv_set_autotune_cache(pdv_ctx* c, const char* path) {
+  if (!c) return fail(PDV_EINVAL, "ctx is NULL");
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->tune_cache = path ? path : "";
+  return PDV_OK;
+}
+
 extern "C" pdv_status pdv_autotune(pdv_ctx* c, const pdv_request* rs, int n, pdv_tuning* out) {
   if (!c || !rs || n < 1) return fail(PDV_EINVAL, "need a context and n >= 1 requests");
   for (int i = 0; i < n; ++i) {
@@ -1144,6 +1249,23 @@ extern "C" pdv_status pdv_autotune(pdv_ctx* c, const pdv_request* rs, int n, pdv
       return fail(PDV_EINVAL, "autotune takes FP32 exact-free-path requests");
   }
   CK(enter(c->device));
+  const std::string key = tune_key(c, rs, n);
+  std::string cache;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    cache = c->tune_cache;
+  }
+  if (!cache.empty()) {
+    std::lock_guard<std::mutex> fl(g_tune_file_mu);
+    pdv_tuning t{};
+    if (tune_cache_find(read_file(cache), key, &t)) {
+      std::lock_guard<std::mutex> lk(c->mu);
+      c->tuning = t;
+      if (!c->tuning.block_threads) c->tuning.block_threads = 256;
+      if (out) *out = c->tuning;
+      return PDV_OK;
+    }
+  }
   // a shortened copy of the batch (1/16 of the packets, at least 65536 each)
   std::vector<pdv_request> shortb(rs, rs + n);
   std::vector<std::vector<double>> specs(n);
@@ -1158,34 +1280,62 @@ extern "C" pdv_status pdv_autotune(pdv_ctx* c, const pdv_request* rs, int n, pdv
     r.out_packets = nullptr;
     r.flags &= ~PDV_OUT_DEVICE;
   }
-  const pdv_tuning saved = c->tuning;
-  pdv_tuning best = saved;
+  pdv_tuning best{};
   float best_ms = 1e30f;
   const int blocks[] = {128, 256};
   const int modes[] = {1, 2};
-  const int bps[] = {0, 1, 2};
+  const int bps[] = {0, 2};
+  const int chunks[] = {32, 64, 256};
   std::lock_guard<std::mutex> lk(c->mu);
+  const pdv_tuning saved = c->tuning;
+  best = saved;
   for (int bt : blocks)
     for (int hm : modes)
-      for (int b : bps) {
-        pdv_tuning t{};
-        t.block_threads = bt;
-        t.hist_mode = hm;
-        t.blocks_per_sm = b;
-        c->tuning = t;
-        float ms = 0.f, total = 0.f;
-        bool ok = true;
-        for (int rep = 0; rep < 3 && ok; ++rep) {
-          if (run_batch_f32(c, shortb.data(), n, true, &ms) != PDV_OK) ok = false;
-          if (rep) total += ms;        // first run warms up (and captures the graph)
+      for (int b : bps)
+        for (int ch : chunks) {
+          pdv_tuning t{};
+          t.block_threads = bt;
+          t.hist_mode = hm;
+          t.blocks_per_sm = b;
+          t.tile_packets = ch;
+          c->tuning = t;
+          float ms = 0.f, total = 0.f;
+          bool ok = true;
+          for (int rep = 0; rep < 3 && ok; ++rep) {
+            if (run_batch_f32(c, shortb.data(), n, true, &ms) != PDV_OK) ok = false;
+            if (rep) total += ms;        // first run warms up (and captures the graph)
+          }
+          if (ok && total < best_ms) {
+            best_ms = total;
+            best = t;
+          }
         }
-        if (ok && total < best_ms) {
-          best_ms = total;
-          best = t;
-        }
-      }
   c->tuning = best;
   if (out) *out = best;
+  if (!cache.empty()) {
+    // read-modify-write of the whole file: add this key's entry before the final '}'
+    std::lock_guard<std::mutex> fl(g_tune_file_mu);
+    std::string text = read_file(cache);
+    const size_t last = text.rfind('}');
+    char entry[512];
+    snprintf(entry, sizeof entry,
+             "\"%s\": {\"block_threads\": %d, \"blocks_per_sm\": %d, \"tile_packets\": %d, "
+             "\"hist_mode\": %d, \"ms\": %.4f}", key.c_str(), best.block_threads, best.blocks_per_sm,
+             best.tile_packets, best.hist_mode, best_ms / 2.0);
+    if (last == std::string::npos || text.find('"') == std::string::npos)
+      text = std::string("{\n  ") + entry + "\n}\n";
+    else
+      text = text.substr(0, last) + ",\n  " + entry + "\n}\n";
+    const std::string tmp = cache + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "wb");
+    if (!f || fwrite(text.data(), 1, text.size(), f) != text.size()) {
+      if (f) fclose(f);
+      return fail(PDV_EINVAL, "cannot write the autotune cache %s", cache.c_str());
+    }
+    fclose(f);
+    if (rename(tmp.c_str(), cache.c_str()) != 0)
+      return fail(PDV_EINVAL, "cannot replace the autotune cache %s", cache.c_str());
+  }
   return PDV_OK;
 }
 
@@ -1374,7 +1524,7 @@ static void serving_loop(pdv_ctx* c) {
     unsigned long long* ctr = (unsigned long long*)(s.d_mem + sizeof(SetDesc) * kMaxLaunchSets);
     cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * n, c->serve_stream);
     launch_transport_f32((const SetDesc*)s.d_mem, n, ctr, grid, block, smem, hm, false, impl,
-                         c->serve_stream);
+                         (unsigned)c->tuning.tile_packets, c->serve_stream);
     c->launches += 1;
     cudaEventRecord(s.ev, c->serve_stream);
     s.items = std::move(items);
@@ -1437,8 +1587,9 @@ extern "C" pdv_status pdv_submit(pdv_ctx* c, const pdv_request* r, pdv_ticket* o
     if ((int)c->requests.size() >= c->max_slots)
       return fail(PDV_EAGAIN, "all %d request slots are in use", c->max_slots);
   }
-  // admission by free device memory (keep 256 MiB in reserve); the driver is
-  // asked at most every 20 ms and the bytes admitted since are subtracted
+  // admission by free device memory (keeping mem_reserve free, 256 MiB by
+  // default); the driver is asked at most every 20 ms and the bytes admitted
+  // since are subtracted
   {
     std::lock_guard<std::mutex> lk(c->smu);
     const auto now = std::chrono::steady_clock::now();
@@ -1448,7 +1599,9 @@ extern "C" pdv_status pdv_submit(pdv_ctx* c, const pdv_request* r, pdv_ticket* o
       c->mem_free = fr;
       c->mem_checked = now;
     }
-    if (c->mem_free < q->b.bytes + (256ull << 20)) return fail(PDV_EAGAIN, "not enough free device memory");
+    if (c->mem_free < q->b.bytes || c->mem_free - q->b.bytes < c->mem_reserve)
+      return fail(PDV_EAGAIN, "not enough free device memory (%zu bytes free, %zu needed + %llu kept free)",
+                  c->mem_free, q->b.bytes, (unsigned long long)c->mem_reserve);
     c->mem_free -= q->b.bytes;
   }
   q->arena = (char*)ctx_alloc(c, q->b.bytes, c->serve_stream);
@@ -1504,6 +1657,15 @@ extern "C" pdv_status pdv_submit(pdv_ctx* c, const pdv_request* r, pdv_ticket* o
   }
   c->scv.notify_all();
   *out = q->id;
+  return PDV_OK;
+}
+
+extern "C" pdv_status pdv_set_serving_limits(pdv_ctx* c, int max_requests, uint64_t reserve_bytes) {
+  if (!c) return fail(PDV_EINVAL, "ctx is NULL");
+  if (max_requests < 1 || max_requests > 65536) return fail(PDV_EINVAL, "max_requests must be in [1, 65536]");
+  std::lock_guard<std::mutex> lk(c->smu);
+  c->max_slots = max_requests;
+  c->mem_reserve = reserve_bytes;
   return PDV_OK;
 }
 
@@ -1564,23 +1726,28 @@ constexpr size_t kStaticScratchBytes = 4u << 20;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 // In host code g_static_scratch names a host-side stand-in, not device memory:
-// its device address is looked up once per device, with that device current.
-static std::mutex g_static_mu;
-static void* g_static_addr[128] = {nullptr};
+// pdv_ctx_create looks its device address up with the context's device
+// current and keeps it in the context.
+static cudaError_t static_scratch_lookup(char** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  *out = (char*)p;
+  if (e == cudaSuccess && !p) return cudaErrorInvalidSymbol;
+  return e;
+}
 
-static pdv_status static_scratch_address(int device, char** out) {
-  std::lock_guard<std::mutex> lk(g_static_mu);
-  if (device < 0 || device >= 128) return fail(PDV_EINVAL, "device %d out of range", device);
-  if (!g_static_addr[device]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(PDV_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
-                  cudaGetErrorString(e));
-    g_static_addr[device] = p;
-  }
-  *out = (char*)g_static_addr[device];
-  return PDV_OK;
+// Scratch layout: a 1024-byte slot for the set descriptor, four 256-byte
+// slots (packet counter, event counters, normalisation pointers, flags), then
+// the histogram and the snapshot times, each rounded up to 256 bytes:
+//   2048 + ceil256(8 n_snap (n_bins + 3)) + ceil256(24 n_snap) <= 4 MiB.
+static_assert(sizeof(SetDesc) <= 1024, "set descriptor slot");
+static_assert(sizeof(unsigned long long) * C_NCOUNT <= 256, "counter slot");
+
+static size_t ceil256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static size_t static_scratch_bytes(int n_snap, int n_bins) {
+  return 2048 + ceil256(sizeof(unsigned long long) * (size_t)hist_row(n_bins) * n_snap) +
+         ceil256(sizeof(double) * time_words(n_snap));
 }
 
 extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request* r) {
@@ -1590,33 +1757,24 @@ extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request
   if (r->n_layers) return fail(PDV_EINVAL, "layer stepping runs through pdv_simulate_spectrum only");
   if (r->precision != PDV_PREC_FP32) return fail(PDV_EINVAL, "the static-scratch call runs FP32 requests");
   if (!(r->flags & PDV_OUT_DEVICE)) return fail(PDV_EINVAL, "the static-scratch call needs PDV_OUT_DEVICE outputs");
-  // scratch layout: set descriptor, packet counter, counters, histogram,
-  // snapshot times, normalisation pointers and flags
-  Layout L;
-  const size_t o_set = L.add(sizeof(SetDesc));
-  const size_t o_ctr = L.add(sizeof(unsigned long long));
-  const size_t o_cnt = L.add(sizeof(unsigned long long) * C_NCOUNT);
+  const size_t need = static_scratch_bytes(r->n_snap, r->n_bins);
+  if (need > kStaticScratchBytes)
+    return fail(PDV_EINVAL, "request needs %zu bytes of scratch (2048 + ceil256(8 n_snap (n_bins + 3)) "
+                "+ ceil256(24 n_snap)); the static scratch holds %zu", need, kStaticScratchBytes);
+  const size_t o_set = 0, o_ctr = 1024, o_cnt = 1280, o_ptr = 1536, o_flags = 1792, o_hist = 2048;
   const size_t hist_words = (size_t)hist_row(r->n_bins) * r->n_snap;
-  const size_t o_hist = L.add(sizeof(unsigned long long) * hist_words);
-  const size_t o_t = L.add(sizeof(double) * time_words(r->n_snap));
-  const size_t o_ptr = L.add(sizeof(void*) * 3);
-  const size_t o_flags = L.add(sizeof(unsigned));
-  if (L.bytes > kStaticScratchBytes)
-    return fail(PDV_EINVAL, "request needs %zu bytes of scratch; the static scratch holds %zu "
-                "(n_snap * (n_bins + 3) * 8 + n_snap * 24 + about 1 KiB)", L.bytes, kStaticScratchBytes);
+  const size_t o_t = o_hist + ceil256(sizeof(unsigned long long) * hist_words);
   CK(enter(c->device));
-  char* base = nullptr;
-  s = static_scratch_address(c->device, &base);
-  if (s != PDV_OK) return s;
   std::lock_guard<std::mutex> lk(c->mu);
+  char* base = c->static_scratch;
   cudaStream_t st = c->stream;
   SetDesc d = make_set(r);
   d.t_snap = (const double*)(base + o_t);
   d.hist = (unsigned long long*)(base + o_hist);
   d.cnt = (unsigned long long*)(base + o_cnt);
   d.packets = r->out_packets;
-  double ts[3 * kMaxSnap];          // on the stack: no allocation, heap or TLS
-  fill_times(r, ts);
+  double* ts = c->static_ts.data();            // made with the context: no allocation here
+  fill_times_into(r, ts, c->static_idx.data());
   void* ptrs[3] = {(void*)r->out_spectrum, (void*)r->out_counters, (void*)r->out_raw};
   const unsigned flags = r->flags;
   CK(cudaMemcpyAsync(base + o_t, ts, sizeof(double) * time_words(r->n_snap), cudaMemcpyHostToDevice, st));
@@ -1636,7 +1794,7 @@ extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request
   s = f32_geometry(c, smem, hm, dump, impl, &grid, &block);
   if (s != PDV_OK) return s;
   launch_transport_f32((const SetDesc*)(base + o_set), 1, (unsigned long long*)(base + o_ctr),
-                       grid, block, smem, hm, dump, impl, st);
+                       grid, block, smem, hm, dump, impl, (unsigned)c->tuning.tile_packets, st);
   launch_normalise((const SetDesc*)(base + o_set), 1, (double* const*)(base + o_ptr),
                    (pdv_counters* const*)(base + o_ptr + sizeof(void*)),
                    (unsigned long long* const*)(base + o_ptr + 2 * sizeof(void*)),

@@ -84,6 +84,7 @@ struct SetDesc {
   int n_snap, n_bins;
   int surface_mode, cone_all, ap_all, phase_uniform;   // theta_i = pi i / (n_p - 1)
   int expo;                           // exponential law (Eq. 20): velocities by its closed-form inverse
+  int launch_horizontal;              // PDV_TEST_HORIZONTAL_LAUNCH: packets start along +x
   unsigned omega_q, stream_id, max_events;
   unsigned implicit;                  // PDV_IMPLICIT_CAPTURE: weight omega per interaction + roulette
   unsigned absorb_gate;               // r1 >> 8 at or above it leaves the scatter path: omega_q, or 0 (implicit)
@@ -192,9 +193,10 @@ __device__ __forceinline__ float u64_to_f(unsigned long long d) {
 // Kernel entry points (defined in the .cu files).
 // impl: some set of the launch has PDV_IMPLICIT_CAPTURE (a kernel build that
 // holds the implicit-capture branch; the analog build leaves it out).
+// chunk: packets a warp claims at a time (0: the default, 64)
 void launch_transport_f32(const SetDesc* d_sets, int n_sets, unsigned long long* d_set_ctr,
                           int grid, int block, size_t smem, int hist_mode, bool dump, bool impl,
-                          cudaStream_t st);
+                          unsigned chunk, cudaStream_t st);
 void launch_transport_f64(const SetDesc* d_set, int grid, int block, cudaStream_t st);
 void launch_normalise(const SetDesc* d_sets, int n_sets, double* const* d_spec,
                       pdv_counters* const* d_cnt_out, unsigned long long* const* d_raw,
@@ -202,6 +204,9 @@ void launch_normalise(const SetDesc* d_sets, int n_sets, double* const* d_spec,
 size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode,
                           int phase_uniform, int ap_all, int expo);
 int transport_f32_max_smem();
+// Load every FP32 transport build and the normalisation kernel on the current
+// device now (the runtime otherwise loads a kernel at its first launch).
+cudaError_t transport_preload();
 cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, bool impl,
                                     int* blocks);
 

@@ -490,12 +490,12 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
       float sp, cp;
       sincospif(2.0f * u23f(r_phi), &sp, &cp);                         // Eq. 15
       float nx, ny, nz;
-      if (fabsf(uz) > 1.0f - 1e-6f) {                                // Eq. 17
+      const float h2 = fmaf(ux, ux, uy * uy);
+      if (h2 < 1e-30f) {                                             // Eq. 17: vertical
         nx = st * cp;
         ny = st * sp;
         nz = uz >= 0.0f ? ct : -ct;
       } else {                                                       // Eq. 16
-        const float h2 = fmaf(ux, ux, uy * uy);
         const float rs = rsqrtf(h2);
         const float s = h2 * rs;
         const float a = st * rs;

@@ -36,8 +36,11 @@
 namespace pdv {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr unsigned kChunk = 64;          // packets claimed per warp refill
+// Packets a warp claims from its set's counter at a time (the launch's
+// chunk, pdv_tuning.tile_packets; kChunkDefault when 0)
+constexpr unsigned kChunkDefault = 64;
 constexpr float kTwoM62f = 2.168404344971009e-19f;   // 2^-62
+constexpr float kTwoM30f = 9.313225746154785e-10f;   // 2^-30
 
 struct SmemTables {
   const unsigned long long* Sq;
@@ -140,7 +143,8 @@ __device__ __forceinline__ void launch_position(unsigned long long pk, unsigned 
 template <bool DUMP, int HMODE, bool IMPL>
 __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restrict__ sets,
                                                           int n_sets,
-                                                          unsigned long long* __restrict__ set_ctr) {
+                                                          unsigned long long* __restrict__ set_ctr,
+                                                          unsigned chunk) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SetDesc sd;
   __shared__ unsigned long long s_cnt[C_NCOUNT];
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
     // atomic's latency is hidden behind a chunk's worth of events.
     unsigned pool_next = 0, pool_end = 0;
     unsigned long long pre = 0;
-    if (lane == 0) pre = atomicAdd(&set_ctr[si], (unsigned long long)kChunk);
+    if (lane == 0) pre = atomicAdd(&set_ctr[si], (unsigned long long)chunk);
     bool exhausted = false, alive = false;
     unsigned long long pk = 0, W = 0;
     long long Sq = 0;
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
     float vcur = 0.f, ux = 0.f, uy = 0.f, uz = -1.f, iuz = -1.f;
     float Xx = 0.f, Xy = 0.f, vapp = 0.f, vcomp = 0.f;
     unsigned st_launch = 0, st_events = 0, st_scat = 0, st_surf = 0, st_esc = 0;
-    unsigned long long st_wesc = 0, st_wabs = 0;     // escaped / absorbed weight
+    unsigned long long st_wesc = 0, st_wabs = 0, st_wsurf = 0;   // escaped / absorbed weight
 
     for (;;) {
       // refill dead lanes from the warp's chunk of packets
@@ -259,9 +263,9 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
             exhausted = true;
             break;
           }
-          if (lane == 0) pre = atomicAdd(&set_ctr[si], (unsigned long long)kChunk);
+          if (lane == 0) pre = atomicAdd(&set_ctr[si], (unsigned long long)chunk);
           pool_next = (unsigned)b;
-          pool_end = n_pk - pool_next > kChunk ? pool_next + kChunk : n_pk;
+          pool_end = n_pk - pool_next > chunk ? pool_next + chunk : n_pk;
           continue;
         }
         const unsigned cnt = __popc(need);
@@ -271,6 +275,9 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
           // Step (1): a new packet at the top of the cloud moving along -z
           pk = base_pk + (pool_next + rank);
           ux = 0.f; uy = 0.f; uz = -1.f; iuz = -1.f;
+          if (sd.launch_horizontal) {      // test hook: the horizontal-flight rule
+            ux = 1.f; uz = 0.f; iuz = 0.f;
+          }
           Sq = (long long)kOneQ;
           vcur = sd.v_top_f;
           Xx = 0.f; Xy = 0.f; vapp = 0.f; vcomp = 0.f;
@@ -284,48 +291,41 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
         need = __ballot_sync(kFull, !alive);
       }
       if (!__any_sync(kFull, alive)) break;
-      if (!alive) continue;
 
-      // ---- one flight and what ends it
+      // ---- one flight and what ends it. Every lane runs the same straight
+      // line; the outcome's predicates select what each lane commits, and a
+      // lane without a packet (at the end of a set) commits nothing.
       const uint4 r = philox4x32_10_rk(make_uint4((unsigned)pk, (unsigned)(pk >> 32), kev, sid), s_rk);
       ++kev;
       const float tau = -logf(u23f(r.x));                // Step (3): Beer–Lambert
+      const float dS = tau * uz * inv_tau;
+      const bool horiz = fabsf(uz) < 1e-9f;
+      // the largest binary32 magnitude below 1 keeps fix62 in range; a flight of
+      // |dS| >= 1 leaves the cloud whatever its fixed-point end
+      const long long Sn = Sq + fix62(fminf(fmaxf(dS, -0.99999994f), 0.99999994f));
       // 0 interaction, 1 escape through the top, 2 free surface, 3 horizontal
-      int what;
-      long long Sn = Sq;
-      if (fabsf(uz) < 1e-9f) {
-        what = 3;
-      } else {
-        const float dS = tau * uz * inv_tau;
-        if (dS >= 1.0f) what = 1;
-        else if (dS <= -1.0f) what = 2;
-        else {
-          Sn = Sq + fix62(dS);
-          what = (Sn >= (long long)kOneQ) ? 1 : (Sn <= 0 ? 2 : 0);
-        }
-      }
+      const int what = horiz ? 3
+                             : ((dS >= 1.0f || Sn >= (long long)kOneQ) ? 1
+                                                                        : ((dS <= -1.0f || Sn <= 0) ? 2 : 0));
       // velocity coordinate z/t where the flight ends
       float vn = vcur;
-      if (what == 0) {
-        if (sd.expo) {
-          // Eq. 20 inverted in closed form: v = v_fs (1 - ln((1 - S) + S eps) / beta); 1 - S is
-          // exact in the fixed-point state, so the top of the cloud keeps its relative precision
-          const float q = fmaf(__ull2float_rn((unsigned long long)Sn) * kTwoM62f, sd.eps_f,
-                               __ull2float_rn(kOneQ - (unsigned long long)Sn) * kTwoM62f);
-          vn = fmaf(-sd.lg_c_f, __log2f(q), sd.v_fs_f);
-        } else {
-          const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sn);
-          const float fd = u64_to_f((unsigned long long)Sn - tb.Sq[j]);
-          vn = fmaf(fd, tb.w[j], fmaf((float)j, sd.dv_f, sd.v_bot_f));
-        }
-      } else if (what == 1) {
-        vn = sd.v_top_f;
-      } else if (what == 2) {
-        vn = sd.v_fs_f;
-        Sn = 0;
+      if (sd.expo) {
+        // Eq. 20 inverted in closed form: v = v_fs (1 - ln((1 - S) + S eps) / beta); 1 - S is
+        // exact in the fixed-point state, so the top of the cloud keeps its relative precision
+        // (32-bit conversions: the 64-bit ones run on the FP64 pipe)
+        const unsigned long long sn = (unsigned long long)Sn, oms = kOneQ - sn;
+        const float om = fmaf(__uint2float_rn((unsigned)(oms >> 32)), kTwoM30f,
+                              __uint2float_rn((unsigned)oms) * kTwoM62f);
+        const float q = fmaf(__uint2float_rn((unsigned)(sn >> 32)) * kTwoM30f, sd.eps_f, om);
+        vn = fmaf(-sd.lg_c_f, __log2f(q), sd.v_fs_f);
+      } else if (what == 0) {
+        const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sn);
+        const float fd = u64_to_f((unsigned long long)Sn - tb.Sq[j]);
+        vn = fmaf(fd, tb.w[j], fmaf((float)j, sd.dv_f, sd.v_bot_f));
       }
+      vn = what == 1 ? sd.v_top_f : (what == 2 ? sd.v_fs_f : (what == 3 ? vcur : vn));
       // lateral displacement in velocity units (x = x0 + t X)
-      if (what != 3) {
+      if (!horiz) {
         const float d = vn - vcur;
         Xx = fmaf(ux * iuz, d, Xx);
         Xy = fmaf(uy * iuz, d, Xy);
@@ -333,8 +333,10 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
         // horizontal packet: lateral path tau / mu(z), in velocity units tau / tau_tot dv/dS
         float dvds;
         if (sd.expo) {
-          dvds = sd.dvds_c_f / fmaf(__ull2float_rn((unsigned long long)Sq) * kTwoM62f, sd.eps_f,
-                                    __ull2float_rn(kOneQ - (unsigned long long)Sq) * kTwoM62f);
+          const unsigned long long sq = (unsigned long long)Sq, oms = kOneQ - sq;
+          const float om = fmaf(__uint2float_rn((unsigned)(oms >> 32)), kTwoM30f,
+                                __uint2float_rn((unsigned)oms) * kTwoM62f);
+          dvds = sd.dvds_c_f / fmaf(__uint2float_rn((unsigned)(sq >> 32)) * kTwoM30f, sd.eps_f, om);
         } else {
           const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sq);
           dvds = tb.w[j] * 4.611686018427388e18f;
@@ -343,170 +345,178 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
         Xx = fmaf(ux, len, Xx);
         Xy = fmaf(uy, len, Xy);
       }
-      unsigned fate = 0;
-      if (what == 1) {
-        // Step (6): out through the top, vacuum flight to the probe plane
-        if (sd.cone_all || uz >= sd.cos_alpha_f) {
-          const float fb = floorf((vapp - vcomp - sd.v_lo_f) * sd.inv_dbin_f);
-          const int idx = fb < 0.0f ? 0 : (fb >= (float)n_bins ? n_bins + 1 : (int)fb + 1);
-          if (sd.ap_all) {
-            // Eq. 19 at every snapshot time alike (unlimited aperture): one
-            // tally in row 0, which the normalisation reads for each time
-            atomicAdd(&tb.hist[idx], W);
-            atomicAdd(&tb.hist[n_bins + 2], 1ull);
-            if (DUMP) dmask = n_snap >= 64 ? ~0ull : ((1ull << n_snap) - 1ull);
-          } else {
-            float x0, y0;
-            launch_position(pk, sid, key, sd.r_beam_f, x0, y0);
-            const float tx = ux * iuz, ty = uy * iuz;
-            const float ax = fmaf(tx, sd.z_probe_f, x0), ay = fmaf(ty, sd.z_probe_f, y0);
-            const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
-            // |a + t b|^2 <= R^2 holds on one interval of t: visit the ascending
-            // snapshot times inside it, plus one on each side, each re-tested
-            // exactly as below (the interval only narrows the search)
-            int s0 = 0, s1 = n_snap;
-            const float A = fmaf(bx, bx, by * by);
-            const float B = 2.0f * fmaf(ax, bx, ay * by);
-            const float Cc = fmaf(ax, ax, fmaf(ay, ay, -sd.r_ap2_f));
-            const float disc = fmaf(B, B, -4.0f * A * Cc);
-            if (A > 0.0f) {
-              if (disc < 0.0f) {
-                s1 = 0;
-              } else {
-                const float q = sqrtf(disc), ia = 0.5f / A;
-                const float t1 = (-B - q) * ia, t2 = (-B + q) * ia;
-                int lo = 0, hi = n_snap;                   // first time >= t1
-                while (lo < hi) {
-                  const int mid = (lo + hi) >> 1;
-                  if (tb.ts[mid] < t1) lo = mid + 1; else hi = mid;
-                }
-                s0 = lo > 0 ? lo - 1 : 0;
-                hi = n_snap;                               // first time > t2
-                while (lo < hi) {
-                  const int mid = (lo + hi) >> 1;
-                  if (tb.ts[mid] <= t2) lo = mid + 1; else hi = mid;
-                }
-                s1 = lo < n_snap ? lo + 1 : n_snap;
+
+      // ---- Step (6): out through the top, vacuum flight to the probe plane
+      const bool esc = alive && what == 1;
+      if (esc && (sd.cone_all || uz >= sd.cos_alpha_f)) {
+        const float fb = floorf((vapp - vcomp - sd.v_lo_f) * sd.inv_dbin_f);
+        const int idx = fb < 0.0f ? 0 : (fb >= (float)n_bins ? n_bins + 1 : (int)fb + 1);
+        if (sd.ap_all) {
+          // Eq. 19 at every snapshot time alike (unlimited aperture): one
+          // tally in row 0, which the normalisation reads for each time
+          atomicAdd(&tb.hist[idx], W);
+          atomicAdd(&tb.hist[n_bins + 2], 1ull);
+          if (DUMP) dmask = n_snap >= 64 ? ~0ull : ((1ull << n_snap) - 1ull);
+        } else {
+          float x0, y0;
+          launch_position(pk, sid, key, sd.r_beam_f, x0, y0);
+          const float tx = ux * iuz, ty = uy * iuz;
+          const float ax = fmaf(tx, sd.z_probe_f, x0), ay = fmaf(ty, sd.z_probe_f, y0);
+          const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
+          // |a + t b|^2 <= R^2 holds on one interval of t: visit the ascending
+          // snapshot times inside it, plus one on each side, each re-tested
+          // exactly as below (the interval only narrows the search)
+          int s0 = 0, s1 = n_snap;
+          const float A = fmaf(bx, bx, by * by);
+          const float B = 2.0f * fmaf(ax, bx, ay * by);
+          const float Cc = fmaf(ax, ax, fmaf(ay, ay, -sd.r_ap2_f));
+          const float disc = fmaf(B, B, -4.0f * A * Cc);
+          if (A > 0.0f) {
+            if (disc < 0.0f) {
+              s1 = 0;
+            } else {
+              const float q = sqrtf(disc), ia = 0.5f / A;
+              const float t1 = (-B - q) * ia, t2 = (-B + q) * ia;
+              int lo = 0, hi = n_snap;                   // first time >= t1
+              while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (tb.ts[mid] < t1) lo = mid + 1; else hi = mid;
               }
+              s0 = lo > 0 ? lo - 1 : 0;
+              hi = n_snap;                               // first time > t2
+              while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (tb.ts[mid] <= t2) lo = mid + 1; else hi = mid;
+              }
+              s1 = lo < n_snap ? lo + 1 : n_snap;
             }
-            for (int s = s0; s < s1; ++s) {
-              const float t = tb.ts[s];
-              const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
-              if (fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
-                // Eq. 19: tally the out-photon at its frequency shift
-                const int sr = tb.perm[s];
-                atomicAdd(&tb.hist[(size_t)sr * row + idx], W);
-                atomicAdd(&tb.hist[(size_t)sr * row + n_bins + 2], 1ull);
-                if (DUMP && sr < 64) dmask |= 1ull << sr;
-              }
+          }
+          for (int s = s0; s < s1; ++s) {
+            const float t = tb.ts[s];
+            const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
+            if (fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
+              // Eq. 19: tally the out-photon at its frequency shift
+              const int sr = tb.perm[s];
+              atomicAdd(&tb.hist[(size_t)sr * row + idx], W);
+              atomicAdd(&tb.hist[(size_t)sr * row + n_bins + 2], 1ull);
+              if (DUMP && sr < 64) dmask |= 1ull << sr;
             }
           }
         }
-        ++st_esc;
-        st_wesc += W;
-        fate = 1;
-      } else {
-        Sq = Sn;
+      }
+      st_esc += esc ? 1u : 0u;
+      st_wesc += esc ? W : 0ull;
+
+      // ---- an event: interaction (what 0, 3) or the free surface (what 2)
+      const bool ev = alive && what != 1;
+      const bool surf = ev && what == 2;
+      if (ev) {
+        Sq = what == 2 ? 0ll : (what == 3 ? Sq : Sn);
         vcur = vn;
         --nev;
         ++st_events;
-        const bool surf = what == 2;
-        if (surf) {
-          // Step (6): free surface z = v_fs t, reflectivity in 2^32 fixed point
-          ++st_surf;
-          if (DUMP) ++nsurf;
-          const unsigned long long Wn =
-              sd.R_q >= (1ull << 32) ? W : ((W * sd.R_q + (1ull << 31)) >> 32);
-          if (Wn != W) atomicAdd(&s_cnt[C_W_ABS_SURFACE], W - Wn);
+      }
+      // Step (6): free surface z = v_fs t, reflectivity in 2^32 fixed point
+      const unsigned long long Wr =
+          sd.R_q >= (1ull << 32) ? W : ((W * sd.R_q + (1ull << 31)) >> 32);
+      st_surf += surf ? 1u : 0u;
+      if (DUMP) nsurf += surf ? 1u : 0u;
+      st_wsurf += surf ? W - Wr : 0ull;
+      W = surf ? Wr : W;
+      // Eq. 11: analog absorption (the gate is omega_q). Implicit capture (gate
+      // 0): the particle absorbs 1 - omega of the weight and the packet
+      // scatters; a light packet plays the roulette on r1. Launches without
+      // implicit sets compile this out.
+      const bool absorb = ev && !surf && (r.y >> 8) >= (IMPL ? sd.absorb_gate : sd.omega_q);
+      unsigned fate = esc ? 1u : 0u;
+      if (!IMPL) {
+        st_wabs += absorb ? W : 0ull;
+        fate = absorb ? 2u : fate;
+      } else if (absorb) {
+        if (!sd.implicit) {
+          st_wabs += W;
+          fate = 2;
+        } else {
+          const unsigned long long Wn = (W * sd.omega_q + (1ull << 23)) >> 24;
+          st_wabs += W - Wn;
           W = Wn;
-        } else if ((r.y >> 8) >= (IMPL ? sd.absorb_gate : sd.omega_q)) {
-          // analog: Eq. 11 absorbs (the gate is omega_q). Implicit capture
-          // (gate 0, always here): the particle absorbs 1 - omega of the
-          // weight and the packet scatters; a light packet plays the roulette
-          // on r1. Launches without implicit sets compile this out.
-          if (!IMPL || !sd.implicit) {
-            st_wabs += W;
-            fate = 2;
-          } else {
-            const unsigned long long Wn = (W * sd.omega_q + (1ull << 23)) >> 24;
-            st_wabs += W - Wn;
-            W = Wn;
-            if (Wn < PDV_ROULETTE_W) {
-              if (Wn != 0 && (r.y >> 8) < PDV_ROULETTE_Q) {
-                atomicAdd(&s_cnt[C_W_RR_GAINED], (PDV_ROULETTE_M - 1) * Wn);
-                W = Wn * PDV_ROULETTE_M;
-              } else {
-                atomicAdd(&s_cnt[C_W_RR_DROPPED], Wn);
-                fate = 5;
-              }
-            }
-          }
-        }
-        if (fate == 0) {
-          // New direction. Particle scattering (Eq. 13-17): polar angle from the
-          // phase CDF, azimuth uniform (Eq. 15). Free surface (diffuse): polar
-          // angle uniform in [0, pi/2) from +z, azimuth uniform. Both are a
-          // (polar, azimuth) pair in units of pi followed by the same rotation.
-          float tpi;
-          unsigned rphi;
-          if (surf) {
-            tpi = 0.5f * u23f(r.y);
-            rphi = r.z;
-          } else {
-            const unsigned m2 = r.z >> 8;
-            const int i = search_phase(tb.Cq, tb.Gp, m2);
-            const unsigned c0 = tb.Cq[i];
-            if (sd.phase_uniform) {
-              // theta_i / pi = i / (n_p - 1); linear inside the CDF bin
-              const float frac = ((float)(m2 - c0) + 0.5f) * rcp_approx((float)(tb.Cq[i + 1] - c0));
-              tpi = ((float)i + frac) * sd.inv_nm1;
+          if (Wn < PDV_ROULETTE_W) {
+            if (Wn != 0 && (r.y >> 8) < PDV_ROULETTE_Q) {
+              atomicAdd(&s_cnt[C_W_RR_GAINED], (PDV_ROULETTE_M - 1) * Wn);
+              W = Wn * PDV_ROULETTE_M;
             } else {
-              tpi = fmaf((float)(m2 - c0) + 0.5f, tb.dthpi[i], tb.thpi[i]);
+              atomicAdd(&s_cnt[C_W_RR_DROPPED], Wn);
+              fate = 5;
             }
-            rphi = r.w;
-            ++st_scat;
-            if (DUMP) ++nsca;
           }
-          float st, ct, sp, cp;
-          sincospi_half_turns(tpi, &st, &ct);
-          sincospi_half_turns(2.0f * u23f(rphi), &sp, &cp);              // azimuth, Eq. 15
-          if (surf && sd.surface_mode == PDV_SURFACE_LAMBERT) {
-            const float a = u23f(r.y);
-            ct = sqrtf(a);
-            st = sqrtf(1.0f - a);
-          }
-          float nx, ny, nz;
-          if (surf || fabsf(uz) > 1.0f - 1e-6f) {
-            // Eq. 17 (and the wall's frame): cos(theta) along the sign of u_z
-            nx = st * cp;
-            ny = st * sp;
-            nz = (surf || uz >= 0.0f) ? ct : -ct;
-          } else {
-            // Eq. 16 in its standard form
-            const float h2 = fmaf(ux, ux, uy * uy);
-            const float rs = rsqrtf(h2);
-            const float s = h2 * rs;
-            const float a = st * rs;
-            nx = fmaf(a, fmaf(ux * uz, cp, -uy * sp), ux * ct);
-            ny = fmaf(a, fmaf(uy * uz, cp, ux * sp), uy * ct);
-            nz = fmaf(-st * cp, s, uz * ct);
-          }
-          if (surf && sd.surface_mode == PDV_SURFACE_SPECULAR) {
-            nx = ux; ny = uy; nz = -uz;
-          } else {
-            const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
-            nx *= inv_n; ny *= inv_n; nz *= inv_n;
-          }
-          // Eq. 4 / Eq. 18: the moving scatterer (or wall) shifts the frequency
-          // (a rounded product: no FMA contraction into the compensated sum,
-          // so every instantiation of this kernel computes the same bits)
-          kahan_add(vapp, vcomp, __fmul_rn(0.5f * (nz - uz), vn));
-          ux = nx; uy = ny; uz = nz;
-          iuz = rcp_approx(nz);
-          if (W == 0) fate = 3;      // the surface absorbed all of the weight
         }
       }
-      if (fate == 0 && nev == 0u) {
+
+      // ---- new direction. Particle scattering (Eq. 13-17): polar angle from
+      // the phase CDF, azimuth uniform (Eq. 15). Free surface (diffuse): polar
+      // angle uniform in [0, pi/2) from +z, azimuth uniform. Both are a
+      // (polar, azimuth) pair in units of pi followed by the same rotation.
+      const bool scat = ev && fate == 0;
+      const bool part = scat && !surf;
+      float tpi;
+      {
+        const unsigned m2 = r.z >> 8;
+        const unsigned c = m2 >> (24 - kGuidePhaseLog);
+        int lo = tb.Gp[c], hi = part ? (int)tb.Gp[c + 1] : lo;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (tb.Cq[mid] <= m2) lo = mid; else hi = mid - 1;
+        }
+        const unsigned c0 = tb.Cq[lo];
+        float tp;
+        if (sd.phase_uniform) {
+          // theta_i / pi = i / (n_p - 1); linear inside the CDF bin
+          const float frac = ((float)(m2 - c0) + 0.5f) * rcp_approx((float)(tb.Cq[lo + 1] - c0));
+          tp = ((float)lo + frac) * sd.inv_nm1;
+        } else {
+          tp = fmaf((float)(m2 - c0) + 0.5f, tb.dthpi[lo], tb.thpi[lo]);
+        }
+        tpi = surf ? 0.5f * u23f(r.y) : tp;
+      }
+      float st, ct, sp, cp;
+      sincospi_half_turns(tpi, &st, &ct);
+      sincospi_half_turns(2.0f * u23f(surf ? r.z : r.w), &sp, &cp);   // azimuth, Eq. 15
+      if (sd.surface_mode == PDV_SURFACE_LAMBERT) {
+        const float a = u23f(r.y);
+        ct = surf ? sqrtf(a) : ct;
+        st = surf ? sqrtf(1.0f - a) : st;
+      }
+      // Eq. 16 in its standard form, with the horizontal norm from (u_x, u_y);
+      // Eq. 17 (and the wall's frame) when the direction is vertical (its
+      // horizontal part below 1e-15): cos(theta) along the sign of u_z
+      const float h2 = fmaf(ux, ux, uy * uy);
+      const bool vert = surf || h2 < 1e-30f;
+      const float rs = rsqrtf(h2);
+      const float sh = h2 * rs;
+      const float ah = st * rs;
+      float nx = fmaf(ah, fmaf(ux * uz, cp, -uy * sp), ux * ct);
+      float ny = fmaf(ah, fmaf(uy * uz, cp, ux * sp), uy * ct);
+      float nz = fmaf(-st * cp, sh, uz * ct);
+      nx = vert ? st * cp : nx;
+      ny = vert ? st * sp : ny;
+      nz = vert ? ((surf || uz >= 0.0f) ? ct : -ct) : nz;
+      const bool spec = surf && sd.surface_mode == PDV_SURFACE_SPECULAR;
+      const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+      nx = spec ? ux : nx * inv_n;
+      ny = spec ? uy : ny * inv_n;
+      nz = spec ? -uz : nz * inv_n;
+      if (scat) {
+        // Eq. 4 / Eq. 18: the moving scatterer (or wall) shifts the frequency
+        // (a rounded product: no FMA contraction into the compensated sum,
+        // so every instantiation of this kernel computes the same bits)
+        kahan_add(vapp, vcomp, __fmul_rn(0.5f * (nz - uz), vn));
+        ux = nx; uy = ny; uz = nz;
+        iuz = rcp_approx(nz);
+      }
+      st_scat += part ? 1u : 0u;
+      if (DUMP) nsca += part ? 1u : 0u;
+      fate = (scat && W == 0) ? 3u : fate;     // the surface absorbed all of the weight
+      if (fate == 0 && ev && nev == 0u) {
         atomicAdd(&s_cnt[C_W_TRUNCATED], W);
         atomicAdd(&s_cnt[C_TRUNCATED], 1ull);
         fate = 4;
@@ -530,7 +540,7 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
     // ---- flush this set's tallies
     {
       unsigned a = st_launch, b = st_events, c = st_scat, d = st_surf, e = st_esc;
-      unsigned long long we = st_wesc, wa = st_wabs;
+      unsigned long long we = st_wesc, wa = st_wabs, ws = st_wsurf;
       for (int o = 16; o; o >>= 1) {
         a += __shfl_xor_sync(kFull, a, o);
         b += __shfl_xor_sync(kFull, b, o);
@@ -539,6 +549,7 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
         e += __shfl_xor_sync(kFull, e, o);
         we += __shfl_xor_sync(kFull, we, o);
         wa += __shfl_xor_sync(kFull, wa, o);
+        ws += __shfl_xor_sync(kFull, ws, o);
       }
       if (lane == 0) {
         atomicAdd(&s_cnt[C_LAUNCHED], (unsigned long long)a);
@@ -548,6 +559,7 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
         atomicAdd(&s_cnt[C_ESCAPES], (unsigned long long)e);
         atomicAdd(&s_cnt[C_W_ESCAPED], we);
         atomicAdd(&s_cnt[C_W_ABS_PARTICLE], wa);
+        atomicAdd(&s_cnt[C_W_ABS_SURFACE], ws);
       }
     }
     __syncthreads();
@@ -575,6 +587,21 @@ static const void* f32_kernel(int hist_mode, bool dump, bool impl) {
   return impl ? f32_kernel_impl<true>(hist_mode, dump) : f32_kernel_impl<false>(hist_mode, dump);
 }
 
+__global__ void k_normalise(const SetDesc* __restrict__ sets, double* const* spec,
+                            pdv_counters* const* cnt_out, unsigned long long* const* raw,
+                            const unsigned* flags);
+
+cudaError_t transport_preload() {
+  cudaFuncAttributes a;
+  for (int impl = 0; impl < 2; ++impl)
+    for (int dump = 0; dump < 2; ++dump)
+      for (int hm = 1; hm <= 2; ++hm) {
+        const cudaError_t e = cudaFuncGetAttributes(&a, f32_kernel(hm, dump != 0, impl != 0));
+        if (e != cudaSuccess) return e;
+      }
+  return cudaFuncGetAttributes(&a, (const void*)k_normalise);
+}
+
 int transport_f32_max_smem() {
   int dev = 0, v = 0;
   cudaGetDevice(&dev);
@@ -592,10 +619,11 @@ cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool 
 
 void launch_transport_f32(const SetDesc* d_sets, int n_sets, unsigned long long* d_set_ctr,
                           int grid, int block, size_t smem, int hist_mode, bool dump, bool impl,
-                          cudaStream_t st) {
+                          unsigned chunk, cudaStream_t st) {
   const void* k = f32_kernel(hist_mode, dump, impl);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  void* args[] = {(void*)&d_sets, (void*)&n_sets, (void*)&d_set_ctr};
+  if (chunk == 0) chunk = kChunkDefault;
+  void* args[] = {(void*)&d_sets, (void*)&n_sets, (void*)&d_set_ctr, (void*)&chunk};
   cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, st);
 }
 
@@ -626,6 +654,10 @@ __global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict
     const double psi = 2.0 * pi * u23d(r.y);
     const double x0 = rad * cos(psi), y0 = rad * sin(psi);
     double ux = 0.0, uy = 0.0, uz = -1.0;
+    if (sd.launch_horizontal) {          // test hook: the horizontal-flight rule
+      ux = 1.0;
+      uz = 0.0;
+    }
     double S = 1.0, vcur = sd.v_top, Xx = 0.0, Xy = 0.0, vapp = 0.0;
     unsigned long long W = 1ull << 32, dmask = 0;
     unsigned nev = 0, nsca = 0, nsurf = 0, fate = 0;
@@ -744,10 +776,11 @@ __global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict
           const double ph = 2.0 * pi * u23d(r.w);
           const double ct = cos(th), st = sin(th), cp = cos(ph), sp = sin(ph);
           double nx, ny, nz;
-          if (fabs(uz) > 1.0 - 1e-6) {
+          const double h2 = ux * ux + uy * uy;
+          if (h2 < 1e-30) {                      // Eq. 17: vertical
             nx = st * cp; ny = st * sp; nz = uz >= 0.0 ? ct : -ct;
-          } else {
-            const double s = sqrt(1.0 - uz * uz);
+          } else {                               // Eq. 16, horizontal norm from (u_x, u_y)
+            const double s = sqrt(h2);
             nx = st * (ux * uz * cp - uy * sp) / s + ux * ct;
             ny = st * (uy * uz * cp + ux * sp) / s + uy * ct;
             nz = -st * cp * s + uz * ct;

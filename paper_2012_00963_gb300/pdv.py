@@ -25,6 +25,7 @@ from . import build as _build
 PDV_OK, PDV_EINVAL, PDV_ENOMEM, PDV_ECUDA, PDV_EAGAIN = 0, -1, -2, -3, -4
 PDV_ENOTREADY, PDV_ETIMEOUT, PDV_ECANCELLED = -5, -6, -7
 PDV_OUT_DEVICE, PDV_PER_DV, PDV_IN_DEVICE, PDV_IMPLICIT_CAPTURE = 0x1, 0x2, 0x4, 0x8
+PDV_TEST_HORIZONTAL_LAUNCH = 0x10
 PDV_PEAK_OK, PDV_PEAK_NO_PEAK, PDV_PEAK_NOT_MAX, PDV_PEAK_EDGE = 0, 1, 2, 3
 PDV_PREC_FP32, PDV_PREC_FP64 = 0, 1
 STATUS_NAMES = {0: "PDV_OK", -1: "PDV_EINVAL", -2: "PDV_ENOMEM", -3: "PDV_ECUDA",
@@ -39,7 +40,8 @@ ABI_FUNCTIONS = [
     "pdv_create_cloud", "pdv_set_phase_table", "pdv_cloud_get_info", "pdv_destroy_cloud",
     "pdv_phase_hg", "pdv_mie_table", "pdv_simulate_spectrum", "pdv_simulate_batch",
     "pdv_autotune", "pdv_submit", "pdv_poll", "pdv_cancel", "pdv_simulate_spectrum_static",
-    "pdv_ss_spectrum", "pdv_extract_peaks", "pdv_measure_issue_rate",
+    "pdv_ss_spectrum", "pdv_extract_peaks", "pdv_measure_issue_rate", "pdv_set_serving_limits",
+    "pdv_set_autotune_cache",
 ]
 
 
@@ -169,6 +171,8 @@ def lib():
                 "pdv_submit": ([vp, C.POINTER(pdv_request), C.POINTER(C.c_uint64)], ip),
                 "pdv_poll": ([vp, C.c_uint64, C.c_uint32], ip),
                 "pdv_cancel": ([vp, C.c_uint64], ip),
+                "pdv_set_serving_limits": ([vp, ip, C.c_uint64], ip),
+                "pdv_set_autotune_cache": ([vp, C.c_char_p], ip),
                 "pdv_ss_spectrum": ([vp, vp, ip, ip, C.c_double, C.c_double, C.c_uint32, vp], ip),
                 "pdv_extract_peaks": ([vp, vp, ip, ip, C.c_double, C.c_double, C.c_double,
                                        C.POINTER(pdv_peak_opts), C.c_uint32, vp], ip),
@@ -198,10 +202,19 @@ def _dp(a):
 
 
 # ------------------------------------------------------------------ ABI (same names)
-def pdv_ctx_create(device: int = 0, stream: Optional[int] = None) -> int:
+def pdv_ctx_create(device: int = 0, stream: Optional[int] = None,
+                   allocator: Optional[pdv_allocator] = None) -> int:
+    """``allocator``: a pdv_allocator whose callbacks the caller keeps alive
+    for the context's lifetime (None: the context's own memory pool)."""
     h = C.c_void_p()
-    _check(lib().pdv_ctx_create(device, C.c_void_p(stream or 0), None, C.byref(h)))
+    _check(lib().pdv_ctx_create(device, C.c_void_p(stream or 0),
+                                C.c_void_p(C.addressof(allocator)) if allocator is not None else None,
+                                C.byref(h)))
     return h.value
+
+
+def pdv_set_serving_limits(ctx: int, max_requests: int, reserve_bytes: int):
+    _check(lib().pdv_set_serving_limits(C.c_void_p(ctx), int(max_requests), int(reserve_bytes)))
 
 
 def pdv_ctx_destroy(ctx: int):
@@ -276,6 +289,10 @@ def pdv_simulate_spectrum_static(ctx: int, req: pdv_request):
 def pdv_simulate_batch(ctx: int, reqs: Sequence[pdv_request]):
     arr = (pdv_request * len(reqs))(*reqs)
     _check(lib().pdv_simulate_batch(C.c_void_p(ctx), arr, len(reqs)))
+
+
+def pdv_set_autotune_cache(ctx: int, path: Optional[str]):
+    _check(lib().pdv_set_autotune_cache(C.c_void_p(ctx), path.encode() if path else None))
 
 
 def pdv_autotune(ctx: int, reqs: Sequence[pdv_request]) -> dict:
@@ -381,8 +398,10 @@ def extract_peaks(ctx: "Context", spectra, v_lo: float, v_hi: float, v_fs: float
 class Context:
     """A libpdv context on one device (``stream``: a cudaStream_t as int)."""
 
-    def __init__(self, device: int = 0, stream: Optional[int] = None):
-        self.handle = pdv_ctx_create(device, stream)
+    def __init__(self, device: int = 0, stream: Optional[int] = None,
+                 allocator: Optional[pdv_allocator] = None):
+        self.allocator = allocator          # its callbacks must outlive the context
+        self.handle = pdv_ctx_create(device, stream, allocator)
 
     def close(self):
         if self.handle:
@@ -491,6 +510,8 @@ class Request:
         r.flags = PDV_PER_DV if per_dv else 0
         if getattr(wl, "implicit_capture", False):
             r.flags |= PDV_IMPLICIT_CAPTURE
+        if getattr(wl, "horizontal_launch", False):
+            r.flags |= PDV_TEST_HORIZONTAL_LAUNCH
         ns, nb = r.n_snap, r.n_bins
         self.device_out = device_out
         if device_out is not None:

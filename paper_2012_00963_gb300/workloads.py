@@ -85,6 +85,7 @@ class Workload:
     max_events: int = 1_000_000       # with layer stepping: the step limit
     n_layers: int = 0                 # 0 exact free paths; > 0 the paper's H / n_layers steps
     implicit_capture: bool = False    # weight omega per interaction + Russian roulette (exact paths)
+    horizontal_launch: bool = False   # test hook: packets start along +x (the |u_z| < 1e-9 rule)
     precision: str = "fp32"           # "fp32" | "fp64"
     name: str = "custom"
 
