@@ -74,17 +74,26 @@ def surrogate_estimate(records, min_packets=1_000_000, keep=0.4, min_points=12):
 def run_sweep(ctx: pdv.Context, target_hist, target_packets, probe: dict, duration: float = 60.0,
               rate: float = 200.0, seed: int = 5, n_min: float = 1e5, n_max: float = 1e7,
               explore: float = 0.2, poll_us: int = 200,
-              min_best_packets: int = 1_000_000) -> SweepResult:
+              min_best_packets: int = 1_000_000, lag: int = 20) -> SweepResult:
+    """Submit the Poisson stream of candidates and score them as they finish.
+    The candidate proposed at arrival k is computed only from the results of
+    arrivals 0 .. k - lag, taken in arrival order, so the candidate sequence
+    and the recovered parameters do not depend on the order in which requests
+    complete (at 200 requests/s a lag of 20 is 0.1 s, far above the serving
+    latency, so the submitter almost never waits for it)."""
     arrivals = W.cfg5_arrivals(rate=rate, duration=duration, seed=seed, n_min=n_min,
                                n_max=n_max)
     rng = np.random.default_rng(seed + 1)
     res = SweepResult()
     lock = threading.Lock()
-    pending = {}            # ticket -> (request, cloud, t_submit, params)
-    best = {"chi2": math.inf}
+    pending = {}            # ticket -> (request, cloud, t_submit, params, arrival index)
+    done = {}               # arrival index -> record (None: no scored bins)
     target = np.asarray(target_hist, np.float64)
     done_submitting = threading.Event()
     surrogate_center = {}
+    best = {"chi2": math.inf}
+    folded = 0              # arrivals 0 .. folded - 1 are folded into `best` and `prefix`
+    prefix = []             # their records, in arrival order
 
     def poller():
         while True:
@@ -95,7 +104,7 @@ def run_sweep(ctx: pdv.Context, target_hist, target_packets, probe: dict, durati
                     return
                 time.sleep(0.0002)
                 continue
-            for t, (req, cloud, t0, params) in items:
+            for t, (req, cloud, t0, params, k) in items:
                 st = pdv.pdv_poll(ctx.handle, t, poll_us // max(len(items), 1))
                 if st != pdv.PDV_OK:
                     continue
@@ -103,17 +112,13 @@ def run_sweep(ctx: pdv.Context, target_hist, target_packets, probe: dict, durati
                 h = req.raw[0, 1:-1].astype(np.float64) / 2.0**32
                 c2, dof = chi2(h, req.c.n_packets, target, target_packets)
                 tau0 = cloud.info()["tau_tot"]
+                rec = (dict(beta=params["beta"], tau0=tau0, m0=params["m0"], d_m=params["d_m"],
+                            chi2=c2 / dof, n=int(req.c.n_packets)) if dof else None)
                 with lock:
                     del pending[t]
                     res.latencies_ms.append(1e3 * (t1 - t0))
                     res.completed += 1
-                    if dof:
-                        res.records.append(dict(beta=params["beta"], tau0=tau0, m0=params["m0"],
-                                                d_m=params["d_m"], chi2=c2 / dof,
-                                                n=int(req.c.n_packets)))
-                    # only well-sampled candidates can become the best fit
-                    if dof and req.c.n_packets >= min_best_packets and c2 / dof < best["chi2"]:
-                        best.update(chi2=c2 / dof, tau0=tau0, **params)
+                    done[k] = rec
 
     th = threading.Thread(target=poller, daemon=True)
     th.start()
@@ -123,12 +128,28 @@ def run_sweep(ctx: pdv.Context, target_hist, target_packets, probe: dict, durati
         now = time.perf_counter() - t_start
         if a.t > now:
             time.sleep(a.t - now)
-        with lock:
-            have_best = math.isfinite(best["chi2"])
-            b = dict(best)
-            recs = list(res.records) if k % 50 == 0 else None
-        if recs is not None and have_best:
-            sur = surrogate_estimate(recs)
+        # fold the results of arrivals up to k - lag, in arrival order
+        need = k - lag + 1
+        t_wait = time.perf_counter()
+        while True:
+            with lock:
+                while folded < need and folded in done:
+                    rec = done[folded]
+                    if rec is not None:
+                        prefix.append(rec)
+                        # only well-sampled candidates can become the best fit
+                        if rec["n"] >= min_best_packets and rec["chi2"] < best["chi2"]:
+                            best.update(chi2=rec["chi2"], tau0=rec["tau0"], beta=rec["beta"],
+                                        m0=rec["m0"], d_m=rec["d_m"])
+                    folded += 1
+                ready = folded >= need
+            if ready or time.perf_counter() - t_wait > 30.0:
+                break
+            time.sleep(0.0002)
+        have_best = math.isfinite(best["chi2"])
+        b = dict(best)
+        if k % 50 == 0 and have_best:
+            sur = surrogate_estimate(prefix)
             if sur is not None:
                 # move the proposal centre to the surrogate's vertex, keeping m0/d
                 # on the line that gives its tau0 (tau0 is linear in m0/d)
@@ -162,12 +183,16 @@ def run_sweep(ctx: pdv.Context, target_hist, target_packets, probe: dict, durati
                 res.rejected += 1
                 time.sleep(0.001)
         with lock:
-            pending[ticket] = (req, cloud, t0, params)
+            pending[ticket] = (req, cloud, t0, params, k)
         res.submitted += 1
     done_submitting.set()
     th.join()
     res.wall_s = time.perf_counter() - t_start
-    res.best = best
+    res.records = [done[k] for k in sorted(done) if done[k] is not None]
+    res.best = {"chi2": math.inf}
+    for rec in res.records:
+        if rec["n"] >= min_best_packets and rec["chi2"] < res.best["chi2"]:
+            res.best = dict(rec)
     for c in clouds:
         c.close()
     return res

@@ -10,8 +10,10 @@ Calls only the FP64 oracle (oracle/). Run from the repository root:
   counted as the paper does) with the hidden parameters beta = 6,
   m0 = 3 mg/cm^2, d = 2 um, 1e7 packets (seed 77).
 * precision_cfg3.npz — the heavy multiple-scattering cloud (20 mg/cm^2 of
-  1 um tin, beta = 3, Mie m = 3 + 9i) at 1e7 packets (seed 3): the reference
-  for the per-bin error of the GPU paths.
+  1 um tin, beta = 3, Mie m = 3 + 9i) at 1e7 packets: the reference for the
+  per-bin error of the GPU paths. It draws seed 303, so its packets are
+  independent of the GPU runs' (seed 3) and the comparison is between two
+  independent Monte Carlo samples.
 """
 import math
 import os
@@ -36,15 +38,18 @@ def serving_workload(beta, m0, d_m, n_packets, seed):
     return W.cfg5_request(a, **SERVING_PROBE)
 
 
-def precision_workload(n_packets):
-    return W.cfg3(n_packets=n_packets, r_ap=3.0 * W.MM, cone_alpha=0.5)
+PRECISION_SEED = 303
+
+
+def precision_workload(n_packets, seed=PRECISION_SEED):
+    return W.cfg3(n_packets=n_packets, r_ap=3.0 * W.MM, cone_alpha=0.5, seed=seed)
 
 
 def save(name, wl, res, seconds):
     np.savez_compressed(
         os.path.join(HERE, name), hist=res["hist"], counters=res["counters"],
         n_packets=wl.n_packets, v_lo=wl.v_lo, v_hi=wl.v_hi, n_bins=wl.n_bins,
-        tau_tot=res["tau_tot"], seconds=seconds,
+        tau_tot=res["tau_tot"], seconds=seconds, seed=wl.seed,
         note="FP64 oracle (oracle/pdv_oracle.c) written by tests/golden/make_golden.py")
 
 

@@ -32,3 +32,38 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_reference_and_gpu_arms_share_the_config():
+    """Both arms describe the workload with the same dict (workload_config)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import argparse
+    ns = argparse.Namespace(packets=1e8, snapshots=50)
+    wl = bench.workload(ns)
+    a, b = bench.workload_config(wl, 1), bench.workload_config(wl, 1)
+    assert a == b and "l2" in a and a["snapshots"] == 50
+
+
+def test_merged_bin_test_statistic():
+    """The low-count two-sample test of the precision leg: identical
+    histograms give chi^2 = 0; two Poisson samples of one spectrum give chi^2
+    per group near 1 and no 5-sigma group; a 30 % excess in one region is
+    found."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    rng = np.random.default_rng(3)
+    rate = np.exp(-np.linspace(0, 6, 600)) * 40.0
+    a = rng.poisson(rate).astype(float)
+    b = rng.poisson(rate * 2).astype(float)              # twice the packets
+    same = bench.merged_bin_test(a, 1e6, a, 1e6)
+    assert same["chi2_per_group"] == 0.0 and same["max_abs_z"] == 0.0
+    r = bench.merged_bin_test(a, 1e6, b, 2e6)
+    assert 0.6 < r["chi2_per_group"] < 1.5 and r["pass_5sigma"], r
+    assert r["groups"] > 50
+    c = b.copy()
+    c[:100] *= 1.3
+    bad = bench.merged_bin_test(a, 1e6, rng.poisson(c).astype(float), 2e6)
+    assert bad["chi2_per_group"] > 2.0 * r["chi2_per_group"], bad
+    assert bad["max_abs_z"] > bad["bonferroni_z_1e-3"] > r["max_abs_z"], bad
