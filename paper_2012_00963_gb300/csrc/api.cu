@@ -162,6 +162,7 @@ struct pdv_cloud {
   bool has_phase = false;
   CloudTables t;
   float* pn = nullptr;                // p(theta) / max p at the phase nodes (layer stepping)
+  double max_dtheta = 0;              // largest spacing of the phase table's angles
   void* mass_arena = nullptr;
   void* phase_arena = nullptr;
 };
@@ -459,6 +460,7 @@ extern "C" pdv_status pdv_set_phase_table(pdv_cloud* cl, int n, const double* th
   const size_t oCq = L.add(sizeof(unsigned) * n);
   const size_t oth = L.add(sizeof(float) * n);
   const size_t odt = L.add(sizeof(float) * n);
+  const size_t ocs = L.add(sizeof(float2) * n);
   const size_t othd = L.add(sizeof(double) * n);
   const size_t oGp = L.add(sizeof(unsigned short) * ngp);
   const size_t oin = L.add(sizeof(double) * 2 * n);
@@ -477,6 +479,7 @@ extern "C" pdv_status pdv_set_phase_table(pdv_cloud* cl, int n, const double* th
   cl->t.Cq = (unsigned*)(base + oCq);
   cl->t.thpi = (float*)(base + oth);
   cl->t.dthpi = (float*)(base + odt);
+  cl->t.cs = (float2*)(base + ocs);
   cl->t.th_d = (double*)(base + othd);
   cl->t.Gp = (unsigned short*)(base + oGp);
   cl->t.n_p = n;
@@ -489,6 +492,15 @@ extern "C" pdv_status pdv_set_phase_table(pdv_cloud* cl, int n, const double* th
     e = cudaMemcpyAsync(din + n, p, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(cl->pn, pn.data(), sizeof(float) * n, cudaMemcpyHostToDevice, c->stream);
+  // (cos theta_i, sin theta_i) of the nodes: the FP32 walk's angle tables
+  std::vector<float2> cs(n);
+  cl->max_dtheta = 0;
+  for (int i = 0; i < n; ++i) {
+    cs[i] = make_float2((float)std::cos(theta[i]), (float)std::sin(theta[i]));
+    if (i) cl->max_dtheta = std::max(cl->max_dtheta, theta[i] - theta[i - 1]);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cl->t.cs, cs.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = build_phase_cdf(din, din + n, n, dwk, &cl->t, dg, c->stream);
   c->launches += 6;
   double g = 0.0;
@@ -641,9 +653,12 @@ static SetDesc make_set(const pdv_request* r) {
   memset(&d, 0, sizeof d);
   d.Sq = cl->t.Sq; d.Sd = cl->t.Sd; d.w = cl->t.w; d.G = cl->t.G;
   d.Cq = cl->t.Cq; d.thpi = cl->t.thpi; d.dthpi = cl->t.dthpi; d.th_d = cl->t.th_d; d.Gp = cl->t.Gp;
+  d.cs = cl->t.cs;
   d.n_v = cl->t.n_v; d.n_g = cl->t.n_g; d.g_shift = cl->t.g_shift; d.n_p = cl->t.n_p;
   d.phase_uniform = cl->t.phase_uniform;
   d.inv_nm1 = (float)(1.0 / (double)(cl->t.n_p - 1));
+  d.dth_f = (float)(M_PI / (double)(cl->t.n_p - 1));
+  d.angle_table = cl->max_dtheta <= 3.1e-3 ? 1 : 0;
   d.n_snap = r->n_snap; d.n_bins = r->n_bins;
   d.surface_mode = cl->desc.surface_mode;
   d.cone_all = r->probe.cone_half_angle_rad >= 0.5 * M_PI;
@@ -684,6 +699,13 @@ static SetDesc make_set(const pdv_request* r) {
     d.eps_f = (float)std::exp(-x);
     d.lg_c_f = (float)(cl->desc.v_fs * M_LN2 / cl->desc.beta);
     d.dvds_c_f = (float)(cl->desc.v_fs * -std::expm1(-x) / cl->desc.beta);
+    d.vb_d = cl->desc.v_fs / cl->desc.beta;
+    d.E_d = -std::expm1(-x);
+  }
+  // Philox round keys: the key after i Weyl increments (Salmon et al.), mod 2^32
+  for (unsigned i = 0; i < 10; ++i) {
+    d.rk[i].x = (unsigned)((uint32_t)r->seed + i * 0x9E3779B9u);
+    d.rk[i].y = (unsigned)((uint32_t)(r->seed >> 32) + i * 0xBB67AE85u);
   }
   return d;
 }
@@ -757,10 +779,10 @@ static int pick_hist_mode(const pdv_ctx* c, const SetDesc& d) {
 
 // Launch geometry of the persistent FP32 kernel for given shared memory.
 static pdv_status f32_geometry(pdv_ctx* c, size_t smem, int hist_mode, bool dump, bool impl,
-                               int* grid, int* block) {
+                               int* grid, int* block, bool one = false) {
   const int bt = c->tuning.block_threads ? c->tuning.block_threads : 256;
   int occ = 0;
-  CK(transport_f32_occupancy(bt, smem, hist_mode, dump, impl, &occ));
+  CK(transport_f32_occupancy(bt, smem, hist_mode, dump, impl, one, &occ));
   if (occ < 1) return fail(PDV_EINVAL, "tables need %zu bytes of shared memory, too many for one block", smem);
   int bps = c->tuning.blocks_per_sm ? std::min(c->tuning.blocks_per_sm, occ) : occ;
   *grid = c->sm_count * bps;
@@ -823,11 +845,10 @@ static pdv_status enqueue_transport(pdv_ctx* c, const pdv_request* r, const SetD
     if (smem > (size_t)c->max_smem) return fail(PDV_EINVAL, "tables need %zu bytes of shared memory (max %d)", smem, c->max_smem);
     int grid = 0, block = 0;
     const bool impl = d.implicit != 0;
-    pdv_status s = f32_geometry(c, smem, hm, dump, impl, &grid, &block);
+    pdv_status s = f32_geometry(c, smem, hm, dump, impl, &grid, &block, true);
     if (s != PDV_OK) return s;
-    launch_transport_f32((const SetDesc*)(base + b.o_set), 1,
-                         (unsigned long long*)(base + b.o_ctr), grid, block, smem, hm, dump, impl,
-                         (unsigned)c->tuning.tile_packets, st);
+    launch_transport_f32_one(d, (unsigned long long*)(base + b.o_ctr), grid, block, smem, hm, dump,
+                             impl, (unsigned)c->tuning.tile_packets, st);
     c->last_grid = grid;
     c->last_block = block;
   } else {
@@ -1791,10 +1812,10 @@ extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request
   if (smem > (size_t)c->max_smem) return fail(PDV_EINVAL, "tables need %zu bytes of shared memory", smem);
   int grid = 0, block = 0;
   const bool impl = d.implicit != 0;
-  s = f32_geometry(c, smem, hm, dump, impl, &grid, &block);
+  s = f32_geometry(c, smem, hm, dump, impl, &grid, &block, true);
   if (s != PDV_OK) return s;
-  launch_transport_f32((const SetDesc*)(base + o_set), 1, (unsigned long long*)(base + o_ctr),
-                       grid, block, smem, hm, dump, impl, (unsigned)c->tuning.tile_packets, st);
+  launch_transport_f32_one(d, (unsigned long long*)(base + o_ctr), grid, block, smem, hm, dump, impl,
+                           (unsigned)c->tuning.tile_packets, st);
   launch_normalise((const SetDesc*)(base + o_set), 1, (double* const*)(base + o_ptr),
                    (pdv_counters* const*)(base + o_ptr + sizeof(void*)),
                    (unsigned long long* const*)(base + o_ptr + 2 * sizeof(void*)),

@@ -60,6 +60,7 @@ struct CloudTables {
   float* thpi = nullptr;              // [n_p] theta / pi (f32)
   float* dthpi = nullptr;             // [n_p] (theta_{i+1} - theta_i) / pi / (Cq_{i+1} - Cq_i)
   double* th_d = nullptr;             // [n_p] theta (FP64 path)
+  float2* cs = nullptr;               // [n_p] (cos theta_i, sin theta_i), FP64 rounded to FP32
   unsigned short* Gp = nullptr;       // [n_gp + 1] guide over the 2^24 CDF
   int n_p = 0;
   int phase_uniform = 0;              // theta grid uniform over [0, pi]
@@ -75,6 +76,7 @@ struct SetDesc {
   const float* thpi;
   const float* dthpi;
   const double* th_d;
+  const float2* cs;                   // [n_p] (cos theta_i, sin theta_i)
   const unsigned short* Gp;
   const double* t_snap;               // [3 n_snap]: seconds in request order, ascending, index
   unsigned long long* hist;           // [n_snap][n_bins + 3]
@@ -94,8 +96,12 @@ struct SetDesc {
   double z_probe, r_beam, r_ap2, cos_alpha, v_lo, inv_dbin;
   float inv_tau_f, v_bot_f, dv_f, v_top_f, v_fs_f, z_probe_f, r_beam_f, r_ap2_f;
   float cos_alpha_f, v_lo_f, inv_dbin_f, inv_nm1;      // 1 / (n_p - 1)
+  float dth_f;                        // pi / (n_p - 1): a uniform grid's step in theta
+  int angle_table;                    // node spacing <= 3.1e-3: sin/cos from the node table
   // exponential law: v(S) = v_fs - lg_c log2((1 - S) + S eps), dv/dS = dvds_c / ((1 - S) + S eps)
   float lg_c_f, eps_f, dvds_c_f;      // v_fs ln2 / beta, exp(-beta (v_top/v_fs - 1)), v_fs E / beta
+  double vb_d, E_d;                   // FP64 path: v_fs / beta and E = 1 - exp(-beta (v_top/v_fs - 1))
+  uint2 rk[10];                       // Philox round keys of the seed (philox_round_key)
 };
 
 // ------------------------------------------------------------- Philox4x32-10
@@ -197,6 +203,11 @@ __device__ __forceinline__ float u64_to_f(unsigned long long d) {
 void launch_transport_f32(const SetDesc* d_sets, int n_sets, unsigned long long* d_set_ctr,
                           int grid, int block, size_t smem, int hist_mode, bool dump, bool impl,
                           unsigned chunk, cudaStream_t st);
+// One set whose descriptor (host copy, device pointers inside) is passed by
+// value as a kernel parameter.
+void launch_transport_f32_one(const SetDesc& sd, unsigned long long* d_ctr, int grid, int block,
+                              size_t smem, int hist_mode, bool dump, bool impl, unsigned chunk,
+                              cudaStream_t st);
 void launch_transport_f64(const SetDesc* d_set, int grid, int block, cudaStream_t st);
 void launch_normalise(const SetDesc* d_sets, int n_sets, double* const* d_spec,
                       pdv_counters* const* d_cnt_out, unsigned long long* const* d_raw,
@@ -208,7 +219,7 @@ int transport_f32_max_smem();
 // device now (the runtime otherwise loads a kernel at its first launch).
 cudaError_t transport_preload();
 cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, bool impl,
-                                    int* blocks);
+                                    bool one, int* blocks);
 
 cudaError_t build_mass_table(int kind, double beta, double v_fs, double v_bot, double v_top,
                              const double* d_prof_v, const double* d_prof_f, int prof_n,

@@ -53,7 +53,24 @@ struct SmemTables {
   const float* ts;                    // snapshot times, ascending (seconds)
   const unsigned short* perm;         // request index of each ascending time
   unsigned long long* hist;
+  const float2* cs;                   // (cos, sin) of the phase nodes
+  const float2* turn;                 // (cos, sin) of 2 pi j / kTurn, j = 0 .. kTurn - 1
 };
+
+// Angles as a table value and a small remainder: cos(a + d) and sin(a + d)
+// from (cos a, sin a) and cos d = 1 - d^2/2, sin d = d - d^3/6, exact to 2e-12
+// for |d| <= 3.1e-3 (half a step of the kTurn-entry table; a phase-table step
+// of 1800 nodes is 1.7e-3).
+constexpr int kTurnLog = 10, kTurn = 1 << kTurnLog;
+constexpr float kPi2m25f = 9.3626757e-08f;   // pi 2^-25
+constexpr float kPi2m23f = 3.7450703e-07f;   // pi 2^-23
+__device__ __forceinline__ void cos_sin_add(float2 cs, float d, float* c, float* s) {
+  const float d2 = d * d;
+  const float cd = fmaf(d2, -0.5f, 1.0f);
+  const float sd = d * fmaf(d2, -0.16666667f, 1.0f);
+  *c = fmaf(cs.x, cd, -cs.y * sd);
+  *s = fmaf(cs.y, cd, cs.x * sd);
+}
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -80,6 +97,8 @@ __host__ __device__ inline size_t smem_layout(int n_v, int n_g, int n_p, int n_s
   off[6] = o; o = align16(o + sizeof(unsigned short) * ((1 << kGuidePhaseLog) + 1));  // Gp
   off[7] = o; o = align16(o + sizeof(float) * (size_t)n_snap);                    // ts
   off[8] = o; o = align16(o + sizeof(unsigned short) * (size_t)n_snap);           // perm
+  off[10] = o; o = align16(o + sizeof(float2) * (size_t)n_p);                     // cs
+  off[11] = o; o = align16(o + sizeof(float2) * (size_t)kTurn);                   // turn
   off[9] = o;
   if (hist_mode == 2)
     o = align16(o + sizeof(unsigned long long) * (size_t)tally_rows(n_snap, ap_all) * hist_row(n_bins));
@@ -88,7 +107,7 @@ __host__ __device__ inline size_t smem_layout(int n_v, int n_g, int n_p, int n_s
 
 size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode,
                           int phase_uniform, int ap_all, int expo) {
-  size_t off[10];
+  size_t off[12];
   return smem_layout(n_v, n_g, n_p, n_snap, n_bins, hist_mode, phase_uniform, ap_all, expo, off);
 }
 
@@ -140,6 +159,450 @@ __device__ __forceinline__ void launch_position(unsigned long long pk, unsigned 
   y0 = rad * sp;
 }
 
+// Stage one set's tables (and a cleared private histogram) in shared memory.
+template <int HMODE>
+__device__ __forceinline__ SmemTables stage_set(const SetDesc& sd, unsigned char* smem) {
+  size_t off[12];
+  smem_layout(sd.n_v, sd.n_g, sd.n_p, sd.n_snap, sd.n_bins, HMODE, sd.phase_uniform, sd.ap_all,
+              sd.expo, off);
+  SmemTables tb;
+  tb.Sq = reinterpret_cast<const unsigned long long*>(smem + off[0]);
+  tb.w = reinterpret_cast<const float*>(smem + off[1]);
+  tb.G = reinterpret_cast<const unsigned short*>(smem + off[2]);
+  tb.Cq = reinterpret_cast<const unsigned*>(smem + off[3]);
+  tb.thpi = reinterpret_cast<const float*>(smem + off[4]);
+  tb.dthpi = reinterpret_cast<const float*>(smem + off[5]);
+  tb.Gp = reinterpret_cast<const unsigned short*>(smem + off[6]);
+  tb.ts = reinterpret_cast<const float*>(smem + off[7]);
+  tb.perm = reinterpret_cast<const unsigned short*>(smem + off[8]);
+  tb.hist = HMODE == 2 ? reinterpret_cast<unsigned long long*>(smem + off[9]) : sd.hist;
+  tb.cs = reinterpret_cast<const float2*>(smem + off[10]);
+  tb.turn = reinterpret_cast<const float2*>(smem + off[11]);
+  {
+    if (!sd.expo) {
+      unsigned long long* Sq = reinterpret_cast<unsigned long long*>(smem + off[0]);
+      for (int i = threadIdx.x; i <= sd.n_v; i += blockDim.x) Sq[i] = sd.Sq[i];
+      float* w = reinterpret_cast<float*>(smem + off[1]);
+      for (int i = threadIdx.x; i < sd.n_v; i += blockDim.x) w[i] = sd.w[i];
+      unsigned short* G = reinterpret_cast<unsigned short*>(smem + off[2]);
+      for (int i = threadIdx.x; i <= sd.n_g; i += blockDim.x) G[i] = sd.G[i];
+    }
+    unsigned* Cq = reinterpret_cast<unsigned*>(smem + off[3]);
+    float* thpi = reinterpret_cast<float*>(smem + off[4]);
+    float* dthpi = reinterpret_cast<float*>(smem + off[5]);
+    float2* cs = reinterpret_cast<float2*>(smem + off[10]);
+    float2* turn = reinterpret_cast<float2*>(smem + off[11]);
+    for (int j = threadIdx.x; j < kTurn; j += blockDim.x) {
+      float sj, cj;
+      sincospif((float)j * (2.0f / (float)kTurn), &sj, &cj);   // exact argument 2 j / kTurn
+      turn[j] = make_float2(cj, sj);
+    }
+    for (int i = threadIdx.x; i < sd.n_p; i += blockDim.x) {
+      Cq[i] = sd.Cq[i];
+      cs[i] = sd.cs[i];
+      if (!sd.phase_uniform) {
+        thpi[i] = sd.thpi[i];
+        dthpi[i] = sd.dthpi[i];
+      }
+    }
+    unsigned short* Gp = reinterpret_cast<unsigned short*>(smem + off[6]);
+    for (int i = threadIdx.x; i <= (1 << kGuidePhaseLog); i += blockDim.x) Gp[i] = sd.Gp[i];
+    float* ts = reinterpret_cast<float*>(smem + off[7]);
+    unsigned short* perm = reinterpret_cast<unsigned short*>(smem + off[8]);
+    for (int i = threadIdx.x; i < sd.n_snap; i += blockDim.x) {
+      ts[i] = (float)sd.t_snap[sd.n_snap + i];
+      perm[i] = (unsigned short)sd.t_snap[2 * sd.n_snap + i];
+    }
+    if (HMODE == 2) {
+      unsigned long long* h = reinterpret_cast<unsigned long long*>(smem + off[9]);
+      const int nh = tally_rows(sd.n_snap, sd.ap_all) * hist_row(sd.n_bins);
+      for (int i = threadIdx.x; i < nh; i += blockDim.x) h[i] = 0ull;
+    }
+  }
+  __syncthreads();
+  return tb;
+}
+
+// The walks of one set by this block's warps (Section II.B steps (1)-(7)),
+// with the per-set sums added to the block's counters s_cnt.
+template <bool DUMP, int HMODE, bool IMPL>
+__device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb,
+                                         unsigned long long* __restrict__ ctr, unsigned chunk,
+                                         unsigned long long* s_cnt) {
+  const int lane = threadIdx.x & 31;
+  // ---- per-set constants in registers
+  const uint2 key = make_uint2((unsigned)sd.seed, (unsigned)(sd.seed >> 32));
+  const unsigned sid = sd.stream_id;
+  const unsigned long long base_pk = sd.packet_begin;
+  const unsigned n_pk = (unsigned)sd.n_packets;    // at most 4e9 packets per set
+  const float inv_tau = sd.inv_tau_f;
+  const int n_bins = sd.n_bins, row = hist_row(sd.n_bins), n_snap = sd.n_snap;
+
+  // ---- warp loop
+  // The warp owns a chunk [pool_next, pool_end) of packet offsets and has the
+  // next chunk's claim already in flight (lane 0's `pre`), so the global
+  // atomic's latency is hidden behind a chunk's worth of events.
+  unsigned pool_next = 0, pool_end = 0;
+  unsigned long long pre = 0;
+  if (lane == 0) pre = atomicAdd(ctr, (unsigned long long)chunk);
+  bool exhausted = false, alive = false;
+  unsigned long long pk = 0, W = 0;
+  long long Sq = 0;
+  unsigned kev = 0, nev = 0, nsca = 0, nsurf = 0;   // nev: events left before the limit
+  unsigned long long dmask = 0;
+  float vcur = 0.f, ux = 0.f, uy = 0.f, uz = -1.f, iuz = -1.f;
+  float Xx = 0.f, Xy = 0.f, vapp = 0.f, vcomp = 0.f;
+  unsigned st_launch = 0, st_events = 0, st_scat = 0, st_surf = 0, st_esc = 0;
+  unsigned long long st_wesc = 0, st_wabs = 0, st_wsurf = 0;   // escaped / absorbed weight
+
+  for (;;) {
+    // refill dead lanes from the warp's chunk of packets, in one pass: when
+    // the chunk runs out, the lanes it could not serve wait one flight
+    const unsigned need = __ballot_sync(kFull, !alive);
+    if (need) {
+      unsigned avail = pool_end - pool_next;
+      if (avail == 0 && !exhausted) {
+        const unsigned long long b = __shfl_sync(kFull, pre, 0);
+        if (b >= (unsigned long long)n_pk) {
+          exhausted = true;
+        } else {
+          if (lane == 0) pre = atomicAdd(ctr, (unsigned long long)chunk);
+          pool_next = (unsigned)b;
+          pool_end = n_pk - pool_next > chunk ? pool_next + chunk : n_pk;
+          avail = pool_end - pool_next;
+        }
+      }
+      const unsigned cnt = __popc(need);
+      const unsigned take = avail < cnt ? avail : cnt;
+      const unsigned rank = __popc(need & lanemask_lt());
+      if (!alive && rank < take) {
+        // Step (1): a new packet at the top of the cloud moving along -z
+        pk = base_pk + (pool_next + rank);
+        ux = 0.f; uy = 0.f; uz = -1.f; iuz = -1.f;
+        if (sd.launch_horizontal) {      // test hook: the horizontal-flight rule
+          ux = 1.f; uz = 0.f; iuz = 0.f;
+        }
+        Sq = (long long)kOneQ;
+        vcur = sd.v_top_f;
+        Xx = 0.f; Xy = 0.f; vapp = 0.f; vcomp = 0.f;
+        W = 1ull << 32;
+        kev = 1; nev = sd.max_events;
+        if (DUMP) { nsca = 0; nsurf = 0; dmask = 0; }
+        ++st_launch;
+        alive = true;
+      }
+      pool_next += take;
+    }
+    if (!__any_sync(kFull, alive)) break;
+
+    // ---- one flight and what ends it. Every lane runs the same straight
+    // line; the outcome's predicates select what each lane commits, and a
+    // lane without a packet (at the end of a set) commits nothing.
+    const uint4 r = philox4x32_10_rk(make_uint4((unsigned)pk, (unsigned)(pk >> 32), kev, sid), sd.rk);
+    ++kev;
+    const float tau = -logf(u23f(r.x));                // Step (3): Beer–Lambert
+    const float dS = tau * uz * inv_tau;
+    const bool horiz = fabsf(uz) < 1e-9f;
+    // the largest binary32 magnitude below 1 keeps fix62 in range; a flight of
+    // |dS| >= 1 leaves the cloud whatever its fixed-point end
+    const long long Sn = Sq + fix62(fminf(fmaxf(dS, -0.99999994f), 0.99999994f));
+    // 0 interaction, 1 escape through the top, 2 free surface, 3 horizontal
+    const int what = horiz ? 3
+                           : ((dS >= 1.0f || Sn >= (long long)kOneQ) ? 1
+                                                                      : ((dS <= -1.0f || Sn <= 0) ? 2 : 0));
+    // velocity coordinate z/t where the flight ends
+    float vn = vcur;
+    if (sd.expo) {
+      // Eq. 20 inverted in closed form: v = v_fs (1 - ln((1 - S) + S eps) / beta); 1 - S is
+      // exact in the fixed-point state, so the top of the cloud keeps its relative precision
+      // (32-bit conversions: the 64-bit ones run on the FP64 pipe)
+      const unsigned long long sn = (unsigned long long)Sn, oms = kOneQ - sn;
+      const float om = fmaf(__uint2float_rn((unsigned)(oms >> 32)), kTwoM30f,
+                            __uint2float_rn((unsigned)oms) * kTwoM62f);
+      const float q = fmaf(__uint2float_rn((unsigned)(sn >> 32)) * kTwoM30f, sd.eps_f, om);
+      vn = fmaf(-sd.lg_c_f, __log2f(q), sd.v_fs_f);
+    } else if (what == 0) {
+      const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sn);
+      const float fd = u64_to_f((unsigned long long)Sn - tb.Sq[j]);
+      vn = fmaf(fd, tb.w[j], fmaf((float)j, sd.dv_f, sd.v_bot_f));
+    }
+    vn = what == 1 ? sd.v_top_f : (what == 2 ? sd.v_fs_f : (what == 3 ? vcur : vn));
+    // lateral displacement in velocity units (x = x0 + t X)
+    if (!horiz) {
+      const float d = vn - vcur;
+      Xx = fmaf(ux * iuz, d, Xx);
+      Xy = fmaf(uy * iuz, d, Xy);
+    } else {
+      // horizontal packet: lateral path tau / mu(z), in velocity units tau / tau_tot dv/dS
+      float dvds;
+      if (sd.expo) {
+        const unsigned long long sq = (unsigned long long)Sq, oms = kOneQ - sq;
+        const float om = fmaf(__uint2float_rn((unsigned)(oms >> 32)), kTwoM30f,
+                              __uint2float_rn((unsigned)oms) * kTwoM62f);
+        dvds = sd.dvds_c_f / fmaf(__uint2float_rn((unsigned)(sq >> 32)) * kTwoM30f, sd.eps_f, om);
+      } else {
+        const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sq);
+        dvds = tb.w[j] * 4.611686018427388e18f;
+      }
+      const float len = tau * inv_tau * dvds;
+      Xx = fmaf(ux, len, Xx);
+      Xy = fmaf(uy, len, Xy);
+    }
+
+    // ---- Step (6): out through the top, vacuum flight to the probe plane
+    const bool esc = alive && what == 1;
+    const bool cone = esc && (sd.cone_all || uz >= sd.cos_alpha_f);
+    if (cone) {
+      const float fb = floorf((vapp - vcomp - sd.v_lo_f) * sd.inv_dbin_f);
+      const int idx = fb < 0.0f ? 0 : (fb >= (float)n_bins ? n_bins + 1 : (int)fb + 1);
+      if (sd.ap_all) {
+        // Eq. 19 at every snapshot time alike (unlimited aperture): one
+        // tally in row 0, which the normalisation reads for each time
+        atomicAdd(&tb.hist[idx], W);
+        atomicAdd(&tb.hist[n_bins + 2], 1ull);
+        if (DUMP) dmask = n_snap >= 64 ? ~0ull : ((1ull << n_snap) - 1ull);
+      } else {
+        float x0, y0;
+        launch_position(pk, sid, key, sd.r_beam_f, x0, y0);
+        const float tx = ux * iuz, ty = uy * iuz;
+        const float ax = fmaf(tx, sd.z_probe_f, x0), ay = fmaf(ty, sd.z_probe_f, y0);
+        const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
+        // |a + t b|^2 <= R^2 holds on one interval of t: visit the ascending
+        // snapshot times inside it, plus one on each side, each re-tested
+        // exactly as below (the interval only narrows the search)
+        int s0 = 0, s1 = n_snap;
+        const float A = fmaf(bx, bx, by * by);
+        const float B = 2.0f * fmaf(ax, bx, ay * by);
+        const float Cc = fmaf(ax, ax, fmaf(ay, ay, -sd.r_ap2_f));
+        const float disc = fmaf(B, B, -4.0f * A * Cc);
+        if (A > 0.0f) {
+          if (disc < 0.0f) {
+            s1 = 0;
+          } else {
+            const float q = sqrtf(disc), ia = 0.5f / A;
+            const float t1 = (-B - q) * ia, t2 = (-B + q) * ia;
+            int lo = 0, hi = n_snap;                   // first time >= t1
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (tb.ts[mid] < t1) lo = mid + 1; else hi = mid;
+            }
+            s0 = lo > 0 ? lo - 1 : 0;
+            hi = n_snap;                               // first time > t2
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (tb.ts[mid] <= t2) lo = mid + 1; else hi = mid;
+            }
+            s1 = lo < n_snap ? lo + 1 : n_snap;
+          }
+        }
+        for (int s = s0; s < s1; ++s) {
+          const float t = tb.ts[s];
+          const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
+          if (fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
+            // Eq. 19: tally the out-photon at its frequency shift
+            const int sr = tb.perm[s];
+            atomicAdd(&tb.hist[(size_t)sr * row + idx], W);
+            atomicAdd(&tb.hist[(size_t)sr * row + n_bins + 2], 1ull);
+            if (DUMP && sr < 64) dmask |= 1ull << sr;
+          }
+        }
+      }
+    }
+    st_esc += esc ? 1u : 0u;
+    st_wesc += esc ? W : 0ull;
+
+    // ---- an event: interaction (what 0, 3) or the free surface (what 2)
+    const bool ev = alive && what != 1;
+    const bool surf = ev && what == 2;
+    if (ev) {
+      Sq = what == 2 ? 0ll : (what == 3 ? Sq : Sn);
+      vcur = vn;
+      --nev;
+      ++st_events;
+    }
+    // Step (6): free surface z = v_fs t, reflectivity in 2^32 fixed point
+    const unsigned long long Wr =
+        sd.R_q >= (1ull << 32) ? W : ((W * sd.R_q + (1ull << 31)) >> 32);
+    st_surf += surf ? 1u : 0u;
+    if (DUMP) nsurf += surf ? 1u : 0u;
+    st_wsurf += surf ? W - Wr : 0ull;
+    W = surf ? Wr : W;
+    // Eq. 11: analog absorption (the gate is omega_q). Implicit capture (gate
+    // 0): the particle absorbs 1 - omega of the weight and the packet
+    // scatters; a light packet plays the roulette on r1. Launches without
+    // implicit sets compile this out.
+    const bool absorb = ev && !surf && (r.y >> 8) >= (IMPL ? sd.absorb_gate : sd.omega_q);
+    unsigned fate = esc ? 1u : 0u;
+    if (!IMPL) {
+      st_wabs += absorb ? W : 0ull;
+      fate = absorb ? 2u : fate;
+    } else if (absorb) {
+      if (!sd.implicit) {
+        st_wabs += W;
+        fate = 2;
+      } else {
+        const unsigned long long Wn = (W * sd.omega_q + (1ull << 23)) >> 24;
+        st_wabs += W - Wn;
+        W = Wn;
+        if (Wn < PDV_ROULETTE_W) {
+          if (Wn != 0 && (r.y >> 8) < PDV_ROULETTE_Q) {
+            atomicAdd(&s_cnt[C_W_RR_GAINED], (PDV_ROULETTE_M - 1) * Wn);
+            W = Wn * PDV_ROULETTE_M;
+          } else {
+            atomicAdd(&s_cnt[C_W_RR_DROPPED], Wn);
+            fate = 5;
+          }
+        }
+      }
+    }
+
+    // ---- new direction. Particle scattering (Eq. 13-17): polar angle from
+    // the phase CDF, azimuth uniform (Eq. 15). Free surface (diffuse): polar
+    // angle uniform in [0, pi/2) from +z, azimuth uniform. Both are a
+    // (polar, azimuth) pair in units of pi followed by the same rotation.
+    const bool scat = ev && fate == 0;
+    const bool part = scat && !surf;
+    // polar angle as a table node plus a remainder d: a particle's from its
+    // phase-CDF bin (theta_i + frac (theta_{i+1} - theta_i)), the wall's
+    // theta' = (pi/2) u from the turn table at a quarter of a turn. Phase
+    // tables with a node spacing above 3.1e-3 (where d^4/24 would matter)
+    // take sin/cos of the angle in half turns instead.
+    float st, ct, sp, cp;
+    {
+      const unsigned m2 = r.z >> 8;
+      const unsigned c = m2 >> (24 - kGuidePhaseLog);
+      int lo = tb.Gp[c], hi = part ? (int)tb.Gp[c + 1] : lo;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tb.Cq[mid] <= m2) lo = mid; else hi = mid - 1;
+      }
+      const unsigned c0 = tb.Cq[lo];
+      const float fm = (float)(m2 - c0) + 0.5f;
+      if (sd.angle_table) {
+        const float dp = sd.phase_uniform
+                             ? fm * rcp_approx((float)(tb.Cq[lo + 1] - c0)) * sd.dth_f
+                             : fm * tb.dthpi[lo] * 3.14159265f;
+        // theta' = 2 pi f with f = u / 4 = ((r1 >> 9) + 1/2) 2^-25: the nearest
+        // table step j and the remainder, both exact in integers
+        const int m1 = (int)(r.y >> 9);
+        const int js = (m1 + (1 << 14)) >> 15;
+        const float ds = (float)(2 * (m1 - (js << 15)) + 1) * kPi2m25f;
+        cos_sin_add(surf ? tb.turn[js] : tb.cs[lo], surf ? ds : dp, &ct, &st);
+      } else {
+        // theta_i / pi = i / (n_p - 1) on a uniform grid; linear inside the CDF bin
+        const float tp = sd.phase_uniform
+                             ? ((float)lo + fm * rcp_approx((float)(tb.Cq[lo + 1] - c0))) * sd.inv_nm1
+                             : fmaf(fm, tb.dthpi[lo], tb.thpi[lo]);
+        sincospi_half_turns(surf ? 0.5f * u23f(r.y) : tp, &st, &ct);
+      }
+    }
+    {
+      // azimuth, Eq. 15: phi = 2 pi u with u = ((r >> 9) + 1/2) 2^-23
+      const int mp = (int)((surf ? r.z : r.w) >> 9);
+      const int jp = (mp + (1 << 12)) >> 13;
+      const float dphi = (float)(2 * (mp - (jp << 13)) + 1) * kPi2m23f;
+      cos_sin_add(tb.turn[jp & (kTurn - 1)], dphi, &cp, &sp);
+    }
+    if (sd.surface_mode == PDV_SURFACE_LAMBERT) {
+      const float a = u23f(r.y);
+      ct = surf ? sqrtf(a) : ct;
+      st = surf ? sqrtf(1.0f - a) : st;
+    }
+    // Eq. 16 in its standard form, with the horizontal norm from (u_x, u_y);
+    // Eq. 17 (and the wall's frame) when the direction is vertical (its
+    // horizontal part below 1e-15): cos(theta) along the sign of u_z
+    const float h2 = fmaf(ux, ux, uy * uy);
+    const bool vert = surf || h2 < 1e-30f;
+    const float rs = rsqrtf(h2);
+    const float sh = h2 * rs;
+    const float ah = st * rs;
+    float nx = fmaf(ah, fmaf(ux * uz, cp, -uy * sp), ux * ct);
+    float ny = fmaf(ah, fmaf(uy * uz, cp, ux * sp), uy * ct);
+    float nz = fmaf(-st * cp, sh, uz * ct);
+    nx = vert ? st * cp : nx;
+    ny = vert ? st * sp : ny;
+    nz = vert ? ((surf || uz >= 0.0f) ? ct : -ct) : nz;
+    const bool spec = surf && sd.surface_mode == PDV_SURFACE_SPECULAR;
+    const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+    nx = spec ? ux : nx * inv_n;
+    ny = spec ? uy : ny * inv_n;
+    nz = spec ? -uz : nz * inv_n;
+    if (scat) {
+      // Eq. 4 / Eq. 18: the moving scatterer (or wall) shifts the frequency
+      // (a rounded product: no FMA contraction into the compensated sum,
+      // so every instantiation of this kernel computes the same bits)
+      kahan_add(vapp, vcomp, __fmul_rn(0.5f * (nz - uz), vn));
+      ux = nx; uy = ny; uz = nz;
+      iuz = rcp_approx(nz);
+    }
+    st_scat += part ? 1u : 0u;
+    if (DUMP) nsca += part ? 1u : 0u;
+    fate = (scat && W == 0) ? 3u : fate;     // the surface absorbed all of the weight
+    if (fate == 0 && ev && nev == 0u) {
+      atomicAdd(&s_cnt[C_W_TRUNCATED], W);
+      atomicAdd(&s_cnt[C_TRUNCATED], 1ull);
+      fate = 4;
+    }
+    if (fate) {
+      if (DUMP && sd.packets) {
+        pdv_packet_record rec;
+        rec.n_events = sd.max_events - nev;
+        rec.n_scatters = nsca;
+        rec.n_surface = nsurf;
+        rec.fate = fate;
+        rec.weight = W;
+        rec.v_app = (double)vapp - (double)vcomp;
+        rec.detect_mask = dmask;
+        sd.packets[pk - base_pk] = rec;
+      }
+      alive = false;
+    }
+  }
+
+  // ---- flush this set's tallies
+  {
+    unsigned a = st_launch, b = st_events, c = st_scat, d = st_surf, e = st_esc;
+    unsigned long long we = st_wesc, wa = st_wabs, ws = st_wsurf;
+    for (int o = 16; o; o >>= 1) {
+      a += __shfl_xor_sync(kFull, a, o);
+      b += __shfl_xor_sync(kFull, b, o);
+      c += __shfl_xor_sync(kFull, c, o);
+      d += __shfl_xor_sync(kFull, d, o);
+      e += __shfl_xor_sync(kFull, e, o);
+      we += __shfl_xor_sync(kFull, we, o);
+      wa += __shfl_xor_sync(kFull, wa, o);
+      ws += __shfl_xor_sync(kFull, ws, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&s_cnt[C_LAUNCHED], (unsigned long long)a);
+      atomicAdd(&s_cnt[C_EVENTS], (unsigned long long)b);
+      atomicAdd(&s_cnt[C_SCATTERS], (unsigned long long)c);
+      atomicAdd(&s_cnt[C_SURFACE_HITS], (unsigned long long)d);
+      atomicAdd(&s_cnt[C_ESCAPES], (unsigned long long)e);
+      atomicAdd(&s_cnt[C_W_ESCAPED], we);
+      atomicAdd(&s_cnt[C_W_ABS_PARTICLE], wa);
+      atomicAdd(&s_cnt[C_W_ABS_SURFACE], ws);
+    }
+  }
+}
+
+// The block's counters and private histogram into the set's global tallies.
+template <int HMODE>
+__device__ __forceinline__ void flush_set(const SetDesc& sd, const SmemTables& tb,
+                                          const unsigned long long* s_cnt) {
+  if (threadIdx.x < C_NCOUNT && s_cnt[threadIdx.x])
+    atomicAdd(&sd.cnt[threadIdx.x], s_cnt[threadIdx.x]);
+  if (HMODE == 2) {
+    const int nh = tally_rows(sd.n_snap, sd.ap_all) * hist_row(sd.n_bins);
+    for (int i = threadIdx.x; i < nh; i += blockDim.x) {
+      const unsigned long long v = tb.hist[i];
+      if (v) atomicAdd(&sd.hist[i], v);
+    }
+  }
+}
+
+// Persistent launch over a list of sets (batches and serving): blocks walk the
+// list from their own offset and stay on a set until its packets are claimed.
 template <bool DUMP, int HMODE, bool IMPL>
 __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restrict__ sets,
                                                           int n_sets,
@@ -149,11 +612,7 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
   __shared__ SetDesc sd;
   __shared__ unsigned long long s_cnt[C_NCOUNT];
   __shared__ int s_go;
-  __shared__ uint2 s_rk[10];                       // the set's Philox round keys
-
-  const int lane = threadIdx.x & 31;
   const int start = (int)(((long long)blockIdx.x * n_sets) / gridDim.x);
-
   for (int step = 0; step < n_sets; ++step) {
     const int si = (start + step) % n_sets;
     if (threadIdx.x == 0) {
@@ -164,8 +623,6 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
     const int go = s_go;
     __syncthreads();
     if (!go) continue;
-
-    // ---- stage the set descriptor and its tables in shared memory
     {
       const int* src = reinterpret_cast<const int*>(&sets[si]);
       int* dst = reinterpret_cast<int*>(&sd);
@@ -174,417 +631,48 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
       if (threadIdx.x < C_NCOUNT) s_cnt[threadIdx.x] = 0ull;
     }
     __syncthreads();
-    size_t off[10];
-    smem_layout(sd.n_v, sd.n_g, sd.n_p, sd.n_snap, sd.n_bins, HMODE, sd.phase_uniform, sd.ap_all,
-                sd.expo, off);
-    SmemTables tb;
-    tb.Sq = reinterpret_cast<const unsigned long long*>(smem + off[0]);
-    tb.w = reinterpret_cast<const float*>(smem + off[1]);
-    tb.G = reinterpret_cast<const unsigned short*>(smem + off[2]);
-    tb.Cq = reinterpret_cast<const unsigned*>(smem + off[3]);
-    tb.thpi = reinterpret_cast<const float*>(smem + off[4]);
-    tb.dthpi = reinterpret_cast<const float*>(smem + off[5]);
-    tb.Gp = reinterpret_cast<const unsigned short*>(smem + off[6]);
-    tb.ts = reinterpret_cast<const float*>(smem + off[7]);
-    tb.perm = reinterpret_cast<const unsigned short*>(smem + off[8]);
-    tb.hist = HMODE == 2 ? reinterpret_cast<unsigned long long*>(smem + off[9]) : sd.hist;
-    {
-      if (!sd.expo) {
-        unsigned long long* Sq = reinterpret_cast<unsigned long long*>(smem + off[0]);
-        for (int i = threadIdx.x; i <= sd.n_v; i += blockDim.x) Sq[i] = sd.Sq[i];
-        float* w = reinterpret_cast<float*>(smem + off[1]);
-        for (int i = threadIdx.x; i < sd.n_v; i += blockDim.x) w[i] = sd.w[i];
-        unsigned short* G = reinterpret_cast<unsigned short*>(smem + off[2]);
-        for (int i = threadIdx.x; i <= sd.n_g; i += blockDim.x) G[i] = sd.G[i];
-      }
-      unsigned* Cq = reinterpret_cast<unsigned*>(smem + off[3]);
-      float* thpi = reinterpret_cast<float*>(smem + off[4]);
-      float* dthpi = reinterpret_cast<float*>(smem + off[5]);
-      for (int i = threadIdx.x; i < sd.n_p; i += blockDim.x) {
-        Cq[i] = sd.Cq[i];
-        if (!sd.phase_uniform) {
-          thpi[i] = sd.thpi[i];
-          dthpi[i] = sd.dthpi[i];
-        }
-      }
-      unsigned short* Gp = reinterpret_cast<unsigned short*>(smem + off[6]);
-      for (int i = threadIdx.x; i <= (1 << kGuidePhaseLog); i += blockDim.x) Gp[i] = sd.Gp[i];
-      float* ts = reinterpret_cast<float*>(smem + off[7]);
-      unsigned short* perm = reinterpret_cast<unsigned short*>(smem + off[8]);
-      for (int i = threadIdx.x; i < sd.n_snap; i += blockDim.x) {
-        ts[i] = (float)sd.t_snap[sd.n_snap + i];
-        perm[i] = (unsigned short)sd.t_snap[2 * sd.n_snap + i];
-      }
-      if (threadIdx.x < 10)
-        s_rk[threadIdx.x] = philox_round_key(
-            make_uint2((unsigned)sd.seed, (unsigned)(sd.seed >> 32)), threadIdx.x);
-      if (HMODE == 2) {
-        unsigned long long* h = reinterpret_cast<unsigned long long*>(smem + off[9]);
-        const int nh = tally_rows(sd.n_snap, sd.ap_all) * hist_row(sd.n_bins);
-        for (int i = threadIdx.x; i < nh; i += blockDim.x) h[i] = 0ull;
-      }
-    }
+    const SmemTables tb = stage_set<HMODE>(sd, smem);
     __syncthreads();
-
-    // ---- per-set constants in registers
-    const uint2 key = make_uint2((unsigned)sd.seed, (unsigned)(sd.seed >> 32));
-    const unsigned sid = sd.stream_id;
-    const unsigned long long base_pk = sd.packet_begin;
-    const unsigned n_pk = (unsigned)sd.n_packets;    // at most 4e9 packets per set
-    const float inv_tau = sd.inv_tau_f;
-    const int n_bins = sd.n_bins, row = hist_row(sd.n_bins), n_snap = sd.n_snap;
-
-    // ---- warp loop
-    // The warp owns a chunk [pool_next, pool_end) of packet offsets and has the
-    // next chunk's claim already in flight (lane 0's `pre`), so the global
-    // atomic's latency is hidden behind a chunk's worth of events.
-    unsigned pool_next = 0, pool_end = 0;
-    unsigned long long pre = 0;
-    if (lane == 0) pre = atomicAdd(&set_ctr[si], (unsigned long long)chunk);
-    bool exhausted = false, alive = false;
-    unsigned long long pk = 0, W = 0;
-    long long Sq = 0;
-    unsigned kev = 0, nev = 0, nsca = 0, nsurf = 0;   // nev: events left before the limit
-    unsigned long long dmask = 0;
-    float vcur = 0.f, ux = 0.f, uy = 0.f, uz = -1.f, iuz = -1.f;
-    float Xx = 0.f, Xy = 0.f, vapp = 0.f, vcomp = 0.f;
-    unsigned st_launch = 0, st_events = 0, st_scat = 0, st_surf = 0, st_esc = 0;
-    unsigned long long st_wesc = 0, st_wabs = 0, st_wsurf = 0;   // escaped / absorbed weight
-
-    for (;;) {
-      // refill dead lanes from the warp's chunk of packets
-      unsigned need = __ballot_sync(kFull, !alive);
-      while (need) {
-        const unsigned avail = pool_end - pool_next;
-        if (avail == 0) {
-          if (exhausted) break;
-          const unsigned long long b = __shfl_sync(kFull, pre, 0);
-          if (b >= (unsigned long long)n_pk) {
-            exhausted = true;
-            break;
-          }
-          if (lane == 0) pre = atomicAdd(&set_ctr[si], (unsigned long long)chunk);
-          pool_next = (unsigned)b;
-          pool_end = n_pk - pool_next > chunk ? pool_next + chunk : n_pk;
-          continue;
-        }
-        const unsigned cnt = __popc(need);
-        const unsigned take = avail < cnt ? avail : cnt;
-        const unsigned rank = __popc(need & lanemask_lt());
-        if (!alive && rank < take) {
-          // Step (1): a new packet at the top of the cloud moving along -z
-          pk = base_pk + (pool_next + rank);
-          ux = 0.f; uy = 0.f; uz = -1.f; iuz = -1.f;
-          if (sd.launch_horizontal) {      // test hook: the horizontal-flight rule
-            ux = 1.f; uz = 0.f; iuz = 0.f;
-          }
-          Sq = (long long)kOneQ;
-          vcur = sd.v_top_f;
-          Xx = 0.f; Xy = 0.f; vapp = 0.f; vcomp = 0.f;
-          W = 1ull << 32;
-          kev = 1; nev = sd.max_events;
-          if (DUMP) { nsca = 0; nsurf = 0; dmask = 0; }
-          ++st_launch;
-          alive = true;
-        }
-        pool_next += take;
-        need = __ballot_sync(kFull, !alive);
-      }
-      if (!__any_sync(kFull, alive)) break;
-
-      // ---- one flight and what ends it. Every lane runs the same straight
-      // line; the outcome's predicates select what each lane commits, and a
-      // lane without a packet (at the end of a set) commits nothing.
-      const uint4 r = philox4x32_10_rk(make_uint4((unsigned)pk, (unsigned)(pk >> 32), kev, sid), s_rk);
-      ++kev;
-      const float tau = -logf(u23f(r.x));                // Step (3): Beer–Lambert
-      const float dS = tau * uz * inv_tau;
-      const bool horiz = fabsf(uz) < 1e-9f;
-      // the largest binary32 magnitude below 1 keeps fix62 in range; a flight of
-      // |dS| >= 1 leaves the cloud whatever its fixed-point end
-      const long long Sn = Sq + fix62(fminf(fmaxf(dS, -0.99999994f), 0.99999994f));
-      // 0 interaction, 1 escape through the top, 2 free surface, 3 horizontal
-      const int what = horiz ? 3
-                             : ((dS >= 1.0f || Sn >= (long long)kOneQ) ? 1
-                                                                        : ((dS <= -1.0f || Sn <= 0) ? 2 : 0));
-      // velocity coordinate z/t where the flight ends
-      float vn = vcur;
-      if (sd.expo) {
-        // Eq. 20 inverted in closed form: v = v_fs (1 - ln((1 - S) + S eps) / beta); 1 - S is
-        // exact in the fixed-point state, so the top of the cloud keeps its relative precision
-        // (32-bit conversions: the 64-bit ones run on the FP64 pipe)
-        const unsigned long long sn = (unsigned long long)Sn, oms = kOneQ - sn;
-        const float om = fmaf(__uint2float_rn((unsigned)(oms >> 32)), kTwoM30f,
-                              __uint2float_rn((unsigned)oms) * kTwoM62f);
-        const float q = fmaf(__uint2float_rn((unsigned)(sn >> 32)) * kTwoM30f, sd.eps_f, om);
-        vn = fmaf(-sd.lg_c_f, __log2f(q), sd.v_fs_f);
-      } else if (what == 0) {
-        const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sn);
-        const float fd = u64_to_f((unsigned long long)Sn - tb.Sq[j]);
-        vn = fmaf(fd, tb.w[j], fmaf((float)j, sd.dv_f, sd.v_bot_f));
-      }
-      vn = what == 1 ? sd.v_top_f : (what == 2 ? sd.v_fs_f : (what == 3 ? vcur : vn));
-      // lateral displacement in velocity units (x = x0 + t X)
-      if (!horiz) {
-        const float d = vn - vcur;
-        Xx = fmaf(ux * iuz, d, Xx);
-        Xy = fmaf(uy * iuz, d, Xy);
-      } else {
-        // horizontal packet: lateral path tau / mu(z), in velocity units tau / tau_tot dv/dS
-        float dvds;
-        if (sd.expo) {
-          const unsigned long long sq = (unsigned long long)Sq, oms = kOneQ - sq;
-          const float om = fmaf(__uint2float_rn((unsigned)(oms >> 32)), kTwoM30f,
-                                __uint2float_rn((unsigned)oms) * kTwoM62f);
-          dvds = sd.dvds_c_f / fmaf(__uint2float_rn((unsigned)(sq >> 32)) * kTwoM30f, sd.eps_f, om);
-        } else {
-          const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sq);
-          dvds = tb.w[j] * 4.611686018427388e18f;
-        }
-        const float len = tau * inv_tau * dvds;
-        Xx = fmaf(ux, len, Xx);
-        Xy = fmaf(uy, len, Xy);
-      }
-
-      // ---- Step (6): out through the top, vacuum flight to the probe plane
-      const bool esc = alive && what == 1;
-      if (esc && (sd.cone_all || uz >= sd.cos_alpha_f)) {
-        const float fb = floorf((vapp - vcomp - sd.v_lo_f) * sd.inv_dbin_f);
-        const int idx = fb < 0.0f ? 0 : (fb >= (float)n_bins ? n_bins + 1 : (int)fb + 1);
-        if (sd.ap_all) {
-          // Eq. 19 at every snapshot time alike (unlimited aperture): one
-          // tally in row 0, which the normalisation reads for each time
-          atomicAdd(&tb.hist[idx], W);
-          atomicAdd(&tb.hist[n_bins + 2], 1ull);
-          if (DUMP) dmask = n_snap >= 64 ? ~0ull : ((1ull << n_snap) - 1ull);
-        } else {
-          float x0, y0;
-          launch_position(pk, sid, key, sd.r_beam_f, x0, y0);
-          const float tx = ux * iuz, ty = uy * iuz;
-          const float ax = fmaf(tx, sd.z_probe_f, x0), ay = fmaf(ty, sd.z_probe_f, y0);
-          const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
-          // |a + t b|^2 <= R^2 holds on one interval of t: visit the ascending
-          // snapshot times inside it, plus one on each side, each re-tested
-          // exactly as below (the interval only narrows the search)
-          int s0 = 0, s1 = n_snap;
-          const float A = fmaf(bx, bx, by * by);
-          const float B = 2.0f * fmaf(ax, bx, ay * by);
-          const float Cc = fmaf(ax, ax, fmaf(ay, ay, -sd.r_ap2_f));
-          const float disc = fmaf(B, B, -4.0f * A * Cc);
-          if (A > 0.0f) {
-            if (disc < 0.0f) {
-              s1 = 0;
-            } else {
-              const float q = sqrtf(disc), ia = 0.5f / A;
-              const float t1 = (-B - q) * ia, t2 = (-B + q) * ia;
-              int lo = 0, hi = n_snap;                   // first time >= t1
-              while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (tb.ts[mid] < t1) lo = mid + 1; else hi = mid;
-              }
-              s0 = lo > 0 ? lo - 1 : 0;
-              hi = n_snap;                               // first time > t2
-              while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (tb.ts[mid] <= t2) lo = mid + 1; else hi = mid;
-              }
-              s1 = lo < n_snap ? lo + 1 : n_snap;
-            }
-          }
-          for (int s = s0; s < s1; ++s) {
-            const float t = tb.ts[s];
-            const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
-            if (fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
-              // Eq. 19: tally the out-photon at its frequency shift
-              const int sr = tb.perm[s];
-              atomicAdd(&tb.hist[(size_t)sr * row + idx], W);
-              atomicAdd(&tb.hist[(size_t)sr * row + n_bins + 2], 1ull);
-              if (DUMP && sr < 64) dmask |= 1ull << sr;
-            }
-          }
-        }
-      }
-      st_esc += esc ? 1u : 0u;
-      st_wesc += esc ? W : 0ull;
-
-      // ---- an event: interaction (what 0, 3) or the free surface (what 2)
-      const bool ev = alive && what != 1;
-      const bool surf = ev && what == 2;
-      if (ev) {
-        Sq = what == 2 ? 0ll : (what == 3 ? Sq : Sn);
-        vcur = vn;
-        --nev;
-        ++st_events;
-      }
-      // Step (6): free surface z = v_fs t, reflectivity in 2^32 fixed point
-      const unsigned long long Wr =
-          sd.R_q >= (1ull << 32) ? W : ((W * sd.R_q + (1ull << 31)) >> 32);
-      st_surf += surf ? 1u : 0u;
-      if (DUMP) nsurf += surf ? 1u : 0u;
-      st_wsurf += surf ? W - Wr : 0ull;
-      W = surf ? Wr : W;
-      // Eq. 11: analog absorption (the gate is omega_q). Implicit capture (gate
-      // 0): the particle absorbs 1 - omega of the weight and the packet
-      // scatters; a light packet plays the roulette on r1. Launches without
-      // implicit sets compile this out.
-      const bool absorb = ev && !surf && (r.y >> 8) >= (IMPL ? sd.absorb_gate : sd.omega_q);
-      unsigned fate = esc ? 1u : 0u;
-      if (!IMPL) {
-        st_wabs += absorb ? W : 0ull;
-        fate = absorb ? 2u : fate;
-      } else if (absorb) {
-        if (!sd.implicit) {
-          st_wabs += W;
-          fate = 2;
-        } else {
-          const unsigned long long Wn = (W * sd.omega_q + (1ull << 23)) >> 24;
-          st_wabs += W - Wn;
-          W = Wn;
-          if (Wn < PDV_ROULETTE_W) {
-            if (Wn != 0 && (r.y >> 8) < PDV_ROULETTE_Q) {
-              atomicAdd(&s_cnt[C_W_RR_GAINED], (PDV_ROULETTE_M - 1) * Wn);
-              W = Wn * PDV_ROULETTE_M;
-            } else {
-              atomicAdd(&s_cnt[C_W_RR_DROPPED], Wn);
-              fate = 5;
-            }
-          }
-        }
-      }
-
-      // ---- new direction. Particle scattering (Eq. 13-17): polar angle from
-      // the phase CDF, azimuth uniform (Eq. 15). Free surface (diffuse): polar
-      // angle uniform in [0, pi/2) from +z, azimuth uniform. Both are a
-      // (polar, azimuth) pair in units of pi followed by the same rotation.
-      const bool scat = ev && fate == 0;
-      const bool part = scat && !surf;
-      float tpi;
-      {
-        const unsigned m2 = r.z >> 8;
-        const unsigned c = m2 >> (24 - kGuidePhaseLog);
-        int lo = tb.Gp[c], hi = part ? (int)tb.Gp[c + 1] : lo;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (tb.Cq[mid] <= m2) lo = mid; else hi = mid - 1;
-        }
-        const unsigned c0 = tb.Cq[lo];
-        float tp;
-        if (sd.phase_uniform) {
-          // theta_i / pi = i / (n_p - 1); linear inside the CDF bin
-          const float frac = ((float)(m2 - c0) + 0.5f) * rcp_approx((float)(tb.Cq[lo + 1] - c0));
-          tp = ((float)lo + frac) * sd.inv_nm1;
-        } else {
-          tp = fmaf((float)(m2 - c0) + 0.5f, tb.dthpi[lo], tb.thpi[lo]);
-        }
-        tpi = surf ? 0.5f * u23f(r.y) : tp;
-      }
-      float st, ct, sp, cp;
-      sincospi_half_turns(tpi, &st, &ct);
-      sincospi_half_turns(2.0f * u23f(surf ? r.z : r.w), &sp, &cp);   // azimuth, Eq. 15
-      if (sd.surface_mode == PDV_SURFACE_LAMBERT) {
-        const float a = u23f(r.y);
-        ct = surf ? sqrtf(a) : ct;
-        st = surf ? sqrtf(1.0f - a) : st;
-      }
-      // Eq. 16 in its standard form, with the horizontal norm from (u_x, u_y);
-      // Eq. 17 (and the wall's frame) when the direction is vertical (its
-      // horizontal part below 1e-15): cos(theta) along the sign of u_z
-      const float h2 = fmaf(ux, ux, uy * uy);
-      const bool vert = surf || h2 < 1e-30f;
-      const float rs = rsqrtf(h2);
-      const float sh = h2 * rs;
-      const float ah = st * rs;
-      float nx = fmaf(ah, fmaf(ux * uz, cp, -uy * sp), ux * ct);
-      float ny = fmaf(ah, fmaf(uy * uz, cp, ux * sp), uy * ct);
-      float nz = fmaf(-st * cp, sh, uz * ct);
-      nx = vert ? st * cp : nx;
-      ny = vert ? st * sp : ny;
-      nz = vert ? ((surf || uz >= 0.0f) ? ct : -ct) : nz;
-      const bool spec = surf && sd.surface_mode == PDV_SURFACE_SPECULAR;
-      const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
-      nx = spec ? ux : nx * inv_n;
-      ny = spec ? uy : ny * inv_n;
-      nz = spec ? -uz : nz * inv_n;
-      if (scat) {
-        // Eq. 4 / Eq. 18: the moving scatterer (or wall) shifts the frequency
-        // (a rounded product: no FMA contraction into the compensated sum,
-        // so every instantiation of this kernel computes the same bits)
-        kahan_add(vapp, vcomp, __fmul_rn(0.5f * (nz - uz), vn));
-        ux = nx; uy = ny; uz = nz;
-        iuz = rcp_approx(nz);
-      }
-      st_scat += part ? 1u : 0u;
-      if (DUMP) nsca += part ? 1u : 0u;
-      fate = (scat && W == 0) ? 3u : fate;     // the surface absorbed all of the weight
-      if (fate == 0 && ev && nev == 0u) {
-        atomicAdd(&s_cnt[C_W_TRUNCATED], W);
-        atomicAdd(&s_cnt[C_TRUNCATED], 1ull);
-        fate = 4;
-      }
-      if (fate) {
-        if (DUMP && sd.packets) {
-          pdv_packet_record rec;
-          rec.n_events = sd.max_events - nev;
-          rec.n_scatters = nsca;
-          rec.n_surface = nsurf;
-          rec.fate = fate;
-          rec.weight = W;
-          rec.v_app = (double)vapp - (double)vcomp;
-          rec.detect_mask = dmask;
-          sd.packets[pk - base_pk] = rec;
-        }
-        alive = false;
-      }
-    }
-
-    // ---- flush this set's tallies
-    {
-      unsigned a = st_launch, b = st_events, c = st_scat, d = st_surf, e = st_esc;
-      unsigned long long we = st_wesc, wa = st_wabs, ws = st_wsurf;
-      for (int o = 16; o; o >>= 1) {
-        a += __shfl_xor_sync(kFull, a, o);
-        b += __shfl_xor_sync(kFull, b, o);
-        c += __shfl_xor_sync(kFull, c, o);
-        d += __shfl_xor_sync(kFull, d, o);
-        e += __shfl_xor_sync(kFull, e, o);
-        we += __shfl_xor_sync(kFull, we, o);
-        wa += __shfl_xor_sync(kFull, wa, o);
-        ws += __shfl_xor_sync(kFull, ws, o);
-      }
-      if (lane == 0) {
-        atomicAdd(&s_cnt[C_LAUNCHED], (unsigned long long)a);
-        atomicAdd(&s_cnt[C_EVENTS], (unsigned long long)b);
-        atomicAdd(&s_cnt[C_SCATTERS], (unsigned long long)c);
-        atomicAdd(&s_cnt[C_SURFACE_HITS], (unsigned long long)d);
-        atomicAdd(&s_cnt[C_ESCAPES], (unsigned long long)e);
-        atomicAdd(&s_cnt[C_W_ESCAPED], we);
-        atomicAdd(&s_cnt[C_W_ABS_PARTICLE], wa);
-        atomicAdd(&s_cnt[C_W_ABS_SURFACE], ws);
-      }
-    }
+    walk_set<DUMP, HMODE, IMPL>(sd, tb, &set_ctr[si], chunk, s_cnt);
     __syncthreads();
-    if (threadIdx.x < C_NCOUNT && s_cnt[threadIdx.x])
-      atomicAdd(&sd.cnt[threadIdx.x], s_cnt[threadIdx.x]);
-    if (HMODE == 2) {
-      const int nh = tally_rows(n_snap, sd.ap_all) * row;
-      for (int i = threadIdx.x; i < nh; i += blockDim.x) {
-        const unsigned long long v = tb.hist[i];
-        if (v) atomicAdd(&sd.hist[i], v);
-      }
-    }
+    flush_set<HMODE>(sd, tb, s_cnt);
     __syncthreads();
   }
 }
 
+// Persistent launch of one set whose descriptor is a kernel parameter: the
+// walk reads its constants (and Philox's round keys) as constant-bank
+// operands instead of shared-memory loads and registers.
+template <bool DUMP, int HMODE, bool IMPL>
+__global__ void __launch_bounds__(256, 4) k_transport_f32_one(const __grid_constant__ SetDesc sd,
+                                                              unsigned long long* __restrict__ ctr,
+                                                              unsigned chunk) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_cnt[C_NCOUNT];
+  if (threadIdx.x < C_NCOUNT) s_cnt[threadIdx.x] = 0ull;
+  const SmemTables tb = stage_set<HMODE>(sd, smem);
+  __syncthreads();
+  walk_set<DUMP, HMODE, IMPL>(sd, tb, ctr, chunk, s_cnt);
+  __syncthreads();
+  flush_set<HMODE>(sd, tb, s_cnt);
+}
+
 template <bool IMPL>
-static const void* f32_kernel_impl(int hist_mode, bool dump) {
+static const void* f32_kernel_impl(int hist_mode, bool dump, bool one) {
+  if (one) {
+    if (dump)
+      return hist_mode == 2 ? (const void*)k_transport_f32_one<true, 2, IMPL>
+                            : (const void*)k_transport_f32_one<true, 1, IMPL>;
+    return hist_mode == 2 ? (const void*)k_transport_f32_one<false, 2, IMPL>
+                          : (const void*)k_transport_f32_one<false, 1, IMPL>;
+  }
   if (dump)
     return hist_mode == 2 ? (const void*)k_transport_f32<true, 2, IMPL> : (const void*)k_transport_f32<true, 1, IMPL>;
   return hist_mode == 2 ? (const void*)k_transport_f32<false, 2, IMPL> : (const void*)k_transport_f32<false, 1, IMPL>;
 }
 
-static const void* f32_kernel(int hist_mode, bool dump, bool impl) {
-  return impl ? f32_kernel_impl<true>(hist_mode, dump) : f32_kernel_impl<false>(hist_mode, dump);
+static const void* f32_kernel(int hist_mode, bool dump, bool impl, bool one = false) {
+  return impl ? f32_kernel_impl<true>(hist_mode, dump, one) : f32_kernel_impl<false>(hist_mode, dump, one);
 }
 
 __global__ void k_normalise(const SetDesc* __restrict__ sets, double* const* spec,
@@ -593,12 +681,14 @@ __global__ void k_normalise(const SetDesc* __restrict__ sets, double* const* spe
 
 cudaError_t transport_preload() {
   cudaFuncAttributes a;
-  for (int impl = 0; impl < 2; ++impl)
-    for (int dump = 0; dump < 2; ++dump)
-      for (int hm = 1; hm <= 2; ++hm) {
-        const cudaError_t e = cudaFuncGetAttributes(&a, f32_kernel(hm, dump != 0, impl != 0));
-        if (e != cudaSuccess) return e;
-      }
+  for (int one = 0; one < 2; ++one)
+    for (int impl = 0; impl < 2; ++impl)
+      for (int dump = 0; dump < 2; ++dump)
+        for (int hm = 1; hm <= 2; ++hm) {
+          const cudaError_t e =
+              cudaFuncGetAttributes(&a, f32_kernel(hm, dump != 0, impl != 0, one != 0));
+          if (e != cudaSuccess) return e;
+        }
   return cudaFuncGetAttributes(&a, (const void*)k_normalise);
 }
 
@@ -610,8 +700,8 @@ int transport_f32_max_smem() {
 }
 
 cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, bool impl,
-                                    int* blocks) {
-  const void* k = f32_kernel(hist_mode, dump, impl);
+                                    bool one, int* blocks) {
+  const void* k = f32_kernel(hist_mode, dump, impl, one);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, block, smem);
@@ -624,6 +714,17 @@ void launch_transport_f32(const SetDesc* d_sets, int n_sets, unsigned long long*
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (chunk == 0) chunk = kChunkDefault;
   void* args[] = {(void*)&d_sets, (void*)&n_sets, (void*)&d_set_ctr, (void*)&chunk};
+  cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, st);
+}
+
+void launch_transport_f32_one(const SetDesc& sd, unsigned long long* d_ctr, int grid, int block,
+                              size_t smem, int hist_mode, bool dump, bool impl, unsigned chunk,
+                              cudaStream_t st) {
+  const void* k = f32_kernel(hist_mode, dump, impl, true);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (chunk == 0) chunk = kChunkDefault;
+  SetDesc arg = sd;
+  void* args[] = {(void*)&arg, (void*)&d_ctr, (void*)&chunk};
   cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, st);
 }
 
@@ -669,8 +770,13 @@ __global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict
       int what;
       if (fabs(uz) < 1e-9) {
         what = 3;
-        const int j = search_mass_d(sd.Sd, sd.n_v, S);
-        const double dvds = sd.dv / (sd.Sd[j + 1] - sd.Sd[j]);
+        double dvds;
+        if (sd.expo) {                    // Eq. 20: dv/dS = (v_fs / beta) E / (1 - S E)
+          dvds = sd.vb_d * sd.E_d / (1.0 - S * sd.E_d);
+        } else {
+          const int j = search_mass_d(sd.Sd, sd.n_v, S);
+          dvds = sd.dv / (sd.Sd[j + 1] - sd.Sd[j]);
+        }
         Xx += ux * tau * sd.inv_tau * dvds;
         Xy += uy * tau * sd.inv_tau * dvds;
       } else {
@@ -730,7 +836,12 @@ __global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict
         vapp += 0.5 * (uz - uz_old) * sd.v_fs;
         if (W == 0) fate = 3;
       } else {
-        if (what == 0) {
+        if (what == 0 && sd.expo) {
+          // Eq. 20 inverted in closed form: v = v_fs (1 - ln(1 - S E) / beta)
+          vn = sd.v_fs - sd.vb_d * log1p(-Sn * sd.E_d);
+          Xx += ux / uz * (vn - vcur);
+          Xy += uy / uz * (vn - vcur);
+        } else if (what == 0) {
           const int j = search_mass_d(sd.Sd, sd.n_v, Sn);
           vn = sd.v_bot + j * sd.dv + (Sn - sd.Sd[j]) / (sd.Sd[j + 1] - sd.Sd[j]) * sd.dv;
           Xx += ux / uz * (vn - vcur);
