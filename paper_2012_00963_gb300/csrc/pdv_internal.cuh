@@ -149,16 +149,6 @@ __device__ __forceinline__ double u23d(unsigned r) {
   return ((double)(r >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
-// x * 2^62 truncated towards zero for |x| < 1, exactly: with a = x 2^31
-// (exact), x 2^62 = trunc(a) 2^31 + (a - trunc(a)) 2^31, and both parts are
-// exact 32-bit conversions (the fractional part keeps at most 24 bits).
-__device__ __forceinline__ long long fix62(float x) {
-  const float a = x * 2147483648.0f;
-  const int hi = __float2int_rz(a);
-  const int lo = __float2int_rz((a - truncf(a)) * 2147483648.0f);
-  return ((long long)hi << 31) + (long long)lo;
-}
-
 // sin(pi y) and cos(pi y) for y in [0, 2] (an angle in half turns), in FP32
 // with about 2 ulp error (9.1e-8 absolute): y = q/2 + r with q = rint(2 y) and
 // r in [-1/4, 1/4], both exact; sin(pi r) = r P(r^2) and cos(pi r) =

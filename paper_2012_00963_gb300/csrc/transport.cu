@@ -303,9 +303,11 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     const float tau = -logf(u23f(r.x));                // Step (3): Beer–Lambert
     const float dS = tau * uz * inv_tau;
     const bool horiz = fabsf(uz) < 1e-9f;
-    // the largest binary32 magnitude below 1 keeps fix62 in range; a flight of
-    // |dS| >= 1 leaves the cloud whatever its fixed-point end
-    const long long Sn = Sq + fix62(fminf(fmaxf(dS, -0.99999994f), 0.99999994f));
+    // dS 2^62 truncated towards zero, exactly (a power-of-two scaling, then a
+    // 64-bit conversion); the largest binary32 magnitude below 1 keeps it in
+    // range, and a flight of |dS| >= 1 leaves the cloud whatever its end
+    const long long Sn =
+        Sq + __float2ll_rz(fminf(fmaxf(dS, -0.99999994f), 0.99999994f) * 4.611686018427388e18f);
     // 0 interaction, 1 escape through the top, 2 free surface, 3 horizontal
     const int what = horiz ? 3
                            : ((dS >= 1.0f || Sn >= (long long)kOneQ) ? 1
