@@ -373,6 +373,8 @@ def our_arm(args):
     if rank == 0 and world == 1 and args.side_legs:
         line["precision"] = precision_leg(ctx, stream, 10_000_000)
         line["batch"] = batch_leg(ctx, stream, scale=0.1)
+        line["model"] = model_leg(ctx, stream)
+        line["stepping"] = stepping_leg(ctx, stream)
     ctx.close()
     if rank == 0:
         print(json.dumps(line))
@@ -489,19 +491,24 @@ def batch_leg(ctx, stream, scale):
     sets = [w.replace(n_packets=max(1000, int(w.n_packets * scale))) for w in W.cfg4_sets()]
     clouds = [pdv.Cloud(ctx, w) for w in sets]
     reqs = [pdv.Request(c, w) for c, w in zip(clouds, sets)]
+    def launches():
+        pdv.pdv_simulate_batch(ctx.handle, [r.c for r in reqs])
+        times = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pdv.pdv_simulate_batch(ctx.handle, [r.c for r in reqs])
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b) / 1e3)
+        return statistics.median(times)
+
+    ctx.set_tuning()                                   # the library's defaults
+    t_untuned = launches()
     t0 = time.perf_counter()
     tuning = pdv.pdv_autotune(ctx.handle, [r.c for r in reqs])
     tune_s = time.perf_counter() - t0
-    pdv.pdv_simulate_batch(ctx.handle, [r.c for r in reqs])
-    times = []
-    for _ in range(3):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        pdv.pdv_simulate_batch(ctx.handle, [r.c for r in reqs])
-        b.record(stream)
-        b.synchronize()
-        times.append(a.elapsed_time(b) / 1e3)
-    t = statistics.median(times)
+    t = launches()
     scat = sum(int(r.result()["counters"][0][2]) for r in reqs)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
@@ -519,15 +526,98 @@ def batch_leg(ctx, stream, scale):
         check.append({"set": i, "packets": sets[i].n_packets,
                       "bins_differing": int((got != ref["hist"]).sum()),
                       "max_abs_z": float((np.abs(h_g - h_o) / np.sqrt(h_g + h_o + 1.0)).max())})
+    ctx.set_tuning()
     for c in clouds:
         c.close()
     return {"sets": len(sets), "packet_scale": scale,
             "packets_per_launch": int(sum(w.n_packets for w in sets)),
             "spectra_per_s": len(sets) / t, "ms_per_launch": 1e3 * t,
             "scatter_events_per_s": scat / t, "tuning": tuning, "autotune_s": tune_s,
+            "ms_per_launch_untuned": 1e3 * t_untuned, "tuned_speedup": t_untuned / t,
             "fp64_plain_spectra_per_s": len(sets) / f64, "speedup_vs_fp64_plain": f64 / t,
             "oracle_same_packets": check}
 
+
+
+def model_leg(ctx, stream, n=100_000):
+    """Single-scattering spectra (Eq. 28) of n parameter sets and peak
+    extraction (Eq. 29-35) of n noisy spectra, device-resident, CUDA-event
+    timed; a few of each against the FP64 oracle (ss_peaks)."""
+    import numpy as np
+    import torch
+    from oracle import ss_peaks as OS
+    from paper_2012_00963_gb300 import pdv
+    from paper_2012_00963_gb300 import workloads as W
+    nb, v_lo, v_hi, v_fs, k_c, x_lo, x_hi = 600, 0.0, 8000.0, 2000.0, 40, 1.02, 3.5
+    sets = W.model_sets(n, v_fs=v_fs)
+    d_sets = torch.tensor(sets, device="cuda")
+    d_spec = torch.empty(n * nb, dtype=torch.float64, device="cuda")
+    d_pk = torch.empty(n * pdv.PEAK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    pdv.pdv_ss_spectrum(ctx.handle, d_sets, n, nb, v_lo, v_hi, d_spec, per_dv=True)
+    d_in = (d_spec.view(n, nb) * torch.tensor(W.spectrum_noise((n, nb)), device="cuda")).contiguous()
+    torch.cuda.synchronize()
+
+    def timed(fn, reps=5):
+        fn()
+        ms, kms = [], []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            kms.append(ctx.stats()["last_model_ms"])
+        return statistics.median(ms), statistics.median(kms)
+
+    ss_ms, ss_k = timed(lambda: pdv.pdv_ss_spectrum(ctx.handle, d_sets, n, nb, v_lo, v_hi, d_spec,
+                                                      per_dv=True))
+    pk_ms, pk_k = timed(lambda: pdv.pdv_extract_peaks(ctx.handle, d_in, n, nb, v_lo, v_hi, v_fs, k_c,
+                                                        x_lo, x_hi, d_pk))
+    spec = d_spec.view(n, nb)[:8].cpu().numpy()
+    ss_err = max(float(np.max(np.abs(spec[i] - OS.ss_spectrum_bins(*sets[i][:3], nb, v_lo, v_hi,
+                                                                     per_dv=True)) /
+                         np.max(np.abs(spec[i])))) for i in range(8))
+    pk = np.frombuffer(d_pk.cpu().numpy().tobytes(), pdv.PEAK_DTYPE)
+    noisy = d_in[:8].cpu().numpy()
+    beta_err = max(abs(pk["beta"][i] / OS.extract_peak(noisy[i], v_lo, v_hi, v_fs, k_c, x_lo, x_hi)["beta"]
+                       - 1.0) for i in range(8))
+    return {"sets": n, "bins": nb, "k_c": k_c,
+            "ss_spectra_per_s": n / (ss_ms / 1e3), "ss_kernel_ms": ss_k,
+            "extract_spectra_per_s": n / (pk_ms / 1e3), "extract_kernel_ms": pk_k,
+            "oracle_check": {"ss_max_rel_to_peak": ss_err, "beta_max_rel": float(beta_err),
+                             "sample": 8}}
+
+
+def stepping_leg(ctx, stream, n=10_000_000):
+    """The paper's layer stepping (1000 layers, acceptance-rejection angles) on
+    the Fig. 4 cloud, n photons, CUDA-event timed; 500 photons against the
+    oracle's stepping packet by packet (identical step counts)."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_2012_00963_gb300 import pdv
+    from paper_2012_00963_gb300 import workloads as W
+    wl = W.fig4(n_packets=n)
+    table = O.phase_table(wl)
+    cloud = pdv.Cloud(ctx, wl, table=table)
+    pdv.simulate_spectrum(ctx, cloud, wl, n_packets=100000)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    pdv.simulate_spectrum(ctx, cloud, wl, per_dv=True)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    st = ctx.stats()
+    m = 500
+    got = pdv.simulate_spectrum(ctx, cloud, wl, n_packets=m, packets=True)["packets"]
+    ref = O.simulate(wl, n_packets=m, packets=True, table=table, spread_runs=0)["packets"]
+    cloud.close()
+    return {"photons": n, "layers": wl.n_layers, "seconds_per_spectrum": ms / 1e3,
+            "photons_per_s": n / (ms / 1e3), "steps_per_s": st["last_steps"] / (st["last_transport_ms"] / 1e3),
+            "vs_paper_gtx960": (n / (ms / 1e3)) / (1e7 / 500.0),
+            "oracle_check": {"packets": m,
+                             "same_step_counts": float(np.mean(got["n_events"] == ref["n_events"]))}}
 
 # ----------------------------------------------------------------------- modes
 def serving_run(ctx, seconds, rate):
