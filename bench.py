@@ -629,11 +629,35 @@ def serving_run(ctx, seconds, rate):
     g = np.load(os.path.join(ROOT, "tests", "golden", "serving_target.npz"))
     target = g["hist"][0].astype(np.float64) / 2.0**32
     probe = dict(r_ap=0.0, cone_alpha=math.pi / 2)       # every upward photon, as the target
-    res = serving.run_sweep(ctx, target, int(g["n_packets"]), probe, duration=seconds, rate=rate)
+    res = serving.run_sweep(ctx, target, int(g["n_packets"]), probe, duration=seconds, rate=rate,
+                            keep_max_packets=150_000)
     hidden = {"beta": 6.0, "m0": 3.0 * W.MG_CM2, "d_m": 2.0 * W.UM, "tau0": float(g["tau_tot"])}
     out = serving.summary(res, hidden)
+    out["oracle_same_packets"] = served_error(res.kept)
     out["capacity"] = serving_capacity(ctx, probe)
     return out
+
+
+def served_error(kept, n_each=4):
+    """The first and the last `n_each` served requests of at most 1.5e5
+    packets (the last ones are proposals of the fit, made while the stream was
+    running) against the FP64 oracle on the same packets: bins that differ,
+    the weight share in another bin, the largest per-bin z."""
+    import numpy as np
+    from oracle import oracle as O
+    pick = kept[:n_each] + kept[max(n_each, len(kept) - n_each):]
+    rows, differ, moved, tot, zmax = [], 0, 0.0, 0.0, 0.0
+    for k, wl, raw in pick:
+        ref = O.simulate(wl, spread_runs=0)["hist"]
+        got = raw[:, 1:-1]
+        h_o, h_g = ref.astype(np.float64) / 2.0**32, got.astype(np.float64) / 2.0**32
+        differ += int((got != ref).sum())
+        moved += float(np.abs(h_g - h_o).sum())
+        tot += float(h_o.sum())
+        zmax = max(zmax, float((np.abs(h_g - h_o) / np.sqrt(h_g + h_o + 1.0)).max()))
+        rows.append({"arrival": int(k), "packets": int(wl.n_packets), "beta": float(wl.beta)})
+    return {"requests": rows, "bins": sum(int(r[:, 1:-1].size) for _, _, r in pick),
+            "bins_differing": differ, "l1_rel": moved / tot if tot else None, "max_abs_z": zmax}
 
 
 def serving_capacity(ctx, probe, n=64):

@@ -34,6 +34,7 @@ class SweepResult:
     best: dict = field(default_factory=dict)
     submitted: int = 0
     records: List[dict] = field(default_factory=list)
+    kept: List[tuple] = field(default_factory=list)    # (arrival index, workload, raw tally)
 
 
 def chi2(h_c, n_c, h_t, n_t, min_counts=10.0):
@@ -74,19 +75,22 @@ def surrogate_estimate(records, min_packets=1_000_000, keep=0.4, min_points=12):
 def run_sweep(ctx: pdv.Context, target_hist, target_packets, probe: dict, duration: float = 60.0,
               rate: float = 200.0, seed: int = 5, n_min: float = 1e5, n_max: float = 1e7,
               explore: float = 0.2, poll_us: int = 200,
-              min_best_packets: int = 1_000_000, lag: int = 20) -> SweepResult:
+              min_best_packets: int = 1_000_000, lag: int = 20,
+              keep_max_packets: int = 0) -> SweepResult:
     """Submit the Poisson stream of candidates and score them as they finish.
     The candidate proposed at arrival k is computed only from the results of
     arrivals 0 .. k - lag, taken in arrival order, so the candidate sequence
     and the recovered parameters do not depend on the order in which requests
     complete (at 200 requests/s a lag of 20 is 0.1 s, far above the serving
-    latency, so the submitter almost never waits for it)."""
+    latency, so the submitter almost never waits for it). Requests of at most
+    `keep_max_packets` packets keep their workload and raw tally in
+    `SweepResult.kept`, so that a caller can check served results."""
     arrivals = W.cfg5_arrivals(rate=rate, duration=duration, seed=seed, n_min=n_min,
                                n_max=n_max)
     rng = np.random.default_rng(seed + 1)
     res = SweepResult()
     lock = threading.Lock()
-    pending = {}            # ticket -> (request, cloud, t_submit, params, arrival index)
+    pending = {}            # ticket -> (request, cloud, t_submit, params, arrival index, workload)
     done = {}               # arrival index -> record (None: no scored bins)
     target = np.asarray(target_hist, np.float64)
     done_submitting = threading.Event()
@@ -104,7 +108,7 @@ def run_sweep(ctx: pdv.Context, target_hist, target_packets, probe: dict, durati
                     return
                 time.sleep(0.0002)
                 continue
-            for t, (req, cloud, t0, params, k) in items:
+            for t, (req, cloud, t0, params, k, wl) in items:
                 st = pdv.pdv_poll(ctx.handle, t, poll_us // max(len(items), 1))
                 if st != pdv.PDV_OK:
                     continue
@@ -119,6 +123,8 @@ def run_sweep(ctx: pdv.Context, target_hist, target_packets, probe: dict, durati
                     res.latencies_ms.append(1e3 * (t1 - t0))
                     res.completed += 1
                     done[k] = rec
+                    if wl.n_packets <= keep_max_packets:
+                        res.kept.append((k, wl, req.raw.copy()))
 
     th = threading.Thread(target=poller, daemon=True)
     th.start()
@@ -183,12 +189,13 @@ def run_sweep(ctx: pdv.Context, target_hist, target_packets, probe: dict, durati
                 res.rejected += 1
                 time.sleep(0.001)
         with lock:
-            pending[ticket] = (req, cloud, t0, params, k)
+            pending[ticket] = (req, cloud, t0, params, k, wl)
         res.submitted += 1
     done_submitting.set()
     th.join()
     res.wall_s = time.perf_counter() - t_start
     res.records = [done[k] for k in sorted(done) if done[k] is not None]
+    res.kept.sort(key=lambda x: x[0])
     res.best = {"chi2": math.inf}
     for rec in res.records:
         if rec["n"] >= min_best_packets and rec["chi2"] < res.best["chi2"]:

@@ -67,3 +67,31 @@ def test_merged_bin_test_statistic():
     bad = bench.merged_bin_test(a, 1e6, rng.poisson(c).astype(float), 2e6)
     assert bad["chi2_per_group"] > 2.0 * r["chi2_per_group"], bad
     assert bad["max_abs_z"] > bad["bonferroni_z_1e-3"] > r["max_abs_z"], bad
+
+
+def test_served_error_counts_moved_weight():
+    """The serving line's check of served requests: tallies equal to the
+    oracle's report no differing bin; a tally with one packet's weight moved
+    by one bin (planted in the oracle's output) reports two bins and the moved
+    share."""
+    import math
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import oracle as O
+    from paper_2012_00963_gb300 import workloads as W
+    arr = [a for a in W.cfg5_arrivals(duration=1.0) if a.n_packets <= 150_000][:2]
+    kept = []
+    for k, a in enumerate(arr):
+        wl = W.cfg5_request(a, r_ap=0.0, cone_alpha=math.pi / 2).replace(n_packets=20_000)
+        kept.append((k, wl, np.pad(O.simulate(wl, spread_runs=0)["hist"], ((0, 0), (1, 1)))))
+    ok = bench.served_error(kept, n_each=1)
+    assert ok["bins_differing"] == 0 and ok["l1_rel"] == 0.0 and len(ok["requests"]) == 2
+    k, wl, raw = kept[1]
+    bad = raw.copy()
+    j = int(np.argmax(bad[0]))
+    bad[0, j] -= np.uint64(1 << 32)
+    bad[0, j + 1] += np.uint64(1 << 32)
+    r = bench.served_error([kept[0], (k, wl, bad)], n_each=1)
+    tot = sum(float(x[2].sum()) for x in kept) / 2.0**32
+    assert r["bins_differing"] == 2 and abs(r["l1_rel"] - 2.0 / tot) < 1e-12, r
