@@ -43,7 +43,9 @@ typedef enum {
   PDV_EAGAIN = -4,       /* admission refused: not enough device memory/slots */
   PDV_ENOTREADY = -5,    /* request still running (pdv_poll)                  */
   PDV_ETIMEOUT = -6,     /* a bounded wait ran out                            */
-  PDV_ECANCELLED = -7    /* request cancelled                                 */
+  PDV_ECANCELLED = -7,   /* request cancelled                                 */
+  PDV_EDEBUG = -8        /* libpdv_debug.so only: an index check failed during
+                            the call; the access was skipped (pdv_debug_get)  */
 } pdv_status;
 
 enum { PDV_SURFACE_UNIFORM_THETA = 0, PDV_SURFACE_LAMBERT = 1, PDV_SURFACE_SPECULAR = 2 };
@@ -76,6 +78,13 @@ enum { PDV_PREC_FP32 = 0, PDV_PREC_FP64 = 1 };
  * and random directions reach it with a probability of about 1e-9, so this flag
  * is how tests exercise it. Exact free paths only (n_layers == 0). */
 #define PDV_TEST_HORIZONTAL_LAUNCH 0x10u
+
+/* Test hook of the debug build (libpdv_debug.so, compiled with PDV_DEBUG):
+ * the transport evaluates one index check at one past the end of the
+ * request's histogram, without the access, so the call returns PDV_EDEBUG
+ * with a record at PDV_DEBUG_SITE_SELFTEST. The release library refuses the
+ * flag (PDV_EINVAL). */
+#define PDV_TEST_DEBUG_CHECK 0x20u
 
 /* Optional device allocator (NULL: cudaMallocAsync/cudaFreeAsync on the
  * context stream). Both callbacks are called from library threads. */
@@ -409,6 +418,63 @@ typedef struct {
 pdv_status pdv_extract_peaks(pdv_ctx* ctx, const double* spectra, int n_spectra, int n_bins,
                              double v_lo, double v_hi, double v_fs, const pdv_peak_opts* opts,
                              uint32_t flags, pdv_peak* out);
+
+/* ---------------------------------------------------------------- debug build
+ *
+ * libpdv_debug.so is the same library compiled with PDV_DEBUG. Its transport,
+ * layer-stepping and normalisation kernels check every index into the staged
+ * tables, the tallies and the per-packet outputs before the access. A failed
+ * check skips the access and records itself in a device word; it never traps,
+ * so the context stays usable. pdv_simulate_spectrum, pdv_simulate_batch and
+ * pdv_simulate_spectrum_static read the word after their kernels finish and
+ * return PDV_EDEBUG while it holds a failure (until pdv_debug_get resets it).
+ * The release library (libpdv.so) compiles the checks out. */
+enum {
+  PDV_DEBUG_SITE_NONE = 0,
+  PDV_DEBUG_SITE_MASS_GUIDE = 1,   /* guide of the velocity table            */
+  PDV_DEBUG_SITE_MASS_NODE = 2,    /* velocity table nodes (S_j, slopes)     */
+  PDV_DEBUG_SITE_PHASE_GUIDE = 3,  /* guide of the phase CDF                 */
+  PDV_DEBUG_SITE_PHASE_NODE = 4,   /* phase CDF nodes, angles, (cos, sin)    */
+  PDV_DEBUG_SITE_TURN = 5,         /* table of (cos, sin) of 2 pi j / 1024   */
+  PDV_DEBUG_SITE_SNAPSHOT = 6,     /* snapshot times and their order         */
+  PDV_DEBUG_SITE_HISTOGRAM = 7,    /* tally rows                             */
+  PDV_DEBUG_SITE_PACKET = 8,       /* per-packet records                     */
+  PDV_DEBUG_SITE_SELFTEST = 9      /* PDV_TEST_DEBUG_CHECK                   */
+};
+
+typedef struct {
+  int32_t debug_build;             /* 1: libpdv_debug.so; 0: the release library
+                                      (the other fields are then 0)          */
+  uint32_t site;                   /* PDV_DEBUG_SITE_* of the first failed check */
+  uint64_t violations;             /* failed checks since the last reset     */
+  int64_t index;                   /* the first failed check: its index ...  */
+  int64_t bound;                   /* ... and the size it was checked against */
+} pdv_debug_info;
+
+/* Read (and with reset != 0 clear) the failed-check record of the context's
+ * device. Waits for the context's stream first. */
+pdv_status pdv_debug_get(pdv_ctx* ctx, pdv_debug_info* out, int reset);
+
+/* One vertex of a packet's path at the request's first snapshot time t
+ * (Section II.B steps (1)-(6)): position (m), the velocity coordinate z / t
+ * of the vertex (m/s; 0 at the probe plane), the direction after the vertex,
+ * and what happened there: 0 launch at the probe plane, 1 particle scatter,
+ * 2 free surface, 3 escape (at the probe plane), 4 absorbed by a particle or
+ * dropped by the roulette. event: the Philox event counter of the vertex. */
+typedef struct {
+  double x, y, z, v, ux, uy, uz;
+  int32_t kind;
+  uint32_t event;
+} pdv_trace_vertex;
+
+/* libpdv_debug.so only (the release library returns PDV_EINVAL): the next
+ * pdv_simulate_spectrum on this context that asks for per-packet records
+ * (out_packets) also writes the paths of its first n_trace packets to
+ * out[n_trace][max_vertices] (host), in FP32 or FP64 as the request's
+ * precision; unused slots get kind -1. Exact free paths only (n_layers == 0).
+ * n_trace in 1..65536, max_vertices in 1..4096; n_trace = 0 disarms. */
+pdv_status pdv_debug_set_trace(pdv_ctx* ctx, int n_trace, int max_vertices,
+                               pdv_trace_vertex* out);
 
 #ifdef __cplusplus
 }

@@ -2,6 +2,10 @@
 
 Translation units are compiled in parallel into ``_build/`` and linked into
 ``paper_2012_00963_gb300/libpdv.so``. Only one ``-gencode`` target is built.
+The debug library ``libpdv_debug.so`` is the same sources compiled with
+``-DPDV_DEBUG`` (index checks in the kernels, path traces) into
+``_build/debug/``; ``build(debug=True)`` makes it, ``build_all()`` makes both
+in one parallel compile.
 """
 from __future__ import annotations
 
@@ -16,6 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpdv.so")
+LIB_DEBUG = os.path.join(PKG, "libpdv_debug.so")
 SOURCES = ["tables.cu", "transport.cu", "spectra.cu", "stepping.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Host code is compiled without FMA contraction (gcc contracts by default on
@@ -43,38 +48,65 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile (if needed) and return the path of libpdv.so."""
+def _variants(debug_list, force):
     deps = _deps()
-    if not force and not _stale(LIB, deps):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    out = []
+    for debug in debug_list:
+        lib = LIB_DEBUG if debug else LIB
+        if force or _stale(lib, deps):
+            out.append((debug, lib))
+    return out
+
+
+def _build(debug_list, force: bool = False, verbose: bool = False):
+    todo = _variants(debug_list, force)
+    if not todo:
+        return
     cc = nvcc()
 
-    def one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [cc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def one(job):
+        debug, src = job
+        d = os.path.join(BUILD, "debug") if debug else BUILD
+        os.makedirs(d, exist_ok=True)
+        obj = os.path.join(d, os.path.splitext(src)[0] + ".o")
+        cmd = [cc] + ARCH + FLAGS + (["-DPDV_DEBUG"] if debug else []) + \
+            ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s" % (src, r.stderr))
-        return obj, r.stderr
+        return debug, obj, r.stderr
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        results = list(ex.map(one, SOURCES))
-    objs = [o for o, _ in results]
-    tmp = LIB + ".tmp.%d" % os.getpid()
-    r = subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("link failed:\n%s" % r.stderr)
-    os.replace(tmp, LIB)
+    jobs = [(debug, src) for debug, _ in todo for src in SOURCES]
+    with cf.ThreadPoolExecutor(len(jobs)) as ex:
+        results = list(ex.map(one, jobs))
+    for debug, lib in todo:
+        objs = [o for dbg, o, _ in results if dbg == debug]
+        tmp = lib + ".tmp.%d" % os.getpid()
+        r = subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True,
+                           text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n%s" % r.stderr)
+        os.replace(tmp, lib)
     if verbose:
-        for _, err in results:
+        for _, _, err in results:
             print(err)
-    return LIB
+
+
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile (if needed) and return the path of libpdv.so (libpdv_debug.so
+    with debug=True)."""
+    _build([debug], force, verbose)
+    return LIB_DEBUG if debug else LIB
+
+
+def build_all(force: bool = False, verbose: bool = False) -> tuple:
+    """Compile both libraries (release and debug) in one parallel pass."""
+    _build([False, True], force, verbose)
+    return LIB, LIB_DEBUG
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build_all(force="--force" in sys.argv, verbose="-v" in sys.argv))

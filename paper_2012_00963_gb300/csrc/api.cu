@@ -120,6 +120,10 @@ struct pdv_ctx {
   char* static_scratch = nullptr;
   std::vector<double> static_ts;
   std::vector<int> static_idx;
+  // debug build: the path trace armed by pdv_debug_set_trace for the next
+  // synchronous spectrum call with per-packet records
+  pdv_trace_vertex* trace_out = nullptr;
+  int trace_n = 0, trace_max = 0;
 };
 
 static size_t pin_class(size_t bytes) {
@@ -201,6 +205,7 @@ static cudaError_t static_scratch_lookup(char** out);
 
 extern "C" pdv_status pdv_ctx_create(int device, void* cuda_stream, const pdv_allocator* alloc,
                                      pdv_ctx** out) {
+  NvtxRange nvtx_range("pdv_ctx_create");
   if (!out) return fail(PDV_EINVAL, "out is NULL");
   *out = nullptr;
   int ndev = 0;
@@ -271,6 +276,7 @@ extern "C" pdv_status pdv_ctx_create(int device, void* cuda_stream, const pdv_al
 static void serving_stop(pdv_ctx* c);
 
 extern "C" pdv_status pdv_ctx_destroy(pdv_ctx* c) {
+  NvtxRange nvtx_range("pdv_ctx_destroy");
   if (!c) return fail(PDV_EINVAL, "ctx is NULL");
   enter(c->device);
   serving_stop(c);
@@ -357,6 +363,7 @@ static int next_pow2(int x) {
 }
 
 extern "C" pdv_status pdv_create_cloud(pdv_ctx* c, const pdv_cloud_desc* d, pdv_cloud** out) {
+  NvtxRange nvtx_range("pdv_create_cloud");
   if (!c || !d || !out) return fail(PDV_EINVAL, "NULL argument");
   *out = nullptr;
   double v_bot = 0, v_top = 0;
@@ -431,6 +438,7 @@ extern "C" pdv_status pdv_create_cloud(pdv_ctx* c, const pdv_cloud_desc* d, pdv_
 
 extern "C" pdv_status pdv_set_phase_table(pdv_cloud* cl, int n, const double* theta,
                                           const double* p, double q_ext, double albedo) {
+  NvtxRange nvtx_range("pdv_set_phase_table");
   if (!cl || !theta || !p) return fail(PDV_EINVAL, "NULL argument");
   if (n < 2 || n > kMaxPhase) return fail(PDV_EINVAL, "phase table needs 2..%d angles", kMaxPhase);
   if (std::fabs(theta[0]) > 1e-12 || std::fabs(theta[n - 1] - M_PI) > 1e-12)
@@ -574,6 +582,7 @@ extern "C" pdv_status pdv_mie_table(pdv_ctx* c, double m_re, double m_im, double
                                     double d_median_um, double sigma_ln, int n_size, int n_angle,
                                     double* theta, double* p, double* q_ext, double* albedo,
                                     double* g) {
+  NvtxRange nvtx_range("pdv_mie_table");
   if (!c || !theta || !p) return fail(PDV_EINVAL, "NULL argument");
   if (!(m_re > 0) || !(m_im >= 0)) return fail(PDV_EINVAL, "need Re m > 0 and Im m >= 0");
   if (!(wavelength_nm > 0) || !(d_median_um > 0) || !(sigma_ln >= 0) || sigma_ln > 3)
@@ -625,8 +634,11 @@ static pdv_status validate_request(const pdv_request* r) {
   if (!r->out_spectrum) return fail(PDV_EINVAL, "out_spectrum is required");
   if (r->out_packets && r->n_packets > ((r->flags & PDV_OUT_DEVICE) ? (1ull << 28) : (1ull << 26)))
     return fail(PDV_EINVAL, "packet dumps need n_packets <= 2^26 (2^28 into device memory)");
-  if (r->flags & ~(PDV_OUT_DEVICE | PDV_PER_DV | PDV_IMPLICIT_CAPTURE | PDV_TEST_HORIZONTAL_LAUNCH))
+  if (r->flags & ~(PDV_OUT_DEVICE | PDV_PER_DV | PDV_IMPLICIT_CAPTURE | PDV_TEST_HORIZONTAL_LAUNCH |
+                   PDV_TEST_DEBUG_CHECK))
     return fail(PDV_EINVAL, "unknown flags");
+  if ((r->flags & PDV_TEST_DEBUG_CHECK) && !kDebugBuild)
+    return fail(PDV_EINVAL, "PDV_TEST_DEBUG_CHECK needs the debug build (libpdv_debug.so)");
   if (r->n_layers && (r->flags & PDV_TEST_HORIZONTAL_LAUNCH))
     return fail(PDV_EINVAL, "the horizontal launch runs with exact free paths only (n_layers = 0)");
   if (r->reserved) return fail(PDV_EINVAL, "reserved must be 0");
@@ -668,6 +680,8 @@ static SetDesc make_set(const pdv_request* r) {
   d.max_events = r->max_events ? r->max_events : 1000000u;
   d.implicit = (r->flags & PDV_IMPLICIT_CAPTURE) ? 1u : 0u;
   d.launch_horizontal = (r->flags & PDV_TEST_HORIZONTAL_LAUNCH) ? 1 : 0;
+  d.debug_check = (r->flags & PDV_TEST_DEBUG_CHECK) ? 1 : 0;
+  d.t_trace = r->t_snap_us[0] * 1e-6;
   d.absorb_gate = d.implicit ? 0u : d.omega_q;
   d.R_q = (unsigned long long)std::floor(cl->desc.reflectivity * kTwo32 + 0.5);
   d.seed = r->seed;
@@ -790,6 +804,21 @@ static pdv_status f32_geometry(pdv_ctx* c, size_t smem, int hist_mode, bool dump
   return PDV_OK;
 }
 
+// Debug build: after a synchronous call's kernels have finished, a failed
+// index check (left in the device words until pdv_debug_get resets them)
+// turns the call's status into PDV_EDEBUG. The release build has no checks.
+static pdv_status debug_after(pdv_ctx* c) {
+  if (!kDebugBuild) return PDV_OK;
+  DebugWord a{}, b{};
+  CK(transport_debug_io(&a, false, c->stream));
+  CK(stepping_debug_io(&b, false, c->stream));
+  const DebugWord& f = a.violations ? a : b;
+  if (!f.violations) return PDV_OK;
+  return fail(PDV_EDEBUG, "index check failed: site %u, index %lld, bound %lld (%llu failed checks)",
+              f.site, (long long)f.index, (long long)f.bound,
+              (unsigned long long)(a.violations + b.violations));
+}
+
 // Enqueue the transport of one request whose buffers are at `base`
 // (descriptor already uploaded). Returns the number of kernels launched.
 static pdv_status enqueue_transport(pdv_ctx* c, const pdv_request* r, const SetDesc& d,
@@ -865,6 +894,7 @@ static pdv_status enqueue_transport(pdv_ctx* c, const pdv_request* r, const SetD
 }
 
 extern "C" pdv_status pdv_simulate_spectrum(pdv_ctx* c, const pdv_request* r) {
+  NvtxRange nvtx_range("pdv_simulate_spectrum");
   if (!c) return fail(PDV_EINVAL, "ctx is NULL");
   pdv_status s = validate_request(r);
   if (s != PDV_OK) return s;
@@ -885,6 +915,22 @@ extern "C" pdv_status pdv_simulate_spectrum(pdv_ctx* c, const pdv_request* r) {
   d.hist = (unsigned long long*)(base + b.o_hist);
   d.cnt = (unsigned long long*)(base + b.o_cnt);
   d.packets = r->out_packets ? (dev_out ? r->out_packets : (pdv_packet_record*)(base + b.o_pk)) : nullptr;
+  // debug build: the armed path trace of the first packets
+  struct TraceGuard {
+    pdv_ctx* c; void* p; cudaStream_t st;
+    ~TraceGuard() { if (p) ctx_free(c, p, st); }
+  } tguard{c, nullptr, st};
+  int n_tr = 0;
+  if (c->trace_n > 0 && r->out_packets && !r->n_layers) {
+    n_tr = (int)std::min<uint64_t>((uint64_t)c->trace_n, r->n_packets);
+    const size_t tb = sizeof(pdv_trace_vertex) * (size_t)n_tr * (size_t)c->trace_max;
+    tguard.p = ctx_alloc(c, tb, st);
+    if (!tguard.p) return fail(PDV_ENOMEM, "path trace allocation of %zu bytes failed", tb);
+    CK(cudaMemsetAsync(tguard.p, 0xFF, tb, st));            // kind -1 in every unused slot
+    d.trace = (pdv_trace_vertex*)tguard.p;
+    d.n_trace = n_tr;
+    d.max_vtx = c->trace_max;
+  }
   std::vector<double> ts(time_words(r->n_snap));
   fill_times(r, ts.data());
   double* spec = dev_out ? r->out_spectrum : (double*)(base + b.o_spec);
@@ -900,12 +946,18 @@ extern "C" pdv_status pdv_simulate_spectrum(pdv_ctx* c, const pdv_request* r) {
   CK(cudaMemsetAsync(base + b.o_ctr, 0, sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(base + b.o_cnt, 0, sizeof(unsigned long long) * C_NCOUNT, st));
   CK(cudaMemsetAsync(base + b.o_hist, 0, sizeof(unsigned long long) * hist_row(r->n_bins) * r->n_snap, st));
-  s = enqueue_transport(c, r, d, base, b, st, true);
-  if (s != PDV_OK) return s;
-  launch_normalise((const SetDesc*)(base + b.o_set), 1, (double* const*)(base + b.o_ptr_spec),
-                   (pdv_counters* const*)(base + b.o_ptr_cnt),
-                   (unsigned long long* const*)(base + b.o_ptr_raw),
-                   (const unsigned*)(base + b.o_flags), r->n_snap, st);
+  {
+    NvtxRange nvtx_launch("pdv transport launch");
+    s = enqueue_transport(c, r, d, base, b, st, true);
+    if (s != PDV_OK) return s;
+  }
+  {
+    NvtxRange nvtx_norm("pdv normalise");
+    launch_normalise((const SetDesc*)(base + b.o_set), 1, (double* const*)(base + b.o_ptr_spec),
+                     (pdv_counters* const*)(base + b.o_ptr_cnt),
+                     (unsigned long long* const*)(base + b.o_ptr_raw),
+                     (const unsigned*)(base + b.o_flags), r->n_snap, st);
+  }
   c->launches += 1;
   CK(cudaGetLastError());
   if (!dev_out) {
@@ -918,13 +970,22 @@ extern "C" pdv_status pdv_simulate_spectrum(pdv_ctx* c, const pdv_request* r) {
   CK(cudaMemcpyAsync(&ev, base + b.o_cnt + sizeof(unsigned long long) * C_EVENTS, sizeof ev, cudaMemcpyDeviceToHost, st));
   if (r->n_layers)
     CK(cudaMemcpyAsync(&steps, base + b.o_steps, sizeof steps, cudaMemcpyDeviceToHost, st));
+  if (n_tr) {
+    const size_t row_b = sizeof(pdv_trace_vertex) * (size_t)c->trace_max;
+    CK(cudaMemcpyAsync(c->trace_out, tguard.p, row_b * n_tr, cudaMemcpyDeviceToHost, st));
+    if (n_tr < c->trace_n) memset((char*)c->trace_out + row_b * n_tr, 0xFF, row_b * (c->trace_n - n_tr));
+  }
   CK(cudaStreamSynchronize(st));
+  if (n_tr) {
+    c->trace_n = 0;                               // one call per arming
+    c->trace_out = nullptr;
+  }
   c->last_steps = steps;
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) c->last_transport_ms = ms;
   cudaGetLastError();
   c->last_events = ev;
-  return PDV_OK;
+  return debug_after(c);
 }
 
 // ------------------------------------------------------------------ batches
@@ -1124,6 +1185,7 @@ static pdv_status run_batch_f32(pdv_ctx* c, const pdv_request* rs, int n, bool t
 }
 
 extern "C" pdv_status pdv_simulate_batch(pdv_ctx* c, const pdv_request* rs, int n) {
+  NvtxRange nvtx_range("pdv_simulate_batch");
   if (!c || !rs || n < 1) return fail(PDV_EINVAL, "need a context and n >= 1 requests");
   for (int i = 0; i < n; ++i) {
     pdv_status s = validate_request(&rs[i]);
@@ -1142,7 +1204,8 @@ extern "C" pdv_status pdv_simulate_batch(pdv_ctx* c, const pdv_request* rs, int 
   if (f32.empty()) return PDV_OK;
   CK(enter(c->device));
   std::lock_guard<std::mutex> lk(c->mu);
-  return run_batch_f32(c, f32.data(), (int)f32.size(), true, nullptr);
+  const pdv_status s = run_batch_f32(c, f32.data(), (int)f32.size(), true, nullptr);
+  return s != PDV_OK ? s : debug_after(c);
 }
 
 // ------------------------------------------------------------------ issue-rate probe
@@ -1171,6 +1234,7 @@ __global__ void __launch_bounds__(256) k_issue_probe(int iters, float m, float a
 }  // namespace pdv
 
 extern "C" pdv_status pdv_measure_issue_rate(pdv_ctx* c, double seconds, double* out) {
+  NvtxRange nvtx_range("pdv_measure_issue_rate");
   if (!c || !out) return fail(PDV_EINVAL, "ctx and out must not be NULL");
   if (!(seconds > 0.0) || seconds > 10.0) return fail(PDV_EINVAL, "seconds must be in (0, 10]");
   std::lock_guard<std::mutex> lk(c->mu);
@@ -1262,6 +1326,7 @@ extern "C" pdv_status pdv_set_autotune_cache(pdv_ctx* c, const char* path) {
 }
 
 extern "C" pdv_status pdv_autotune(pdv_ctx* c, const pdv_request* rs, int n, pdv_tuning* out) {
+  NvtxRange nvtx_range("pdv_autotune");
   if (!c || !rs || n < 1) return fail(PDV_EINVAL, "need a context and n >= 1 requests");
   for (int i = 0; i < n; ++i) {
     pdv_status s = validate_request(&rs[i]);
@@ -1398,6 +1463,7 @@ struct LaunchSlot {
 
 static void finish_request(pdv_ctx* c, const std::shared_ptr<Request>& q) {
   // normalise and stage the outputs into pinned memory on the serving stream
+  NvtxRange nvtx_range("pdv serving normalise");
   const pdv_request& r = q->req;
   char* base = q->arena;
   const bool dev = (r.flags & PDV_OUT_DEVICE) != 0;
@@ -1513,6 +1579,7 @@ static void serving_loop(pdv_ctx* c) {
       std::this_thread::sleep_for(std::chrono::microseconds(50));
       continue;
     }
+    NvtxRange nvtx_launch("pdv serving launch");
     LaunchSlot& s = slots[free_slot];
     for (size_t k = 0; k < items.size(); ++k) {
       const auto& q = items[k].first;
@@ -1588,6 +1655,7 @@ static void serving_stop(pdv_ctx* c) {
 }
 
 extern "C" pdv_status pdv_submit(pdv_ctx* c, const pdv_request* r, pdv_ticket* out) {
+  NvtxRange nvtx_range("pdv_submit");
   if (!c || !out) return fail(PDV_EINVAL, "NULL argument");
   pdv_status s = validate_request(r);
   if (s != PDV_OK) return s;
@@ -1691,6 +1759,7 @@ extern "C" pdv_status pdv_set_serving_limits(pdv_ctx* c, int max_requests, uint6
 }
 
 extern "C" pdv_status pdv_poll(pdv_ctx* c, pdv_ticket t, uint32_t timeout_us) {
+  NvtxRange nvtx_range("pdv_poll");
   if (!c) return fail(PDV_EINVAL, "ctx is NULL");
   std::unique_lock<std::mutex> lk(c->smu);
   auto it = c->requests.find(t);
@@ -1772,6 +1841,7 @@ static size_t static_scratch_bytes(int n_snap, int n_bins) {
 }
 
 extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request* r) {
+  NvtxRange nvtx_range("pdv_simulate_spectrum_static");
   if (!c) return fail(PDV_EINVAL, "ctx is NULL");
   pdv_status s = validate_request(r);
   if (s != PDV_OK) return s;
@@ -1823,7 +1893,7 @@ extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request
   c->launches += 2;
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
-  return PDV_OK;
+  return debug_after(c);
 }
 
 // ------------------------------------------------------------------ spectrum model
@@ -1835,6 +1905,7 @@ static bool ss_set_valid(const pdv_ss_set& s) {
 
 extern "C" pdv_status pdv_ss_spectrum(pdv_ctx* c, const pdv_ss_set* sets, int n_sets, int n_bins,
                                       double v_lo, double v_hi, uint32_t flags, double* out) {
+  NvtxRange nvtx_range("pdv_ss_spectrum");
   if (!c) return fail(PDV_EINVAL, "ctx is NULL");
   if (n_sets < 0 || n_bins < 1) return fail(PDV_EINVAL, "n_sets must be >= 0 and n_bins >= 1");
   if (!(v_hi > v_lo) || !std::isfinite(v_lo) || !std::isfinite(v_hi))
@@ -1888,6 +1959,7 @@ extern "C" pdv_status pdv_ss_spectrum(pdv_ctx* c, const pdv_ss_set* sets, int n_
 extern "C" pdv_status pdv_extract_peaks(pdv_ctx* c, const double* spectra, int n_spectra,
                                         int n_bins, double v_lo, double v_hi, double v_fs,
                                         const pdv_peak_opts* opts, uint32_t flags, pdv_peak* out) {
+  NvtxRange nvtx_range("pdv_extract_peaks");
   if (!c || !opts) return fail(PDV_EINVAL, "ctx and opts must not be NULL");
   if (n_spectra < 0) return fail(PDV_EINVAL, "n_spectra must be >= 0");
   if (n_bins < 3 || n_bins > kPeakMaxBins) return fail(PDV_EINVAL, "n_bins must be in [3, %d]", kPeakMaxBins);
@@ -1956,5 +2028,45 @@ extern "C" pdv_status pdv_extract_peaks(pdv_ctx* c, const double* spectra, int n
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) c->last_model_ms = ms;
   cudaGetLastError();
+  return PDV_OK;
+}
+
+// ------------------------------------------------------------------ debug build
+extern "C" pdv_status pdv_debug_get(pdv_ctx* c, pdv_debug_info* out, int reset) {
+  if (!c || !out) return fail(PDV_EINVAL, "ctx and out must not be NULL");
+  memset(out, 0, sizeof *out);
+  out->debug_build = kDebugBuild ? 1 : 0;
+  if (!kDebugBuild) return PDV_OK;
+  CK(enter(c->device));
+  std::lock_guard<std::mutex> lk(c->mu);
+  CK(cudaStreamSynchronize(c->stream));
+  DebugWord a{}, b{};
+  CK(transport_debug_io(&a, reset != 0, c->stream));
+  CK(stepping_debug_io(&b, reset != 0, c->stream));
+  const DebugWord& f = a.violations ? a : b;
+  out->violations = a.violations + b.violations;
+  if (f.violations) {
+    out->site = f.site;
+    out->index = f.index;
+    out->bound = f.bound;
+  }
+  return PDV_OK;
+}
+
+extern "C" pdv_status pdv_debug_set_trace(pdv_ctx* c, int n_trace, int max_vertices,
+                                          pdv_trace_vertex* out) {
+  if (!c) return fail(PDV_EINVAL, "ctx is NULL");
+  if (!kDebugBuild) return fail(PDV_EINVAL, "path traces need the debug build (libpdv_debug.so)");
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (n_trace == 0) {
+    c->trace_n = 0;
+    c->trace_out = nullptr;
+    return PDV_OK;
+  }
+  if (n_trace < 1 || n_trace > 65536 || max_vertices < 1 || max_vertices > 4096 || !out)
+    return fail(PDV_EINVAL, "need 1 <= n_trace <= 65536, 1 <= max_vertices <= 4096 and an output array");
+  c->trace_out = out;
+  c->trace_n = n_trace;
+  c->trace_max = max_vertices;
   return PDV_OK;
 }

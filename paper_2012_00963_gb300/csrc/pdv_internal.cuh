@@ -12,11 +12,71 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "pdv.h"
 
 namespace pdv {
+
+// NVTX range for the lifetime of a scope (host code): API calls, launches,
+// normalisation and the serving loop show up by name in a profiler timeline.
+// Without a tool attached a push or pop is one indirect call.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// ------------------------------------------------------------- PDV_DEBUG
+// The debug build checks each index into the staged tables, the tallies and
+// the per-packet outputs before the access. A failed check skips the access
+// and records (site, index, bound) in its translation unit's device word; the
+// first failure's details are kept, later ones only counted. The release
+// build compiles every check to `true`.
+struct DebugWord {
+  unsigned long long violations;
+  long long index, bound;
+  unsigned site, pad;
+};
+
+#ifdef PDV_DEBUG
+constexpr bool kDebugBuild = true;
+static __device__ DebugWord g_debug_word;
+
+__device__ __noinline__ static bool debug_fail(long long i, long long n, unsigned site) {
+  if (atomicAdd(&g_debug_word.violations, 1ull) == 0ull) {
+    g_debug_word.index = i;
+    g_debug_word.bound = n;
+    g_debug_word.site = site;
+  }
+  return false;
+}
+#define PDV_IN(i, n, site)                                                          \
+  ((long long)(i) >= 0 && (long long)(i) < (long long)(n)                           \
+       ? true                                                                       \
+       : ::pdv::debug_fail((long long)(i), (long long)(n), (site)))
+
+// Host side: read (and optionally clear) this translation unit's word.
+static inline cudaError_t debug_word_io(DebugWord* out, bool reset, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_debug_word, sizeof(DebugWord), 0,
+                                            cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && reset) {
+    const DebugWord z{};
+    e = cudaMemcpyToSymbolAsync(g_debug_word, &z, sizeof(DebugWord), 0, cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+#else
+constexpr bool kDebugBuild = false;
+#define PDV_IN(i, n, site) ((void)sizeof((i) + (n)), true)   // nothing evaluated
+#endif
+
+// Load a[i] after the check; a failed check loads a[0] (every checked table
+// has at least one element).
+#define PDV_LD(a, i, n, site) (PDV_IN((i), (n), (site)) ? (a)[(i)] : (a)[0])
 
 constexpr unsigned long long kOneQ = 1ull << 62;     // S = 1 in 2^62 fixed point
 constexpr double kTwo62 = 4611686018427387904.0;
@@ -102,6 +162,12 @@ struct SetDesc {
   float lg_c_f, eps_f, dvds_c_f;      // v_fs ln2 / beta, exp(-beta (v_top/v_fs - 1)), v_fs E / beta
   double vb_d, E_d;                   // FP64 path: v_fs / beta and E = 1 - exp(-beta (v_top/v_fs - 1))
   uint2 rk[10];                       // Philox round keys of the seed (philox_round_key)
+  // debug build: path trace of the first n_trace packets at snapshot time t_trace
+  // (seconds), and the index check of PDV_TEST_DEBUG_CHECK
+  pdv_trace_vertex* trace;
+  int n_trace, max_vtx;
+  double t_trace;
+  int debug_check;
 };
 
 // ------------------------------------------------------------- Philox4x32-10
@@ -210,6 +276,10 @@ int transport_f32_max_smem();
 cudaError_t transport_preload();
 cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, bool impl,
                                     bool one, int* blocks);
+// The debug words of the transport and the layer-stepping translation units
+// (all zero in the release build).
+cudaError_t transport_debug_io(DebugWord* out, bool reset, cudaStream_t st);
+cudaError_t stepping_debug_io(DebugWord* out, bool reset, cudaStream_t st);
 
 cudaError_t build_mass_table(int kind, double beta, double v_fs, double v_bot, double v_top,
                              const double* d_prof_v, const double* d_prof_f, int prof_n,

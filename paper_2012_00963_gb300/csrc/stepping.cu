@@ -74,7 +74,9 @@ __device__ __forceinline__ long long mass_at(const unsigned long long* Sq, int n
   const unsigned long long q = (unsigned long long)P << 2;           // P 2^2 < 2^64
   const int j = (int)__umul64hi(q, (unsigned long long)n_v);         // floor(P n_v / 2^62)
   const unsigned long long frac = q * (unsigned long long)n_v;       // position in the node, 2^64 scale
-  return (long long)(Sq[j] + __umul64hi(Sq[j + 1] - Sq[j], frac));
+  const unsigned long long s0 = PDV_LD(Sq, j, n_v + 1, PDV_DEBUG_SITE_MASS_NODE);
+  const unsigned long long s1 = PDV_LD(Sq, j + 1, n_v + 1, PDV_DEBUG_SITE_MASS_NODE);
+  return (long long)(s0 + __umul64hi(s1 - s0, frac));
 }
 
 // p(theta) / max p at cos(theta) = mu, linear in theta between the nodes.
@@ -91,13 +93,15 @@ __device__ __forceinline__ float phase_ratio(float mu, const float* pn, const fl
     int lo = 0, hi = n_p - 2;                                         // largest thpi_i <= tpi
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (thpi[mid] <= tpi) lo = mid; else hi = mid - 1;
+      if (PDV_LD(thpi, mid, n_p, PDV_DEBUG_SITE_PHASE_NODE) <= tpi) lo = mid; else hi = mid - 1;
     }
     i = lo;
-    f = (tpi - thpi[i]) / (thpi[i + 1] - thpi[i]);
+    const float t0 = PDV_LD(thpi, i, n_p, PDV_DEBUG_SITE_PHASE_NODE);
+    f = (tpi - t0) / (PDV_LD(thpi, i + 1, n_p, PDV_DEBUG_SITE_PHASE_NODE) - t0);
   }
   f = fminf(fmaxf(f, 0.0f), 1.0f);
-  return fmaf(pn[i + 1] - pn[i], f, pn[i]);
+  const float p0 = PDV_LD(pn, i, n_p, PDV_DEBUG_SITE_PHASE_NODE);
+  return fmaf(PDV_LD(pn, i + 1, n_p, PDV_DEBUG_SITE_PHASE_NODE) - p0, f, p0);
 }
 
 // Section II.B step (4): acceptance-rejection for cos(theta), run by the whole
@@ -214,7 +218,8 @@ __device__ __forceinline__ bool step_passes(const StepConst& sc, const unsigned 
     float d = 0.0f;
     if (P > 0 && P < kOneP) {
       const int j = (int)__umul64hi((unsigned long long)P << 2, (unsigned long long)n_v);
-      d = u64_to_f(Sq[j + 1] - Sq[j]);
+      d = u64_to_f(PDV_LD(Sq, j + 1, n_v + 1, PDV_DEBUG_SITE_MASS_NODE) -
+                   PDV_LD(Sq, j, n_v + 1, PDV_DEBUG_SITE_MASS_NODE));
     }
     dtau = d * sc.tau_hv_dv;
   } else {
@@ -301,6 +306,8 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
   const uint2 key = make_uint2((unsigned)sd.seed, (unsigned)(sd.seed >> 32));
   const unsigned sid = sd.stream_id;
   const int n_bins = sd.n_bins, row = hist_row(sd.n_bins), n_snap = sd.n_snap;
+  const long long n_tally = (long long)n_snap * row;   // the debug build checks tallies against it
+  (void)n_tally;
   const float vP32 = sc.v_per_P * 4294967296.0f;           // m/s per unit of P >> 32
   const float vPd = sc.v_per_P * (float)(1ll << sc.shift_d);    // m/s per unit of dP >> shift_d
 
@@ -391,8 +398,10 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
             if (sd.ap_all) {
               // every snapshot time alike: one tally in row 0 (the
               // normalisation reads it for each time)
-              atomicAdd(&sd.hist[idx], W);                                  // Eq. 19
-              atomicAdd(&sd.hist[n_bins + 2], 1ull);
+              if (PDV_IN(idx, n_tally, PDV_DEBUG_SITE_HISTOGRAM))
+                atomicAdd(&sd.hist[idx], W);                                // Eq. 19
+              if (PDV_IN(n_bins + 2, n_tally, PDV_DEBUG_SITE_HISTOGRAM))
+                atomicAdd(&sd.hist[n_bins + 2], 1ull);
               dmask = n_snap >= 64 ? ~0ull : ((1ull << n_snap) - 1ull);
             } else {
               float x0, y0;
@@ -401,11 +410,13 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
               const float ax = fmaf(tx, sd.z_probe_f, x0), ay = fmaf(ty, sd.z_probe_f, y0);
               const float bx = fmaf(-tx, sd.v_top_f, Xx), by = fmaf(-ty, sd.v_top_f, Xy);
               for (int s = 0; s < n_snap; ++s) {
-                const float t = ts[s];
+                const float t = PDV_LD(ts, s, n_snap, PDV_DEBUG_SITE_SNAPSHOT);
                 const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
                 if (fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
-                  atomicAdd(&sd.hist[(size_t)s * row + idx], W);           // Eq. 19
-                  atomicAdd(&sd.hist[(size_t)s * row + n_bins + 2], 1ull);
+                  if (PDV_IN((long long)s * row + idx, n_tally, PDV_DEBUG_SITE_HISTOGRAM))
+                    atomicAdd(&sd.hist[(size_t)s * row + idx], W);         // Eq. 19
+                  if (PDV_IN((long long)s * row + n_bins + 2, n_tally, PDV_DEBUG_SITE_HISTOGRAM))
+                    atomicAdd(&sd.hist[(size_t)s * row + n_bins + 2], 1ull);
                   if (s < 64) dmask |= 1ull << s;
                 }
               }
@@ -526,7 +537,8 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
         rec.weight = W;
         rec.v_app = (double)vapp - (double)vcomp;
         rec.detect_mask = dmask;
-        sd.packets[pk - sd.packet_begin] = rec;
+        if (PDV_IN(pk - sd.packet_begin, sd.n_packets, PDV_DEBUG_SITE_PACKET))
+          sd.packets[pk - sd.packet_begin] = rec;
       }
       alive = false;
     }
@@ -544,6 +556,17 @@ __global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restric
 }
 
 }  // namespace
+
+cudaError_t stepping_debug_io(DebugWord* out, bool reset, cudaStream_t st) {
+#ifdef PDV_DEBUG
+  return debug_word_io(out, reset, st);
+#else
+  (void)reset;
+  (void)st;
+  *out = DebugWord{};
+  return cudaSuccess;
+#endif
+}
 
 size_t transport_step_smem(int n_v, int n_p, int n_snap, int phase_uniform) {
   return step_layout(n_v, n_p, n_snap, phase_uniform).bytes;

@@ -112,24 +112,14 @@ size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int
 }
 
 __device__ __forceinline__ int search_mass(const unsigned long long* Sq, const unsigned short* G,
-                                           int g_shift, int n_g, unsigned long long s) {
+                                           int g_shift, int n_g, int n_v, unsigned long long s) {
   unsigned kg = (unsigned)(s >> g_shift);
   if (kg > (unsigned)(n_g - 1)) kg = (unsigned)(n_g - 1);
-  int lo = G[kg], hi = G[kg + 1];
+  int lo = PDV_LD(G, kg, n_g + 1, PDV_DEBUG_SITE_MASS_GUIDE);
+  int hi = PDV_LD(G, kg + 1, n_g + 1, PDV_DEBUG_SITE_MASS_GUIDE);
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (Sq[mid] <= s) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ int search_phase(const unsigned* Cq, const unsigned short* Gp,
-                                            unsigned m) {
-  const unsigned c = m >> (24 - kGuidePhaseLog);
-  int lo = Gp[c], hi = Gp[c + 1];
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (Cq[mid] <= m) lo = mid; else hi = mid - 1;
+    if (PDV_LD(Sq, mid, n_v + 1, PDV_DEBUG_SITE_MASS_NODE) <= s) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -158,6 +148,25 @@ __device__ __forceinline__ void launch_position(unsigned long long pk, unsigned 
   x0 = rad * cp;
   y0 = rad * sp;
 }
+
+#ifdef PDV_DEBUG
+// Debug build: one vertex of a traced packet's path (pdv_debug_set_trace).
+__device__ __noinline__ static void trace_put(const SetDesc& sd, unsigned long long off,
+                                              unsigned& nv, double x, double y, double z, double v,
+                                              double ux, double uy, double uz, int kind,
+                                              unsigned ev) {
+  if (sd.trace == nullptr || off >= (unsigned long long)sd.n_trace) return;
+  if (nv < (unsigned)sd.max_vtx) {
+    pdv_trace_vertex e;
+    e.x = x; e.y = y; e.z = z; e.v = v;
+    e.ux = ux; e.uy = uy; e.uz = uz;
+    e.kind = kind;
+    e.event = ev;
+    sd.trace[off * (unsigned long long)sd.max_vtx + nv] = e;
+  }
+  ++nv;
+}
+#endif
 
 // Stage one set's tables (and a cleared private histogram) in shared memory.
 template <int HMODE>
@@ -237,6 +246,15 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
   const unsigned n_pk = (unsigned)sd.n_packets;    // at most 4e9 packets per set
   const float inv_tau = sd.inv_tau_f;
   const int n_bins = sd.n_bins, row = hist_row(sd.n_bins), n_snap = sd.n_snap;
+  // sizes of the staged tables and of the tally (the debug build checks against them)
+  const int n_p = sd.n_p;
+  const long long n_tally = (long long)tally_rows(n_snap, sd.ap_all) * row;
+#ifdef PDV_DEBUG
+  unsigned n_vtx = 0;                               // vertices of this lane's traced packet
+#else
+  (void)n_p;
+  (void)n_tally;
+#endif
 
   // ---- warp loop
   // The warp owns a chunk [pool_next, pool_end) of packet offsets and has the
@@ -290,6 +308,16 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
         if (DUMP) { nsca = 0; nsurf = 0; dmask = 0; }
         ++st_launch;
         alive = true;
+#ifdef PDV_DEBUG
+        if (sd.debug_check && pk == base_pk)     // PDV_TEST_DEBUG_CHECK: once per set
+          (void)PDV_IN(n_tally, n_tally, PDV_DEBUG_SITE_SELFTEST);
+        if (DUMP && sd.trace) {
+          float x0, y0;
+          launch_position(pk, sid, key, sd.r_beam_f, x0, y0);
+          n_vtx = 0;
+          trace_put(sd, pk - base_pk, n_vtx, x0, y0, sd.z_probe_f, 0.0, ux, uy, uz, 0, 0u);
+        }
+#endif
       }
       pool_next += take;
     }
@@ -324,9 +352,11 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
       const float q = fmaf(__uint2float_rn((unsigned)(sn >> 32)) * kTwoM30f, sd.eps_f, om);
       vn = fmaf(-sd.lg_c_f, __log2f(q), sd.v_fs_f);
     } else if (what == 0) {
-      const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sn);
-      const float fd = u64_to_f((unsigned long long)Sn - tb.Sq[j]);
-      vn = fmaf(fd, tb.w[j], fmaf((float)j, sd.dv_f, sd.v_bot_f));
+      const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, sd.n_v, (unsigned long long)Sn);
+      const float fd =
+          u64_to_f((unsigned long long)Sn - PDV_LD(tb.Sq, j, sd.n_v + 1, PDV_DEBUG_SITE_MASS_NODE));
+      vn = fmaf(fd, PDV_LD(tb.w, j, sd.n_v, PDV_DEBUG_SITE_MASS_NODE),
+                fmaf((float)j, sd.dv_f, sd.v_bot_f));
     }
     vn = what == 1 ? sd.v_top_f : (what == 2 ? sd.v_fs_f : (what == 3 ? vcur : vn));
     // lateral displacement in velocity units (x = x0 + t X)
@@ -343,8 +373,8 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
                               __uint2float_rn((unsigned)oms) * kTwoM62f);
         dvds = sd.dvds_c_f / fmaf(__uint2float_rn((unsigned)(sq >> 32)) * kTwoM30f, sd.eps_f, om);
       } else {
-        const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, (unsigned long long)Sq);
-        dvds = tb.w[j] * 4.611686018427388e18f;
+        const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, sd.n_v, (unsigned long long)Sq);
+        dvds = PDV_LD(tb.w, j, sd.n_v, PDV_DEBUG_SITE_MASS_NODE) * 4.611686018427388e18f;
       }
       const float len = tau * inv_tau * dvds;
       Xx = fmaf(ux, len, Xx);
@@ -360,8 +390,9 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
       if (sd.ap_all) {
         // Eq. 19 at every snapshot time alike (unlimited aperture): one
         // tally in row 0, which the normalisation reads for each time
-        atomicAdd(&tb.hist[idx], W);
-        atomicAdd(&tb.hist[n_bins + 2], 1ull);
+        if (PDV_IN(idx, n_tally, PDV_DEBUG_SITE_HISTOGRAM)) atomicAdd(&tb.hist[idx], W);
+        if (PDV_IN(n_bins + 2, n_tally, PDV_DEBUG_SITE_HISTOGRAM))
+          atomicAdd(&tb.hist[n_bins + 2], 1ull);
         if (DUMP) dmask = n_snap >= 64 ? ~0ull : ((1ull << n_snap) - 1ull);
       } else {
         float x0, y0;
@@ -386,25 +417,27 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
             int lo = 0, hi = n_snap;                   // first time >= t1
             while (lo < hi) {
               const int mid = (lo + hi) >> 1;
-              if (tb.ts[mid] < t1) lo = mid + 1; else hi = mid;
+              if (PDV_LD(tb.ts, mid, n_snap, PDV_DEBUG_SITE_SNAPSHOT) < t1) lo = mid + 1; else hi = mid;
             }
             s0 = lo > 0 ? lo - 1 : 0;
             hi = n_snap;                               // first time > t2
             while (lo < hi) {
               const int mid = (lo + hi) >> 1;
-              if (tb.ts[mid] <= t2) lo = mid + 1; else hi = mid;
+              if (PDV_LD(tb.ts, mid, n_snap, PDV_DEBUG_SITE_SNAPSHOT) <= t2) lo = mid + 1; else hi = mid;
             }
             s1 = lo < n_snap ? lo + 1 : n_snap;
           }
         }
         for (int s = s0; s < s1; ++s) {
-          const float t = tb.ts[s];
+          const float t = PDV_LD(tb.ts, s, n_snap, PDV_DEBUG_SITE_SNAPSHOT);
           const float dx = fmaf(t, bx, ax), dy = fmaf(t, by, ay);
           if (fmaf(dx, dx, dy * dy) <= sd.r_ap2_f) {
             // Eq. 19: tally the out-photon at its frequency shift
-            const int sr = tb.perm[s];
-            atomicAdd(&tb.hist[(size_t)sr * row + idx], W);
-            atomicAdd(&tb.hist[(size_t)sr * row + n_bins + 2], 1ull);
+            const int sr = PDV_LD(tb.perm, s, n_snap, PDV_DEBUG_SITE_SNAPSHOT);
+            if (PDV_IN((long long)sr * row + idx, n_tally, PDV_DEBUG_SITE_HISTOGRAM))
+              atomicAdd(&tb.hist[(size_t)sr * row + idx], W);
+            if (PDV_IN((long long)sr * row + n_bins + 2, n_tally, PDV_DEBUG_SITE_HISTOGRAM))
+              atomicAdd(&tb.hist[(size_t)sr * row + n_bins + 2], 1ull);
             if (DUMP && sr < 64) dmask |= 1ull << sr;
           }
         }
@@ -473,28 +506,38 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     {
       const unsigned m2 = r.z >> 8;
       const unsigned c = m2 >> (24 - kGuidePhaseLog);
-      int lo = tb.Gp[c], hi = part ? (int)tb.Gp[c + 1] : lo;
+      constexpr int n_gp = (1 << kGuidePhaseLog) + 1;
+      int lo = PDV_LD(tb.Gp, c, n_gp, PDV_DEBUG_SITE_PHASE_GUIDE);
+      int hi = part ? (int)PDV_LD(tb.Gp, c + 1, n_gp, PDV_DEBUG_SITE_PHASE_GUIDE) : lo;
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (tb.Cq[mid] <= m2) lo = mid; else hi = mid - 1;
+        if (PDV_LD(tb.Cq, mid, n_p, PDV_DEBUG_SITE_PHASE_NODE) <= m2) lo = mid; else hi = mid - 1;
       }
-      const unsigned c0 = tb.Cq[lo];
+      const unsigned c0 = PDV_LD(tb.Cq, lo, n_p, PDV_DEBUG_SITE_PHASE_NODE);
       const float fm = (float)(m2 - c0) + 0.5f;
       if (sd.angle_table) {
-        const float dp = sd.phase_uniform
-                             ? fm * rcp_approx((float)(tb.Cq[lo + 1] - c0)) * sd.dth_f
-                             : fm * tb.dthpi[lo] * 3.14159265f;
+        const float dp =
+            sd.phase_uniform
+                ? fm * rcp_approx((float)(PDV_LD(tb.Cq, lo + 1, n_p, PDV_DEBUG_SITE_PHASE_NODE) - c0)) *
+                      sd.dth_f
+                : fm * PDV_LD(tb.dthpi, lo, n_p, PDV_DEBUG_SITE_PHASE_NODE) * 3.14159265f;
         // theta' = 2 pi f with f = u / 4 = ((r1 >> 9) + 1/2) 2^-25: the nearest
         // table step j and the remainder, both exact in integers
         const int m1 = (int)(r.y >> 9);
         const int js = (m1 + (1 << 14)) >> 15;
         const float ds = (float)(2 * (m1 - (js << 15)) + 1) * kPi2m25f;
-        cos_sin_add(surf ? tb.turn[js] : tb.cs[lo], surf ? ds : dp, &ct, &st);
+        cos_sin_add(surf ? PDV_LD(tb.turn, js, kTurn, PDV_DEBUG_SITE_TURN)
+                         : PDV_LD(tb.cs, lo, n_p, PDV_DEBUG_SITE_PHASE_NODE),
+                    surf ? ds : dp, &ct, &st);
       } else {
         // theta_i / pi = i / (n_p - 1) on a uniform grid; linear inside the CDF bin
-        const float tp = sd.phase_uniform
-                             ? ((float)lo + fm * rcp_approx((float)(tb.Cq[lo + 1] - c0))) * sd.inv_nm1
-                             : fmaf(fm, tb.dthpi[lo], tb.thpi[lo]);
+        const float tp =
+            sd.phase_uniform
+                ? ((float)lo +
+                   fm * rcp_approx((float)(PDV_LD(tb.Cq, lo + 1, n_p, PDV_DEBUG_SITE_PHASE_NODE) - c0))) *
+                      sd.inv_nm1
+                : fmaf(fm, PDV_LD(tb.dthpi, lo, n_p, PDV_DEBUG_SITE_PHASE_NODE),
+                       PDV_LD(tb.thpi, lo, n_p, PDV_DEBUG_SITE_PHASE_NODE));
         sincospi_half_turns(surf ? 0.5f * u23f(r.y) : tp, &st, &ct);
       }
     }
@@ -545,6 +588,23 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
       atomicAdd(&s_cnt[C_TRUNCATED], 1ull);
       fate = 4;
     }
+#ifdef PDV_DEBUG
+    if (DUMP && alive && sd.trace && pk - base_pk < (unsigned long long)sd.n_trace) {
+      // the vertex that ended this flight, at the first snapshot time
+      float x0, y0;
+      launch_position(pk, sid, key, sd.r_beam_f, x0, y0);
+      const float t = (float)sd.t_trace;
+      if (esc) {
+        const float zt = sd.v_top_f * t;
+        trace_put(sd, pk - base_pk, n_vtx, fmaf(ux * iuz, sd.z_probe_f - zt, fmaf(t, Xx, x0)),
+                  fmaf(uy * iuz, sd.z_probe_f - zt, fmaf(t, Xy, y0)), sd.z_probe_f, 0.0, ux, uy, uz, 3,
+                  kev - 1);
+      } else if (ev) {
+        trace_put(sd, pk - base_pk, n_vtx, fmaf(t, Xx, x0), fmaf(t, Xy, y0), vn * t, vn, ux, uy, uz,
+                  surf ? 2 : (scat ? 1 : 4), kev - 1);
+      }
+    }
+#endif
     if (fate) {
       if (DUMP && sd.packets) {
         pdv_packet_record rec;
@@ -555,7 +615,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
         rec.weight = W;
         rec.v_app = (double)vapp - (double)vcomp;
         rec.detect_mask = dmask;
-        sd.packets[pk - base_pk] = rec;
+        if (PDV_IN(pk - base_pk, sd.n_packets, PDV_DEBUG_SITE_PACKET)) sd.packets[pk - base_pk] = rec;
       }
       alive = false;
     }
@@ -598,7 +658,8 @@ __device__ __forceinline__ void flush_set(const SetDesc& sd, const SmemTables& t
     const int nh = tally_rows(sd.n_snap, sd.ap_all) * hist_row(sd.n_bins);
     for (int i = threadIdx.x; i < nh; i += blockDim.x) {
       const unsigned long long v = tb.hist[i];
-      if (v) atomicAdd(&sd.hist[i], v);
+      if (v && PDV_IN(i, (long long)sd.n_snap * hist_row(sd.n_bins), PDV_DEBUG_SITE_HISTOGRAM))
+        atomicAdd(&sd.hist[i], v);
     }
   }
 }
@@ -735,7 +796,7 @@ __device__ int search_mass_d(const double* Sd, int n_v, double s) {
   int lo = 0, hi = n_v - 1;                      // largest j <= n_v-1 with Sd_j <= s
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (Sd[mid] <= s) lo = mid; else hi = mid - 1;
+    if (PDV_LD(Sd, mid, n_v + 1, PDV_DEBUG_SITE_MASS_NODE) <= s) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -765,6 +826,13 @@ __global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict
     unsigned long long W = 1ull << 32, dmask = 0;
     unsigned nev = 0, nsca = 0, nsurf = 0, fate = 0;
     ++st_launch;
+#ifdef PDV_DEBUG
+    if (sd.debug_check && ip == 0)                  // PDV_TEST_DEBUG_CHECK
+      (void)PDV_IN((long long)sd.n_snap * row, (long long)sd.n_snap * row, PDV_DEBUG_SITE_SELFTEST);
+    unsigned n_vtx = 0;
+    const double tt = sd.t_trace;
+    trace_put(sd, ip, n_vtx, x0, y0, sd.z_probe, 0.0, ux, uy, uz, 0, 0u);
+#endif
     for (unsigned k = 1; fate == 0; ++k) {
       r = philox4x32_10(make_uint4((unsigned)pk, (unsigned)(pk >> 32), k, sd.stream_id), key);
       const double tau = -log(u23d(r.x));
@@ -777,7 +845,8 @@ __global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict
           dvds = sd.vb_d * sd.E_d / (1.0 - S * sd.E_d);
         } else {
           const int j = search_mass_d(sd.Sd, sd.n_v, S);
-          dvds = sd.dv / (sd.Sd[j + 1] - sd.Sd[j]);
+          dvds = sd.dv / (PDV_LD(sd.Sd, j + 1, sd.n_v + 1, PDV_DEBUG_SITE_MASS_NODE) -
+                          PDV_LD(sd.Sd, j, sd.n_v + 1, PDV_DEBUG_SITE_MASS_NODE));
         }
         Xx += ux * tau * sd.inv_tau * dvds;
         Xy += uy * tau * sd.inv_tau * dvds;
@@ -797,12 +866,20 @@ __global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict
             const double t = sd.t_snap[s];
             const double dx = ax + t * bx, dy = ay + t * by;
             if (sd.ap_all || dx * dx + dy * dy <= sd.r_ap2) {
-              atomicAdd(&sd.hist[(size_t)s * row + idx], W);
-              atomicAdd(&sd.hist[(size_t)s * row + n_bins + 2], 1ull);
+              const long long n_h = (long long)sd.n_snap * row;
+              if (PDV_IN((long long)s * row + idx, n_h, PDV_DEBUG_SITE_HISTOGRAM))
+                atomicAdd(&sd.hist[(size_t)s * row + idx], W);
+              if (PDV_IN((long long)s * row + n_bins + 2, n_h, PDV_DEBUG_SITE_HISTOGRAM))
+                atomicAdd(&sd.hist[(size_t)s * row + n_bins + 2], 1ull);
               if (s < 64) dmask |= 1ull << s;
             }
           }
         }
+#ifdef PDV_DEBUG
+        trace_put(sd, ip, n_vtx, x0 + tt * Xx + ux / uz * (sd.z_probe - sd.v_top * tt),
+                  y0 + tt * Xy + uy / uz * (sd.z_probe - sd.v_top * tt), sd.z_probe, 0.0, ux, uy, uz,
+                  3, k);
+#endif
         atomicAdd(&s_cnt[C_ESCAPES], 1ull);
         atomicAdd(&s_cnt[C_W_ESCAPED], W);
         fate = 1;
@@ -837,6 +914,9 @@ __global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict
         }
         vapp += 0.5 * (uz - uz_old) * sd.v_fs;
         if (W == 0) fate = 3;
+#ifdef PDV_DEBUG
+        trace_put(sd, ip, n_vtx, x0 + tt * Xx, y0 + tt * Xy, sd.v_fs * tt, sd.v_fs, ux, uy, uz, 2, k);
+#endif
       } else {
         if (what == 0 && sd.expo) {
           // Eq. 20 inverted in closed form: v = v_fs (1 - ln(1 - S E) / beta)
@@ -845,7 +925,9 @@ __global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict
           Xy += uy / uz * (vn - vcur);
         } else if (what == 0) {
           const int j = search_mass_d(sd.Sd, sd.n_v, Sn);
-          vn = sd.v_bot + j * sd.dv + (Sn - sd.Sd[j]) / (sd.Sd[j + 1] - sd.Sd[j]) * sd.dv;
+          const double s0 = PDV_LD(sd.Sd, j, sd.n_v + 1, PDV_DEBUG_SITE_MASS_NODE);
+          const double s1 = PDV_LD(sd.Sd, j + 1, sd.n_v + 1, PDV_DEBUG_SITE_MASS_NODE);
+          vn = sd.v_bot + j * sd.dv + (Sn - s0) / (s1 - s0) * sd.dv;
           Xx += ux / uz * (vn - vcur);
           Xy += uy / uz * (vn - vcur);
         }
@@ -881,11 +963,13 @@ __global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict
           int lo = 0, hi = sd.n_p - 2;
           while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (sd.Cq[mid] <= m2) lo = mid; else hi = mid - 1;
+            if (PDV_LD(sd.Cq, mid, sd.n_p, PDV_DEBUG_SITE_PHASE_NODE) <= m2) lo = mid; else hi = mid - 1;
           }
-          const double th = sd.th_d[lo] + ((double)(m2 - sd.Cq[lo]) + 0.5) /
-                                              (double)(sd.Cq[lo + 1] - sd.Cq[lo]) *
-                                              (sd.th_d[lo + 1] - sd.th_d[lo]);
+          const unsigned c0 = PDV_LD(sd.Cq, lo, sd.n_p, PDV_DEBUG_SITE_PHASE_NODE);
+          const unsigned c1 = PDV_LD(sd.Cq, lo + 1, sd.n_p, PDV_DEBUG_SITE_PHASE_NODE);
+          const double th0 = PDV_LD(sd.th_d, lo, sd.n_p, PDV_DEBUG_SITE_PHASE_NODE);
+          const double th1 = PDV_LD(sd.th_d, lo + 1, sd.n_p, PDV_DEBUG_SITE_PHASE_NODE);
+          const double th = th0 + ((double)(m2 - c0) + 0.5) / (double)(c1 - c0) * (th1 - th0);
           const double ph = 2.0 * pi * u23d(r.w);
           const double ct = cos(th), st = sin(th), cp = cos(ph), sp = sin(ph);
           double nx, ny, nz;
@@ -904,6 +988,10 @@ __global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict
           ux = nx; uy = ny; uz = nz;
           ++nsca; ++st_scat;
         }
+#ifdef PDV_DEBUG
+        trace_put(sd, ip, n_vtx, x0 + tt * Xx, y0 + tt * Xy, vn * tt, vn, ux, uy, uz, scatter ? 1 : 4,
+                  k);
+#endif
       }
       if (fate == 0 && nev >= sd.max_events) {
         atomicAdd(&s_cnt[C_W_TRUNCATED], W);
@@ -920,7 +1008,7 @@ __global__ void __launch_bounds__(256) k_transport_f64(const SetDesc* __restrict
       rec.weight = W;
       rec.v_app = vapp;
       rec.detect_mask = dmask;
-      sd.packets[ip] = rec;
+      if (PDV_IN(ip, sd.n_packets, PDV_DEBUG_SITE_PACKET)) sd.packets[ip] = rec;
     }
   }
   atomicAdd(&s_cnt[C_LAUNCHED], st_launch);
@@ -946,6 +1034,9 @@ __global__ void k_normalise(const SetDesc* __restrict__ sets, double* const* spe
   if (s >= sd.n_snap) return;
   const int n_bins = sd.n_bins, row = hist_row(n_bins);
   // unlimited aperture: every time's tallies are those of row 0
+  if (!PDV_IN((long long)(sd.ap_all ? 0 : s) * row + row - 1, (long long)sd.n_snap * row,
+              PDV_DEBUG_SITE_HISTOGRAM))
+    return;
   const unsigned long long* h = sd.hist + (size_t)(sd.ap_all ? 0 : s) * row;
   double scale = 1.0 / (kTwo32 * (double)sd.norm_packets);
   if (flags[blockIdx.y] & PDV_PER_DV) scale *= sd.inv_dbin;
@@ -989,6 +1080,17 @@ __global__ void k_normalise(const SetDesc* __restrict__ sets, double* const* spe
       co[s] = c;
     }
   }
+}
+
+cudaError_t transport_debug_io(DebugWord* out, bool reset, cudaStream_t st) {
+#ifdef PDV_DEBUG
+  return debug_word_io(out, reset, st);
+#else
+  (void)reset;
+  (void)st;
+  *out = DebugWord{};
+  return cudaSuccess;
+#endif
 }
 
 void launch_normalise(const SetDesc* d_sets, int n_sets, double* const* d_spec,

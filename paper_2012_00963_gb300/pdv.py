@@ -4,6 +4,10 @@ Every step of the Monte Carlo runs in the library's CUDA kernels; there is no
 Python or CPU fallback. If the shared library cannot be built or loaded, or no
 CUDA device is present, the calls raise.
 
+The library is ``libpdv.so``; with the environment variable
+``PDV_LIBRARY=debug`` set before the first call, the process loads the debug
+build ``libpdv_debug.so`` instead (index checks in the kernels, path traces).
+
 Functions keep the C names (``pdv_ctx_create``, ``pdv_create_cloud``,
 ``pdv_set_phase_table``, ``pdv_simulate_spectrum``, ``pdv_simulate_batch``,
 ``pdv_submit``, ``pdv_poll``, ...). ``Context``, ``Cloud`` and
@@ -15,6 +19,7 @@ from __future__ import annotations
 
 import ctypes as C
 import math
+import os
 import threading
 from typing import Optional, Sequence
 
@@ -23,13 +28,16 @@ import numpy as np
 from . import build as _build
 
 PDV_OK, PDV_EINVAL, PDV_ENOMEM, PDV_ECUDA, PDV_EAGAIN = 0, -1, -2, -3, -4
-PDV_ENOTREADY, PDV_ETIMEOUT, PDV_ECANCELLED = -5, -6, -7
+PDV_ENOTREADY, PDV_ETIMEOUT, PDV_ECANCELLED, PDV_EDEBUG = -5, -6, -7, -8
 PDV_OUT_DEVICE, PDV_PER_DV, PDV_IN_DEVICE, PDV_IMPLICIT_CAPTURE = 0x1, 0x2, 0x4, 0x8
-PDV_TEST_HORIZONTAL_LAUNCH = 0x10
+PDV_TEST_HORIZONTAL_LAUNCH, PDV_TEST_DEBUG_CHECK = 0x10, 0x20
+DEBUG_SITES = ["none", "mass_guide", "mass_node", "phase_guide", "phase_node", "turn", "snapshot",
+               "histogram", "packet", "selftest"]
 PDV_PEAK_OK, PDV_PEAK_NO_PEAK, PDV_PEAK_NOT_MAX, PDV_PEAK_EDGE = 0, 1, 2, 3
 PDV_PREC_FP32, PDV_PREC_FP64 = 0, 1
 STATUS_NAMES = {0: "PDV_OK", -1: "PDV_EINVAL", -2: "PDV_ENOMEM", -3: "PDV_ECUDA",
-                -4: "PDV_EAGAIN", -5: "PDV_ENOTREADY", -6: "PDV_ETIMEOUT", -7: "PDV_ECANCELLED"}
+                -4: "PDV_EAGAIN", -5: "PDV_ENOTREADY", -6: "PDV_ETIMEOUT", -7: "PDV_ECANCELLED",
+                -8: "PDV_EDEBUG"}
 COUNTER_NAMES = [
     "launched", "events", "scatters", "surface_hits", "escapes", "detected",
     "w_detected", "w_under", "w_over", "w_escaped_undetected", "w_absorbed_particle",
@@ -41,7 +49,7 @@ ABI_FUNCTIONS = [
     "pdv_phase_hg", "pdv_mie_table", "pdv_simulate_spectrum", "pdv_simulate_batch",
     "pdv_autotune", "pdv_submit", "pdv_poll", "pdv_cancel", "pdv_simulate_spectrum_static",
     "pdv_ss_spectrum", "pdv_extract_peaks", "pdv_measure_issue_rate", "pdv_set_serving_limits",
-    "pdv_set_autotune_cache",
+    "pdv_set_autotune_cache", "pdv_debug_get", "pdv_debug_set_trace",
 ]
 
 
@@ -122,6 +130,18 @@ class pdv_peak_opts(C.Structure):
                 ("x_max", C.c_double)]
 
 
+class pdv_debug_info(C.Structure):
+    _fields_ = [("debug_build", C.c_int32), ("site", C.c_uint32), ("violations", C.c_uint64),
+                ("index", C.c_int64), ("bound", C.c_int64)]
+
+
+TRACE_DTYPE = np.dtype([
+    ("x", np.float64), ("y", np.float64), ("z", np.float64), ("v", np.float64),
+    ("ux", np.float64), ("uy", np.float64), ("uz", np.float64), ("kind", np.int32),
+    ("event", np.uint32),
+])
+
+
 class pdv_peak(C.Structure):
     _fields_ = [("x_peak", C.c_double), ("i_peak", C.c_double), ("curvature", C.c_double),
                 ("beta", C.c_double), ("tau0", C.c_double), ("status", C.c_int32),
@@ -139,16 +159,22 @@ _lock = threading.Lock()
 _lib = None
 
 
+def debug_library() -> bool:
+    """Whether this process loads the debug build (PDV_LIBRARY=debug)."""
+    return os.environ.get("PDV_LIBRARY", "") == "debug"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if debug_library() else _build.LIB
 
 
 def lib():
-    """Load libpdv.so, building it with nvcc first if it is missing or stale."""
+    """Load libpdv.so (libpdv_debug.so under PDV_LIBRARY=debug), building it
+    with nvcc first if it is missing or stale."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(debug=debug_library())
             L = C.CDLL(path)
             vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
             sig = {
@@ -177,6 +203,8 @@ def lib():
                 "pdv_extract_peaks": ([vp, vp, ip, ip, C.c_double, C.c_double, C.c_double,
                                        C.POINTER(pdv_peak_opts), C.c_uint32, vp], ip),
                 "pdv_measure_issue_rate": ([vp, C.c_double, dp], ip),
+                "pdv_debug_get": ([vp, C.POINTER(pdv_debug_info), ip], ip),
+                "pdv_debug_set_trace": ([vp, ip, ip, vp], ip),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -325,6 +353,24 @@ def pdv_poll(ctx: int, ticket: int, timeout_us: int = 0) -> int:
 
 def pdv_cancel(ctx: int, ticket: int):
     _check(lib().pdv_cancel(C.c_void_p(ctx), C.c_uint64(ticket)))
+
+
+def pdv_debug_get(ctx: int, reset: bool = False) -> dict:
+    """The debug build's failed-check record (debug_build 0 in the release
+    library), optionally cleared."""
+    d = pdv_debug_info()
+    _check(lib().pdv_debug_get(C.c_void_p(ctx), C.byref(d), int(bool(reset))))
+    out = {f: getattr(d, f) for f, _ in pdv_debug_info._fields_}
+    out["site_name"] = DEBUG_SITES[out["site"]] if out["site"] < len(DEBUG_SITES) else out["site"]
+    return out
+
+
+def pdv_debug_set_trace(ctx: int, n_trace: int, max_vertices: int, out=None):
+    """Arm a path trace of the next spectrum call with per-packet records;
+    ``out``: TRACE_DTYPE array [n_trace, max_vertices] that must stay alive
+    until that call returns (n_trace = 0 disarms)."""
+    _check(lib().pdv_debug_set_trace(C.c_void_p(ctx), int(n_trace), int(max_vertices),
+                                     C.c_void_p(out.ctypes.data) if out is not None else None))
 
 
 def _addr(a):
@@ -546,10 +592,28 @@ class Request:
         return out
 
 
-def simulate_spectrum(ctx: Context, cloud: Cloud, wl, **kw) -> dict:
+def simulate_spectrum(ctx: Context, cloud: Cloud, wl, trace=None, debug_check=False,
+                      **kw) -> dict:
+    """One spectrum request. Debug build only: ``trace=(n, max_vertices)``
+    also returns the paths of the first n packets (``out["trace"]``,
+    TRACE_DTYPE [n, max_vertices]; needs ``packets=True``), and
+    ``debug_check`` sets PDV_TEST_DEBUG_CHECK."""
     req = Request(cloud, wl, **kw)
-    pdv_simulate_spectrum(ctx.handle, req.c)
-    return req.result()
+    if debug_check:
+        req.c.flags |= PDV_TEST_DEBUG_CHECK
+    tr = None
+    if trace is not None:
+        tr = np.zeros(tuple(trace), TRACE_DTYPE)
+        pdv_debug_set_trace(ctx.handle, trace[0], trace[1], tr)
+    try:
+        pdv_simulate_spectrum(ctx.handle, req.c)
+    finally:
+        if tr is not None:
+            pdv_debug_set_trace(ctx.handle, 0, 0)
+    out = req.result()
+    if tr is not None:
+        out["trace"] = tr
+    return out
 
 
 def simulate_batch(ctx: Context, clouds: Sequence[Cloud], wls, **kw) -> list:

@@ -25,8 +25,9 @@ def test_header_declares_the_binding_functions():
     assert declared_functions() == sorted(pdv.ABI_FUNCTIONS)
 
 
-def test_library_builds_and_exports_every_symbol():
-    path = B.build()
+@pytest.mark.parametrize("debug", [False, True], ids=["release", "debug"])
+def test_library_builds_and_exports_every_symbol(debug):
+    path = B.build(debug=debug)
     assert os.path.exists(path)
     out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
                          check=True).stdout
@@ -47,7 +48,7 @@ def test_ctypes_layouts_match_the_header(tmp_path):
         "pdv_tuning": pdv.pdv_tuning, "pdv_cloud_info": pdv.pdv_cloud_info,
         "pdv_stats": pdv.pdv_stats, "pdv_allocator": pdv.pdv_allocator,
         "pdv_ss_set": pdv.pdv_ss_set, "pdv_peak_opts": pdv.pdv_peak_opts,
-        "pdv_peak": pdv.pdv_peak,
+        "pdv_peak": pdv.pdv_peak, "pdv_debug_info": pdv.pdv_debug_info,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdv.h"', "int main(void){"]
     for sname, cls in structs.items():
@@ -55,6 +56,9 @@ def test_ctypes_layouts_match_the_header(tmp_path):
         for f, _ in cls._fields_:
             lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (sname, f, sname, f))
     lines.append('printf("pdv_packet_record %zu\\n", sizeof(pdv_packet_record));')
+    for f in pdv.TRACE_DTYPE.names:
+        lines.append('printf("pdv_trace_vertex.%s %%zu\\n", offsetof(pdv_trace_vertex, %s));' % (f, f))
+    lines.append('printf("pdv_trace_vertex %zu\\n", sizeof(pdv_trace_vertex));')
     lines.append("return 0;}")
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))
@@ -68,6 +72,9 @@ def test_ctypes_layouts_match_the_header(tmp_path):
         for f, _ in cls._fields_:
             assert int(got["%s.%s" % (sname, f)]) == getattr(cls, f).offset, (sname, f)
     assert int(got["pdv_packet_record"]) == pdv.PACKET_DTYPE.itemsize
+    assert int(got["pdv_trace_vertex"]) == pdv.TRACE_DTYPE.itemsize
+    for f in pdv.TRACE_DTYPE.names:
+        assert int(got["pdv_trace_vertex." + f]) == pdv.TRACE_DTYPE.fields[f][1], f
     assert C.sizeof(pdv.pdv_peak) == pdv.PEAK_DTYPE.itemsize
     assert C.sizeof(pdv.pdv_ss_set) == pdv.SS_SET_DTYPE.itemsize
 
