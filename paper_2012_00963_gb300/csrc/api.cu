@@ -469,6 +469,7 @@ extern "C" pdv_status pdv_set_phase_table(pdv_cloud* cl, int n, const double* th
   const size_t oth = L.add(sizeof(float) * n);
   const size_t odt = L.add(sizeof(float) * n);
   const size_t ocs = L.add(sizeof(float2) * n);
+  const size_t ond = L.add(sizeof(uint2) * n);
   const size_t othd = L.add(sizeof(double) * n);
   const size_t oGp = L.add(sizeof(unsigned short) * ngp);
   const size_t oin = L.add(sizeof(double) * 2 * n);
@@ -488,6 +489,7 @@ extern "C" pdv_status pdv_set_phase_table(pdv_cloud* cl, int n, const double* th
   cl->t.thpi = (float*)(base + oth);
   cl->t.dthpi = (float*)(base + odt);
   cl->t.cs = (float2*)(base + ocs);
+  cl->t.node = (uint2*)(base + ond);
   cl->t.th_d = (double*)(base + othd);
   cl->t.Gp = (unsigned short*)(base + oGp);
   cl->t.n_p = n;
@@ -666,10 +668,10 @@ static SetDesc make_set(const pdv_request* r) {
   d.Sq = cl->t.Sq; d.Sd = cl->t.Sd; d.w = cl->t.w; d.G = cl->t.G;
   d.Cq = cl->t.Cq; d.thpi = cl->t.thpi; d.dthpi = cl->t.dthpi; d.th_d = cl->t.th_d; d.Gp = cl->t.Gp;
   d.cs = cl->t.cs;
+  d.node = cl->t.node;
   d.n_v = cl->t.n_v; d.n_g = cl->t.n_g; d.g_shift = cl->t.g_shift; d.n_p = cl->t.n_p;
   d.phase_uniform = cl->t.phase_uniform;
   d.inv_nm1 = (float)(1.0 / (double)(cl->t.n_p - 1));
-  d.dth_f = (float)(M_PI / (double)(cl->t.n_p - 1));
   d.angle_table = cl->max_dtheta <= 3.1e-3 ? 1 : 0;
   d.n_snap = r->n_snap; d.n_bins = r->n_bins;
   d.surface_mode = cl->desc.surface_mode;
@@ -779,7 +781,7 @@ static ReqBuffers plan_request(const pdv_request* r, bool device_out) {
 
 static size_t set_smem(const SetDesc& d, int hm) {
   return transport_f32_smem(d.n_v, d.n_g, d.n_p, d.n_snap, d.n_bins, hm, d.phase_uniform, d.ap_all,
-                            d.expo);
+                            d.expo, d.angle_table);
 }
 
 static int pick_hist_mode(const pdv_ctx* c, const SetDesc& d) {

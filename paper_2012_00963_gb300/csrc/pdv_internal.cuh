@@ -121,6 +121,8 @@ struct CloudTables {
   float* dthpi = nullptr;             // [n_p] (theta_{i+1} - theta_i) / pi / (Cq_{i+1} - Cq_i)
   double* th_d = nullptr;             // [n_p] theta (FP64 path)
   float2* cs = nullptr;               // [n_p] (cos theta_i, sin theta_i), FP64 rounded to FP32
+  uint2* node = nullptr;              // [n_p] (Cq_i, slope (theta_{i+1} - theta_i) / (Cq_{i+1} - Cq_i)
+                                      //  in radians as FP32 bits); slope 0 for an empty bin
   unsigned short* Gp = nullptr;       // [n_gp + 1] guide over the 2^24 CDF
   int n_p = 0;
   int phase_uniform = 0;              // theta grid uniform over [0, pi]
@@ -137,6 +139,7 @@ struct SetDesc {
   const float* dthpi;
   const double* th_d;
   const float2* cs;                   // [n_p] (cos theta_i, sin theta_i)
+  const uint2* node;                  // [n_p] (Cq_i, slope in radians per CDF unit, FP32 bits)
   const unsigned short* Gp;
   const double* t_snap;               // [3 n_snap]: seconds in request order, ascending, index
   unsigned long long* hist;           // [n_snap][n_bins + 3]
@@ -156,7 +159,6 @@ struct SetDesc {
   double z_probe, r_beam, r_ap2, cos_alpha, v_lo, inv_dbin;
   float inv_tau_f, v_bot_f, dv_f, v_top_f, v_fs_f, z_probe_f, r_beam_f, r_ap2_f;
   float cos_alpha_f, v_lo_f, inv_dbin_f, inv_nm1;      // 1 / (n_p - 1)
-  float dth_f;                        // pi / (n_p - 1): a uniform grid's step in theta
   int angle_table;                    // node spacing <= 3.1e-3: sin/cos from the node table
   // exponential law: v(S) = v_fs - lg_c log2((1 - S) + S eps), dv/dS = dvds_c / ((1 - S) + S eps)
   float lg_c_f, eps_f, dvds_c_f;      // v_fs ln2 / beta, exp(-beta (v_top/v_fs - 1)), v_fs E / beta
@@ -269,7 +271,7 @@ void launch_normalise(const SetDesc* d_sets, int n_sets, double* const* d_spec,
                       pdv_counters* const* d_cnt_out, unsigned long long* const* d_raw,
                       const unsigned* flags, int max_snap, cudaStream_t st);
 size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode,
-                          int phase_uniform, int ap_all, int expo);
+                          int phase_uniform, int ap_all, int expo, int angle_table);
 int transport_f32_max_smem();
 // Load every FP32 transport build and the normalisation kernel on the current
 // device now (the runtime otherwise loads a kernel at its first launch).

@@ -185,12 +185,17 @@ __global__ void k_phase_quant(const double* work, const double* th, int n, unsig
   thd[i] = th[i];
 }
 
-__global__ void k_phase_slopes(const unsigned* Cq, const double* th, int n, float* dthpi) {
+// Slopes of the inverse CDF inside each bin: dthpi in half turns per CDF unit
+// (the coarse-table walk), and the FP32 walk's node record (Cq_i, slope in
+// radians per CDF unit), both from FP64.
+__global__ void k_phase_slopes(const unsigned* Cq, const double* th, int n, float* dthpi,
+                               uint2* node) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  if (i == n - 1) { dthpi[i] = 0.0f; return; }
-  const unsigned dc = Cq[i + 1] - Cq[i];
-  dthpi[i] = dc ? (float)((th[i + 1] - th[i]) / 3.14159265358979323846 / (double)dc) : 0.0f;
+  const unsigned dc = i == n - 1 ? 0u : Cq[i + 1] - Cq[i];
+  const double dth = i == n - 1 ? 0.0 : th[i + 1] - th[i];
+  dthpi[i] = dc ? (float)(dth / 3.14159265358979323846 / (double)dc) : 0.0f;
+  node[i] = make_uint2(Cq[i], __float_as_uint(dc ? (float)(dth / (double)dc) : 0.0f));
 }
 
 // Gp[c] = largest i in [0, n-2] with Cq_i <= c 2^(24 - kGuidePhaseLog).
@@ -232,7 +237,7 @@ cudaError_t build_phase_cdf(const double* d_theta, const double* d_p, int n, dou
   k_phase_trap<<<nb, 256, 0, st>>>(d_theta, d_p, n, d_work);
   k_phase_prefix<<<1, kScanThreads, 0, st>>>(d_work, n);
   k_phase_quant<<<nb, 256, 0, st>>>(d_work, d_theta, n, t->Cq, t->thpi, t->th_d);
-  k_phase_slopes<<<nb, 256, 0, st>>>(t->Cq, d_theta, n, t->dthpi);
+  k_phase_slopes<<<nb, 256, 0, st>>>(t->Cq, d_theta, n, t->dthpi, t->node);
   k_phase_guide<<<((1 << kGuidePhaseLog) + 1 + 255) / 256, 256, 0, st>>>(t->Cq, n, t->Gp);
   k_phase_gtab<<<1, kScanThreads, 0, st>>>(t->Cq, d_theta, n, d_gtab);
   return cudaGetLastError();

@@ -46,15 +46,15 @@ struct SmemTables {
   const unsigned long long* Sq;
   const float* w;
   const unsigned short* G;
-  const unsigned* Cq;
-  const float* thpi;
+  const uint2* node;                  // (Cq_i, slope in radians per CDF unit) of the phase nodes
+  const float* thpi;                  // coarse non-uniform tables only
   const float* dthpi;
   const unsigned short* Gp;
   const float* ts;                    // snapshot times, ascending (seconds)
   const unsigned short* perm;         // request index of each ascending time
   unsigned long long* hist;
-  const float2* cs;                   // (cos, sin) of the phase nodes
-  const float2* turn;                 // (cos, sin) of 2 pi j / kTurn, j = 0 .. kTurn - 1
+  const float2* ang;                  // (cos, sin): the n_p phase nodes, then the kTurn turn steps
+  const float2* turn;                 // ang + n_p: (cos, sin) of 2 pi j / kTurn
 };
 
 // Angles as a table value and a small remainder: cos(a + d) and sin(a + d)
@@ -83,22 +83,23 @@ __host__ __device__ inline int tally_rows(int n_snap, int ap_all) { return ap_al
 
 __host__ __device__ inline size_t smem_layout(int n_v, int n_g, int n_p, int n_snap, int n_bins,
                                               int hist_mode, int phase_uniform, int ap_all, int expo,
-                                              size_t* off) {
+                                              int angle_table, size_t* off) {
   // the exponential law inverts in closed form: its velocity table is not staged
   const size_t n_m = expo ? 0 : (size_t)n_v + 1, n_mg = expo ? 0 : (size_t)n_g + 1;
-  const size_t n_th = phase_uniform ? 0 : (size_t)n_p;
+  // per-node angles in half turns: coarse tables on a non-uniform grid only
+  const size_t n_th = (phase_uniform || angle_table) ? 0 : (size_t)n_p;
   size_t o = 0;
   off[0] = o; o = align16(o + sizeof(unsigned long long) * n_m);                  // Sq
   off[1] = o; o = align16(o + sizeof(float) * n_m);                               // w
   off[2] = o; o = align16(o + sizeof(unsigned short) * n_mg);                     // G
-  off[3] = o; o = align16(o + sizeof(unsigned) * (size_t)n_p);                    // Cq
+  off[3] = o; o = align16(o + sizeof(uint2) * (size_t)n_p);                       // node
   off[4] = o; o = align16(o + sizeof(float) * n_th);                              // thpi
   off[5] = o; o = align16(o + sizeof(float) * n_th);                              // dthpi
   off[6] = o; o = align16(o + sizeof(unsigned short) * ((1 << kGuidePhaseLog) + 1));  // Gp
   off[7] = o; o = align16(o + sizeof(float) * (size_t)n_snap);                    // ts
   off[8] = o; o = align16(o + sizeof(unsigned short) * (size_t)n_snap);           // perm
-  off[10] = o; o = align16(o + sizeof(float2) * (size_t)n_p);                     // cs
-  off[11] = o; o = align16(o + sizeof(float2) * (size_t)kTurn);                   // turn
+  off[10] = o; o = align16(o + sizeof(float2) * ((size_t)n_p + kTurn));           // ang
+  off[11] = off[10] + sizeof(float2) * (size_t)n_p;                               // turn (in ang)
   off[9] = o;
   if (hist_mode == 2)
     o = align16(o + sizeof(unsigned long long) * (size_t)tally_rows(n_snap, ap_all) * hist_row(n_bins));
@@ -106,9 +107,10 @@ __host__ __device__ inline size_t smem_layout(int n_v, int n_g, int n_p, int n_s
 }
 
 size_t transport_f32_smem(int n_v, int n_g, int n_p, int n_snap, int n_bins, int hist_mode,
-                          int phase_uniform, int ap_all, int expo) {
+                          int phase_uniform, int ap_all, int expo, int angle_table) {
   size_t off[12];
-  return smem_layout(n_v, n_g, n_p, n_snap, n_bins, hist_mode, phase_uniform, ap_all, expo, off);
+  return smem_layout(n_v, n_g, n_p, n_snap, n_bins, hist_mode, phase_uniform, ap_all, expo,
+                     angle_table, off);
 }
 
 __device__ __forceinline__ int search_mass(const unsigned long long* Sq, const unsigned short* G,
@@ -173,19 +175,19 @@ template <int HMODE>
 __device__ __forceinline__ SmemTables stage_set(const SetDesc& sd, unsigned char* smem) {
   size_t off[12];
   smem_layout(sd.n_v, sd.n_g, sd.n_p, sd.n_snap, sd.n_bins, HMODE, sd.phase_uniform, sd.ap_all,
-              sd.expo, off);
+              sd.expo, sd.angle_table, off);
   SmemTables tb;
   tb.Sq = reinterpret_cast<const unsigned long long*>(smem + off[0]);
   tb.w = reinterpret_cast<const float*>(smem + off[1]);
   tb.G = reinterpret_cast<const unsigned short*>(smem + off[2]);
-  tb.Cq = reinterpret_cast<const unsigned*>(smem + off[3]);
+  tb.node = reinterpret_cast<const uint2*>(smem + off[3]);
   tb.thpi = reinterpret_cast<const float*>(smem + off[4]);
   tb.dthpi = reinterpret_cast<const float*>(smem + off[5]);
   tb.Gp = reinterpret_cast<const unsigned short*>(smem + off[6]);
   tb.ts = reinterpret_cast<const float*>(smem + off[7]);
   tb.perm = reinterpret_cast<const unsigned short*>(smem + off[8]);
   tb.hist = HMODE == 2 ? reinterpret_cast<unsigned long long*>(smem + off[9]) : sd.hist;
-  tb.cs = reinterpret_cast<const float2*>(smem + off[10]);
+  tb.ang = reinterpret_cast<const float2*>(smem + off[10]);
   tb.turn = reinterpret_cast<const float2*>(smem + off[11]);
   {
     if (!sd.expo) {
@@ -196,10 +198,10 @@ __device__ __forceinline__ SmemTables stage_set(const SetDesc& sd, unsigned char
       unsigned short* G = reinterpret_cast<unsigned short*>(smem + off[2]);
       for (int i = threadIdx.x; i <= sd.n_g; i += blockDim.x) G[i] = sd.G[i];
     }
-    unsigned* Cq = reinterpret_cast<unsigned*>(smem + off[3]);
+    uint2* node = reinterpret_cast<uint2*>(smem + off[3]);
     float* thpi = reinterpret_cast<float*>(smem + off[4]);
     float* dthpi = reinterpret_cast<float*>(smem + off[5]);
-    float2* cs = reinterpret_cast<float2*>(smem + off[10]);
+    float2* ang = reinterpret_cast<float2*>(smem + off[10]);
     float2* turn = reinterpret_cast<float2*>(smem + off[11]);
     for (int j = threadIdx.x; j < kTurn; j += blockDim.x) {
       float sj, cj;
@@ -207,9 +209,9 @@ __device__ __forceinline__ SmemTables stage_set(const SetDesc& sd, unsigned char
       turn[j] = make_float2(cj, sj);
     }
     for (int i = threadIdx.x; i < sd.n_p; i += blockDim.x) {
-      Cq[i] = sd.Cq[i];
-      cs[i] = sd.cs[i];
-      if (!sd.phase_uniform) {
+      node[i] = sd.node[i];
+      ang[i] = sd.cs[i];
+      if (!sd.phase_uniform && !sd.angle_table) {
         thpi[i] = sd.thpi[i];
         dthpi[i] = sd.dthpi[i];
       }
@@ -455,9 +457,14 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
       --nev;
       ++st_events;
     }
-    // Step (6): free surface z = v_fs t, reflectivity in 2^32 fixed point
+    // Step (6): free surface z = v_fs t, reflectivity in 2^32 fixed point:
+    // round(W R_q / 2^32). W <= 2^32, and R_q < 2^32 unless R = 1, so the
+    // product is one 32 x 32 -> 64-bit multiply-add; W = 2^32 gives R_q.
     const unsigned long long Wr =
-        sd.R_q >= (1ull << 32) ? W : ((W * sd.R_q + (1ull << 31)) >> 32);
+        sd.R_q >= (1ull << 32)
+            ? W
+            : ((W >> 32) ? sd.R_q
+                         : (((unsigned long long)(unsigned)W * (unsigned)sd.R_q + (1ull << 31)) >> 32));
     st_surf += surf ? 1u : 0u;
     if (DUMP) nsurf += surf ? 1u : 0u;
     st_wsurf += surf ? W - Wr : 0ull;
@@ -511,30 +518,28 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
       int hi = part ? (int)PDV_LD(tb.Gp, c + 1, n_gp, PDV_DEBUG_SITE_PHASE_GUIDE) : lo;
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (PDV_LD(tb.Cq, mid, n_p, PDV_DEBUG_SITE_PHASE_NODE) <= m2) lo = mid; else hi = mid - 1;
+        if (PDV_LD(tb.node, mid, n_p, PDV_DEBUG_SITE_PHASE_NODE).x <= m2) lo = mid; else hi = mid - 1;
       }
-      const unsigned c0 = PDV_LD(tb.Cq, lo, n_p, PDV_DEBUG_SITE_PHASE_NODE);
-      const float fm = (float)(m2 - c0) + 0.5f;
+      const uint2 nd = PDV_LD(tb.node, lo, n_p, PDV_DEBUG_SITE_PHASE_NODE);
+      const float fm = (float)(m2 - nd.x) + 0.5f;
       if (sd.angle_table) {
-        const float dp =
-            sd.phase_uniform
-                ? fm * rcp_approx((float)(PDV_LD(tb.Cq, lo + 1, n_p, PDV_DEBUG_SITE_PHASE_NODE) - c0)) *
-                      sd.dth_f
-                : fm * PDV_LD(tb.dthpi, lo, n_p, PDV_DEBUG_SITE_PHASE_NODE) * 3.14159265f;
+        // theta = theta_i + d with d = (m - Cq_i + 1/2) times the bin's slope
+        const float dp = fm * __uint_as_float(nd.y);
         // theta' = 2 pi f with f = u / 4 = ((r1 >> 9) + 1/2) 2^-25: the nearest
         // table step j and the remainder, both exact in integers
         const int m1 = (int)(r.y >> 9);
         const int js = (m1 + (1 << 14)) >> 15;
         const float ds = (float)(2 * (m1 - (js << 15)) + 1) * kPi2m25f;
-        cos_sin_add(surf ? PDV_LD(tb.turn, js, kTurn, PDV_DEBUG_SITE_TURN)
-                         : PDV_LD(tb.cs, lo, n_p, PDV_DEBUG_SITE_PHASE_NODE),
+        // one load: the node's (cos, sin), or the wall's turn step
+        cos_sin_add(PDV_LD(tb.ang, surf ? n_p + js : lo, n_p + kTurn, PDV_DEBUG_SITE_PHASE_NODE),
                     surf ? ds : dp, &ct, &st);
       } else {
         // theta_i / pi = i / (n_p - 1) on a uniform grid; linear inside the CDF bin
         const float tp =
             sd.phase_uniform
                 ? ((float)lo +
-                   fm * rcp_approx((float)(PDV_LD(tb.Cq, lo + 1, n_p, PDV_DEBUG_SITE_PHASE_NODE) - c0))) *
+                   fm * rcp_approx(
+                            (float)(PDV_LD(tb.node, lo + 1, n_p, PDV_DEBUG_SITE_PHASE_NODE).x - nd.x))) *
                       sd.inv_nm1
                 : fmaf(fm, PDV_LD(tb.dthpi, lo, n_p, PDV_DEBUG_SITE_PHASE_NODE),
                        PDV_LD(tb.thpi, lo, n_p, PDV_DEBUG_SITE_PHASE_NODE));
