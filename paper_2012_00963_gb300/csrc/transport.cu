@@ -58,18 +58,17 @@ struct SmemTables {
 };
 
 // Angles as a table value and a small remainder: cos(a + d) and sin(a + d)
-// from (cos a, sin a) and cos d = 1 - d^2/2, sin d = d - d^3/6, exact to 2e-12
-// for |d| <= 3.1e-3 (half a step of the kTurn-entry table; a phase-table step
-// of 1800 nodes is 1.7e-3).
+// from (cos a, sin a) and cos d = 1 - d^2/2, sin d = d. For |d| <= 3.1e-3
+// (half a step of the kTurn-entry table; a phase-table bin is at most 3.1e-3
+// wide) the dropped terms are d^3/6 <= 5e-9 and d^4/24 <= 4e-12, below a
+// binary32 ulp of a unit vector's components (6e-8).
 constexpr int kTurnLog = 10, kTurn = 1 << kTurnLog;
 constexpr float kPi2m25f = 9.3626757e-08f;   // pi 2^-25
 constexpr float kPi2m23f = 3.7450703e-07f;   // pi 2^-23
 __device__ __forceinline__ void cos_sin_add(float2 cs, float d, float* c, float* s) {
-  const float d2 = d * d;
-  const float cd = fmaf(d2, -0.5f, 1.0f);
-  const float sd = d * fmaf(d2, -0.16666667f, 1.0f);
-  *c = fmaf(cs.x, cd, -cs.y * sd);
-  *s = fmaf(cs.y, cd, cs.x * sd);
+  const float cd = fmaf(d * d, -0.5f, 1.0f);
+  *c = fmaf(cs.x, cd, -cs.y * d);
+  *s = fmaf(cs.y, cd, cs.x * d);
 }
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -275,6 +274,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
   unsigned st_launch = 0, st_events = 0, st_scat = 0, st_surf = 0, st_esc = 0;
   unsigned long long st_wesc = 0, st_wabs = 0, st_wsurf = 0;   // escaped / absorbed weight
 
+  const unsigned lt_mask = lanemask_lt();
   for (;;) {
     // refill dead lanes from the warp's chunk of packets, in one pass: when
     // the chunk runs out, the lanes it could not serve wait one flight
@@ -294,7 +294,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
       }
       const unsigned cnt = __popc(need);
       const unsigned take = avail < cnt ? avail : cnt;
-      const unsigned rank = __popc(need & lanemask_lt());
+      const unsigned rank = __popc(need & lt_mask);
       if (!alive && rank < take) {
         // Step (1): a new packet at the top of the cloud moving along -z
         pk = base_pk + (pool_next + rank);
