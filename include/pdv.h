@@ -57,6 +57,8 @@ enum { PDV_PREC_FP32 = 0, PDV_PREC_FP64 = 1 };
 #define PDV_PER_DV     0x2u   /* spectrum divided by the bin width (per m/s)   */
 #define PDV_IN_DEVICE  0x4u   /* input arrays are device pointers (pdv_ss_spectrum,
                                  pdv_extract_peaks)                            */
+#define PDV_EXTRACT_TENSOR 0x40u /* pdv_extract_peaks: the DFT product on the tensor
+                                   cores (tcgen05, split TF32) where it fits     */
 /* Implicit capture with Russian roulette, in place of the analog absorption
  * of Eq. 11 (Section II.B step (4)); off by default, exact free paths only
  * (n_layers == 0), both precisions. At every particle interaction the packet
@@ -406,15 +408,21 @@ typedef struct {
 /* Extract the main peak of n_spectra spectra of n_bins uniform bins over
  * [v_lo, v_hi] (row-major [n_spectra][n_bins]). Arithmetic is FP32 with
  * cosine / sine tables computed in FP64 and rounded to FP32; inputs are
- * rounded to FP32 (magnitudes below 1.2e-38 flush to zero). Accuracy: about
- * 1e-6 relative in x_peak, I''/I, beta and tau0 while the cut-off smooths
+ * rounded to FP32 (magnitudes below 1.2e-38 flush to zero). The DFT product
+ * runs as FP32 FMAs on the CUDA cores; with PDV_EXTRACT_TENSOR and k_c <= 63
+ * it runs on the tensor cores instead (TF32 operands split into a high and a
+ * low part, three products per step, so each term carries at most about
+ * 2^-22 of |x| |F| of error, and short FP32 sums of the truncating
+ * accumulators). Accuracy: about 1e-6 relative in x_peak,
+ * I''/I, beta and tau0 while the cut-off smooths
  * (k_c well below n_bins / 2); as k_c nears n_bins / 2 the
  * FP32 rounding of the input itself, amplified by up to pi^2 per bin in the
  * second derivative, dominates the curvature.
  * spectra: host array, or device with PDV_IN_DEVICE. out: host array,
  * or device with PDV_OUT_DEVICE. Errors: PDV_EINVAL (n_spectra < 0,
  * n_bins < 3 or > 8192, k_c outside [1, n_bins / 2), v_hi <= v_lo, v_fs <= 0),
- * PDV_ENOMEM, PDV_ECUDA. */
+ * PDV_ENOMEM, PDV_ECUDA, PDV_ETIMEOUT (a bounded wait of the tensor-core
+ * kernel for its products ran out). */
 pdv_status pdv_extract_peaks(pdv_ctx* ctx, const double* spectra, int n_spectra, int n_bins,
                              double v_lo, double v_hi, double v_fs, const pdv_peak_opts* opts,
                              uint32_t flags, pdv_peak* out);

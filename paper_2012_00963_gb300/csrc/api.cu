@@ -73,7 +73,8 @@ struct pdv_ctx {
   // not map fresh memory each time (the default pool releases at every sync)
   cudaMemPool_t pool = nullptr;
   int sm_count = 0;
-  int max_smem = 0;
+  int max_smem = 0;                   // shared memory the transport's tables may use
+  int smem_optin = 0;                 // the device's opt-in shared memory per block
   pdv_tuning tuning{};
   std::string tune_cache;              // pdv_autotune's JSON cache file (empty: none)
   std::string device_name;
@@ -252,6 +253,7 @@ extern "C" pdv_status pdv_ctx_create(int device, void* cuda_stream, const pdv_al
     cudaGetLastError();
   }
   c->max_smem = transport_f32_max_smem();
+  cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   c->tuning.block_threads = 256;
   cudaEventCreate(&c->ev0);
   cudaEventCreate(&c->ev1);
@@ -1969,7 +1971,7 @@ extern "C" pdv_status pdv_extract_peaks(pdv_ctx* c, const double* spectra, int n
   if (!(v_hi > v_lo) || !std::isfinite(v_lo) || !std::isfinite(v_hi) || !(v_fs > 0.0) || !std::isfinite(v_fs))
     return fail(PDV_EINVAL, "need finite v_lo < v_hi and v_fs > 0");
   if (std::isnan(opts->x_min) || std::isnan(opts->x_max)) return fail(PDV_EINVAL, "window bounds are NaN");
-  if (flags & ~(PDV_IN_DEVICE | PDV_OUT_DEVICE)) return fail(PDV_EINVAL, "unknown flags");
+  if (flags & ~(PDV_IN_DEVICE | PDV_OUT_DEVICE | PDV_EXTRACT_TENSOR)) return fail(PDV_EINVAL, "unknown flags");
   if (n_spectra == 0) return PDV_OK;
   if (!spectra || !out) return fail(PDV_EINVAL, "spectra and out must not be NULL");
   const bool dev_in = (flags & PDV_IN_DEVICE) != 0, dev_out = (flags & PDV_OUT_DEVICE) != 0;
@@ -1984,18 +1986,24 @@ extern "C" pdv_status pdv_extract_peaks(pdv_ctx* c, const double* spectra, int n
   CK(enter(c->device));
   std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t st = c->stream;
-  // cut-offs up to 95 modes take the tiled kernel (64 spectra per block);
-  // larger ones the one-spectrum-per-block kernel
-  const bool tiled = peak_tiled(opts->k_c);
+  // with PDV_EXTRACT_TENSOR the tensor-core kernel (128 spectra per block)
+  // where it fits; else cut-offs up to 95 modes take the tiled kernel (64
+  // spectra per block), larger ones the one-spectrum-per-block kernel
+  const bool tc = (flags & PDV_EXTRACT_TENSOR) && peak_tc(opts->k_c, c->smem_optin);
+  const bool tiled = !tc && peak_tiled(opts->k_c);
   int occ = 0;
-  if (tiled) CK(tiled_occupancy(opts->k_c, &occ));
+  if (tc) CK(tc_occupancy(opts->k_c, &occ));
+  else if (tiled) CK(tiled_occupancy(opts->k_c, &occ));
   else CK(peak_occupancy(n_bins, opts->k_c, &occ));
   if (occ < 1) return fail(PDV_EINVAL, "extraction tables do not fit in shared memory");
   const size_t in_bytes = sizeof(double) * (size_t)n_spectra * n_bins;
   const size_t out_bytes = sizeof(pdv_peak) * (size_t)n_spectra;
   Layout L;
   const size_t o_tw = L.add(sizeof(float2) * (size_t)n_bins);
-  const size_t o_mats = tiled ? L.add(peak_mats_bytes(n_bins, opts->k_c, j_hi - j_lo + 1)) : 0;
+  const size_t o_mats =
+      tc ? L.add(peak_mats_tc_bytes(n_bins, opts->k_c, j_hi - j_lo + 1))
+         : (tiled ? L.add(peak_mats_bytes(n_bins, opts->k_c, j_hi - j_lo + 1)) : 0);
+  const size_t o_err = L.add(sizeof(int));
   const size_t o_in = dev_in ? 0 : L.add(in_bytes);
   const size_t o_out = dev_out ? 0 : L.add(out_bytes);
   char* base = (char*)ctx_alloc(c, L.bytes, st);
@@ -2012,7 +2020,14 @@ extern "C" pdv_status pdv_extract_peaks(pdv_ctx* c, const double* spectra, int n
   geom.x0 = (float)((v_lo + 0.5 * dv) / v_fs);
   geom.dxj = (float)(dv / v_fs);
   geom.scale = (float)((v_fs / dv) * (v_fs / dv));
-  if (tiled) {
+  int* d_err = (int*)(base + o_err);
+  CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+  if (tc) {
+    CK(launch_extract_tc(d_in, n_spectra, n_bins, opts->k_c, j_lo, j_hi, geom,
+                         (const float2*)(base + o_tw), (float*)(base + o_mats), d_out, d_err, occ,
+                         c->sm_count, st, c->ev0, c->ev1));
+    c->launches += 3;
+  } else if (tiled) {
     CK(launch_extract_tiled(d_in, n_spectra, n_bins, opts->k_c, j_lo, j_hi, geom,
                             (const float2*)(base + o_tw), (float*)(base + o_mats), d_out, occ,
                             c->sm_count, st, c->ev0, c->ev1));
@@ -2026,10 +2041,13 @@ extern "C" pdv_status pdv_extract_peaks(pdv_ctx* c, const double* spectra, int n
     c->launches += 2;
   }
   if (!dev_out) CK(cudaMemcpyAsync(out, d_out, out_bytes, cudaMemcpyDeviceToHost, st));
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) c->last_model_ms = ms;
   cudaGetLastError();
+  if (err) return fail(PDV_ETIMEOUT, "tensor-core extraction: a wait for the products timed out");
   return PDV_OK;
 }
 

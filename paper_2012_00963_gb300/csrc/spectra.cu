@@ -447,12 +447,14 @@ __global__ void k_peak_mats(int n, int k_c, int n_p, int k2p, int j_lo, int n_w,
   }
 }
 
-// acc[4][6] += A[rows ty*4..+3] x B[cols tx*6..+5] over `len` reduction steps.
+// acc[4][6] += A[rows ty*4..+3] x B[cols tx*6..+5] over `len` reduction steps
+// (A: reduction-major with row stride AS).
+template <int AS = kAS>
 __device__ __forceinline__ void tile_fma(const float* A, const float* B, int len, int ty, int tx,
                                          float (&acc)[4][6]) {
 #pragma unroll 8
   for (int q = 0; q < len; ++q) {
-    const float4 a = *reinterpret_cast<const float4*>(A + q * kAS + ty * 4);
+    const float4 a = *reinterpret_cast<const float4*>(A + q * AS + ty * 4);
     const float2 b0 = *reinterpret_cast<const float2*>(B + q * kNT + tx * 6);
     const float2 b1 = *reinterpret_cast<const float2*>(B + q * kNT + tx * 6 + 2);
     const float2 b2 = *reinterpret_cast<const float2*>(B + q * kNT + tx * 6 + 4);
@@ -466,7 +468,8 @@ __device__ __forceinline__ void tile_fma(const float* A, const float* B, int len
 }
 
 // smooth_eval with the coefficients of spectrum s read from the tile's
-// mode-major shared array and the twiddles from global memory.
+// mode-major shared array (row stride AS) and the twiddles from global memory.
+template <int AS = kAS>
 __device__ __forceinline__ void tile_smooth_eval(const float2* tw, const float* Cs, int s, int n,
                                                  int k_c, int J, float d, int lane, float* s0,
                                                  float* s1, float* s2) {
@@ -480,7 +483,7 @@ __device__ __forceinline__ void tile_smooth_eval(const float2* tw, const float* 
     const float2 t = __ldg(&tw[m]);
     const float c = t.x * cp - t.y * sp;
     const float sn = t.y * cp + t.x * sp;
-    const float qa = Cs[(2 * k) * kAS + s], qb = Cs[(2 * k + 1) * kAS + s];
+    const float qa = Cs[(2 * k) * AS + s], qb = Cs[(2 * k + 1) * AS + s];
     const float g = k == 0 ? 1.0f : 2.0f;
     const float w = 3.14159265358979f * two_over_n * (float)k;
     const float e = qa * c + qb * sn;
@@ -518,6 +521,117 @@ __device__ __forceinline__ void load_chunk_async(float* dst, const float* src, s
   cp_async_commit();
 }
 
+// Stage 2 of a tile of kTS spectra (the first at global index s0): smoothed
+// window values (coefficients x G, Cs mode-major with row stride AS), the
+// running first maximum per spectrum, then per spectrum the status, the Newton
+// refinement and Eq. 35. Run by 256 threads (tid: 0..255; two groups of 256
+// may run it side by side with their own buffers, as its block barriers
+// match). Bs: two kJC x kNT buffers; red_v / red_j: kTS each.
+template <int AS>
+__device__ __forceinline__ void tile_peaks(const float* Cs, int s0, int n_spec, int n, int k_c,
+                                           int j_lo, int j_hi, PeakGeom geom, const float2* tw,
+                                           const float* G, int k2p, int nw_p, float* Bs,
+                                           float* red_v, int* red_j, pdv_peak* out, int tid) {
+  const int ty = tid >> 4, tx = tid & 15;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int n_w = j_hi - j_lo + 1;
+  // ---- smoothed window values (tile x G), running first maximum per spectrum
+  float best[4];
+  int bj[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    best[i] = -INFINITY;
+    bj[i] = 0x7fffffff;
+  }
+  // chunks run column tile by column tile, the next chunk of G copied into
+  // the other shared buffer (cp.async) while this one is multiplied
+  {
+    const int nr = k2p / kJC, nchunks = nr * (nw_p / kNT);
+    auto g_src = [&](int ch) {
+      return G + (size_t)((ch % nr) * kJC) * nw_p + (ch / nr) * kNT;
+    };
+    float acc[4][6];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc[i][c] = 0.0f;
+    __syncthreads();                               // B buffers free
+    if (nchunks) load_chunk_async(Bs, g_src(0), (size_t)nw_p, tid);
+    for (int ch = 0; ch < nchunks; ++ch) {
+      cp_async_wait_all();
+      __syncthreads();                             // this chunk visible; the other buffer free
+      if (ch + 1 < nchunks)
+        load_chunk_async(Bs + ((ch + 1) & 1) * (kJC * kNT), g_src(ch + 1), (size_t)nw_p, tid);
+      tile_fma<AS>(Cs + (ch % nr) * kJC * AS, Bs + (ch & 1) * (kJC * kNT), kJC, ty, tx, acc);
+      if (ch % nr == nr - 1) {
+        const int wp = (ch / nr) * kNT;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const int j = wp + tx * 6 + c;
+          if (j < n_w) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              if (acc[i][c] > best[i]) {
+                best[i] = acc[i][c];
+                bj[i] = j_lo + j;
+              }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) acc[i][c] = 0.0f;
+      }
+    }
+  }
+  // reduce over the 16 threads sharing ty (lanes 0-15 and 16-31 of a warp)
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    for (int o = 8; o; o >>= 1) {
+      const float ov = __shfl_xor_sync(kFull, best[i], o);
+      const int oj = __shfl_xor_sync(kFull, bj[i], o);
+      if (ov > best[i] || (ov == best[i] && oj < bj[i])) {
+        best[i] = ov;
+        bj[i] = oj;
+      }
+    }
+    if (tx == 0) {
+      red_v[ty * 4 + i] = best[i];
+      red_j[ty * 4 + i] = bj[i];
+    }
+  }
+  __syncthreads();
+  // ---- per spectrum: status, Newton refinement, Eq. 35
+  for (int s = warp; s < kTS; s += 256 / 32) {
+    const int gs = s0 + s;
+    if (gs >= n_spec) break;
+    const float bv = red_v[s];
+    const int J = red_j[s];
+    pdv_peak r;
+    r.x_peak = r.i_peak = r.curvature = r.beta = r.tau0 = NAN;
+    r.j_max = (n_w >= 1) ? J : -1;
+    r.status = PDV_PEAK_NO_PEAK;
+    if (n_w >= 1 && bv > 0.0f) {
+      if (J == j_lo || J == j_hi) {
+        r.status = PDV_PEAK_EDGE;
+      } else {
+        float d = 0.f, q0, q1, q2;
+        tile_smooth_eval<AS>(tw, Cs, s, n, k_c, J, d, lane, &q0, &q1, &q2);
+        for (int it = 0; it < kPeakNewton && q2 < 0.0f; ++it) {
+          const float nd = fminf(fmaxf(d - q1 / q2, -1.0f), 1.0f);
+          const bool done = fabsf(nd - d) <= 1e-6f;
+          d = nd;
+          if (done) break;
+          tile_smooth_eval<AS>(tw, Cs, s, n, k_c, J, d, lane, &q0, &q1, &q2);
+        }
+        peak_finish(r, J, d, q0, q2, 1.0f / (float)n, geom);
+      }
+    }
+    if (lane == 0) out[gs] = r;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(256, 3) k_extract_tiled(
     const double* spec, int n_spec, int n, int k_c, int j_lo, int j_hi, PeakGeom geom,
     const float2* tw, const float* F, const float* G, int n_p, int k2p, int nw_p, pdv_peak* out) {
@@ -530,7 +644,6 @@ __global__ void __launch_bounds__(256, 3) k_extract_tiled(
   int* red_j = reinterpret_cast<int*>(red_v + kTS);
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int warp = tid >> 5, lane = tid & 31;
-  const int n_w = j_hi - j_lo + 1;
   const int n_tiles = (n_spec + kTS - 1) / kTS;
 
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -584,102 +697,340 @@ __global__ void __launch_bounds__(256, 3) k_extract_tiled(
 #pragma unroll
         for (int c = 0; c < 6; ++c) Cs[(cp + tx * 6 + c) * kAS + ty * 4 + i] = acc[i][c];
     }
-    // ---- smoothed window values (tile x G), running first maximum per spectrum
-    float best[4];
-    int bj[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      best[i] = -INFINITY;
-      bj[i] = 0x7fffffff;
-    }
-    // chunks run column tile by column tile, the next chunk of G copied into
-    // the other shared buffer (cp.async) while this one is multiplied
-    {
-      const int nr = k2p / kJC, nchunks = nr * (nw_p / kNT);
-      auto g_src = [&](int ch) {
-        return G + (size_t)((ch % nr) * kJC) * nw_p + (ch / nr) * kNT;
-      };
-      float acc[4][6];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) acc[i][c] = 0.0f;
-      __syncthreads();                               // B buffers free
-      if (nchunks) load_chunk_async(Bs, g_src(0), (size_t)nw_p, tid);
-      for (int ch = 0; ch < nchunks; ++ch) {
-        cp_async_wait_all();
-        __syncthreads();                             // this chunk visible; the other buffer free
-        if (ch + 1 < nchunks)
-          load_chunk_async(Bs + ((ch + 1) & 1) * (kJC * kNT), g_src(ch + 1), (size_t)nw_p, tid);
-        tile_fma(Cs + (ch % nr) * kJC * kAS, Bs + (ch & 1) * (kJC * kNT), kJC, ty, tx, acc);
-        if (ch % nr == nr - 1) {
-          const int wp = (ch / nr) * kNT;
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            const int j = wp + tx * 6 + c;
-            if (j < n_w) {
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-                if (acc[i][c] > best[i]) {
-                  best[i] = acc[i][c];
-                  bj[i] = j_lo + j;
-                }
-            }
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) acc[i][c] = 0.0f;
-        }
-      }
-    }
-    // reduce over the 16 threads sharing ty (lanes 0-15 and 16-31 of a warp)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      for (int o = 8; o; o >>= 1) {
-        const float ov = __shfl_xor_sync(kFull, best[i], o);
-        const int oj = __shfl_xor_sync(kFull, bj[i], o);
-        if (ov > best[i] || (ov == best[i] && oj < bj[i])) {
-          best[i] = ov;
-          bj[i] = oj;
-        }
-      }
-      if (tx == 0) {
-        red_v[ty * 4 + i] = best[i];
-        red_j[ty * 4 + i] = bj[i];
-      }
-    }
-    __syncthreads();
-    // ---- per spectrum: status, Newton refinement, Eq. 35
-    for (int s = warp; s < kTS; s += blockDim.x / 32) {
-      const int gs = s0 + s;
-      if (gs >= n_spec) break;
-      const float bv = red_v[s];
-      const int J = red_j[s];
-      pdv_peak r;
-      r.x_peak = r.i_peak = r.curvature = r.beta = r.tau0 = NAN;
-      r.j_max = (n_w >= 1) ? J : -1;
-      r.status = PDV_PEAK_NO_PEAK;
-      if (n_w >= 1 && bv > 0.0f) {
-        if (J == j_lo || J == j_hi) {
-          r.status = PDV_PEAK_EDGE;
-        } else {
-          float d = 0.f, q0, q1, q2;
-          tile_smooth_eval(tw, Cs, s, n, k_c, J, d, lane, &q0, &q1, &q2);
-          for (int it = 0; it < kPeakNewton && q2 < 0.0f; ++it) {
-            const float nd = fminf(fmaxf(d - q1 / q2, -1.0f), 1.0f);
-            const bool done = fabsf(nd - d) <= 1e-6f;
-            d = nd;
-            if (done) break;
-            tile_smooth_eval(tw, Cs, s, n, k_c, J, d, lane, &q0, &q1, &q2);
-          }
-          peak_finish(r, J, d, q0, q2, 1.0f / (float)n, geom);
-        }
-      }
-      if (lane == 0) out[gs] = r;
-    }
-    __syncthreads();
+    tile_peaks<kAS>(Cs, s0, n_spec, n, k_c, j_lo, j_hi, geom, tw, G, k2p, nw_p, Bs, red_v, red_j,
+                    out, tid);
   }
+}
+
+// ------------------------------------------------------------------ tensor-core extraction
+// The first product (the DFT coefficients of a tile of kTcM = 128 spectra) on
+// the tensor cores: tcgen05.mma kind::tf32 with both operands in shared memory
+// (K-major, 128-byte swizzle) and FP32 accumulators in tensor memory (lane =
+// spectrum, column = coefficient row).
+//  * FP32 accuracy from TF32 operands: x = hi + lo with hi = x rounded to TF32
+//    and lo = the remainder rounded to TF32, three products per step,
+//    hi*hi + hi*lo + lo*hi; the dropped lo*lo and the rounding of lo are each
+//    below 2^-22 of |x| |F|.
+//  * The tensor core adds into its FP32 accumulator with truncation, so the
+//    sums are kept short: hi*hi and the two correction products go to separate
+//    accumulators, and every kTcG chunks (128 bins) both are added into the
+//    coefficient array in FP32 (round to nearest) while the next group
+//    accumulates into a second pair.
+//  * The spectra are read as FP64, converted to FP32 in integer operations,
+//    split and stored by the threads; the split cosine/sine matrix comes from a
+//    table built once per call, by cp.async. Chunks of kTcKC bins alternate
+//    between two shared buffers: while the tensor core multiplies one, the
+//    threads fill the other, and mbarriers that the products' commits arrive
+//    on free buffers and accumulator pairs. Every wait is bounded; a timeout
+//    sets the error word, waits once more for the products in flight, frees
+//    the tensor memory and returns.
+//  * Stage 2 (window product, maximum, Newton refinement, Eq. 35) runs on the
+//    CUDA cores as in the tiled kernel, its two halves of kTS spectra side by
+//    side on the block's two groups of 256 threads.
+constexpr int kTcM = 128;                  // spectra per tile: the products' M
+constexpr int kTcKC = 32;                  // bins per chunk: one 128-byte row, four steps of K = 8
+constexpr int kTcG = 4;                    // chunks an accumulator pair sums before it is added up
+constexpr int kTcThreads = 512;
+constexpr int kTcAS = kTcM + 4;            // row stride of the coefficient array
+constexpr uint32_t kTcCols = 512;          // tensor-memory columns: two pairs of nt <= 128
+constexpr int kTcWaitLimit = 1 << 20;      // polls of an mbarrier before a wait gives up
+
+struct TcSmem {
+  size_t o_a, o_b, o_c, o_red, o_bar, bytes;
+};
+
+__host__ __device__ inline size_t align1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
+
+// nt: the products' N (coefficient rows, a multiple of 16, <= 128); k2s: rows
+// of the coefficient array and of G (a multiple of kJC, >= nt). Offsets from a
+// 1024-byte aligned base (the launch adds 1 KB for that alignment).
+__host__ __device__ inline TcSmem tc_layout(int nt, int k2s) {
+  TcSmem L;
+  const size_t a_tile = sizeof(float) * kTcM * kTcKC, b_tile = sizeof(float) * (size_t)nt * kTcKC;
+  L.o_a = 0;                                         // [buffer][hi, lo] spectra tiles
+  L.o_b = align1k(L.o_a + 4 * a_tile);               // [buffer][hi, lo] matrix tiles
+  L.o_c = align1k(L.o_b + 4 * b_tile);               // [k2s][kTcAS] coefficients
+  L.o_red = L.o_c + sizeof(float) * (size_t)k2s * kTcAS;
+  L.o_bar = (L.o_red + 2 * (sizeof(float) + sizeof(int)) * kTS + 15) & ~(size_t)15;
+  L.bytes = L.o_bar + 48;                            // four mbarriers, the tensor-memory address
+  return L;
+}
+
+// byte offset of the 16 bytes holding bins 4 ch .. 4 ch + 3 of row r in a
+// K-major tile with 128-byte rows: 8-row atoms of 1024 bytes, the 16-byte
+// unit index XORed with the row within the atom (the 128-byte swizzle)
+__device__ __forceinline__ uint32_t sw128(int r, int ch) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4));
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor, K-major with 128-byte swizzle: start
+// address, leading offset 16 bytes (unused for this layout), stride 1024
+// bytes between 8-row atoms, descriptor version 1 (bits 46-48), swizzle mode 2
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// D[tmem] (+)= A B^T, M = kTcM, N from the instruction descriptor, K = 8
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// the mbarrier tracks completion of every product this thread issued before
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < kTcWaitLimit && !done; ++it)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+  return done != 0;
+}
+
+// 16 consecutive columns of this warp's 32 tensor-memory lanes, one lane per thread
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+// FTh / FTl: [nt][n_k], row r = 2k the cosine and 2k + 1 the sine of
+// 2 pi j k / n (zero for k > k_c or j >= n), split into TF32 hi + lo from FP64.
+// G: [k2s][nw_p] as in k_peak_mats.
+__global__ void k_peak_mats_tc(int n, int k_c, int n_k, int nt, int k2s, int j_lo, int n_w,
+                               int nw_p, float* FTh, float* FTl, float* G) {
+  const long long nF = (long long)nt * n_k, nG = (long long)k2s * nw_p;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nF + nG;
+       t += (long long)gridDim.x * blockDim.x) {
+    if (t < nF) {
+      const int r = (int)(t / n_k), j = (int)(t % n_k), k = r >> 1;
+      double v = 0.0;
+      if (j < n && k <= k_c) {
+        double sn, cs;
+        sincospi(2.0 * (double)(((long long)j * k) % n) / n, &sn, &cs);
+        v = (r & 1) ? sn : cs;
+      }
+      const float hi = __uint_as_float(to_tf32((float)v));
+      FTh[t] = hi;
+      FTl[t] = __uint_as_float(to_tf32((float)(v - (double)hi)));
+    } else {
+      const long long u = t - nF;
+      const int r = (int)(u / nw_p), j = (int)(u % nw_p), k = r >> 1;
+      float v = 0.0f;
+      if (j < n_w && k <= k_c && !(k == 0 && (r & 1))) {
+        double sn, cs;
+        sincospi(2.0 * (double)(((long long)(j_lo + j) * k) % n) / n, &sn, &cs);
+        v = (float)(((r & 1) ? sn : cs) * (k == 0 ? 1.0 : 2.0) / n);
+      }
+      G[u] = v;
+    }
+  }
+}
+
+// Adds accumulator pair `set` (hi*hi and corrections, nt columns each) into
+// Cs: warp w reads lanes 32 (w & 3) .. + 31 and every fourth group of 16 columns.
+__device__ __forceinline__ void tc_flush(uint32_t tmem, int set, int nt, float* Cs, int warp,
+                                         int lane) {
+  const int q = warp & 3, row = q * 32 + lane;
+  const uint32_t lanes = (uint32_t)(q * 32) << 16;
+  for (int c0 = (warp >> 2) * 16; c0 < nt; c0 += 64) {
+    uint32_t m[16], e[16];
+    tc_ld16(tmem + lanes + (uint32_t)(set * 2 * nt + c0), m);
+    tc_ld16(tmem + lanes + (uint32_t)(set * 2 * nt + nt + c0), e);
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      Cs[(c0 + j) * kTcAS + row] += __uint_as_float(m[j]) + __uint_as_float(e[j]);
+  }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_extract_tc(
+    const double* spec, int n_spec, int n, int k_c, int j_lo, int j_hi, PeakGeom geom,
+    const float2* tw, const float* FTh, const float* FTl, const float* G, int n_k, int nt, int k2s,
+    int nw_p, pdv_peak* out, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // the swizzled tiles need 1024-byte alignment of their shared-memory addresses
+  unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  const TcSmem L = tc_layout(nt, k2s);
+  unsigned char* As = smem + L.o_a;
+  unsigned char* Bsm = smem + L.o_b;
+  float* Cs = reinterpret_cast<float*>(smem + L.o_c);
+  float* red_v = reinterpret_cast<float*>(smem + L.o_red);
+  int* red_j = reinterpret_cast<int*>(red_v + 2 * kTS);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.o_bar);     // [0, 1]: buffers; [2, 3]: pairs
+  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(smem + L.o_bar + 32);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int half = tid >> 8, ltid = tid & 255;
+  // stage 2's G buffers (two per half) reuse the spectra tiles
+  float* Bs2 = reinterpret_cast<float*>(smem + L.o_a) + half * (2 * kJC * kNT);
+  const size_t a_tile = sizeof(float) * kTcM * kTcKC, b_tile = sizeof(float) * (size_t)nt * kTcKC;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(taddr_s)),
+                 "r"(kTcCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *taddr_s;
+  // F32 accumulator, TF32 A and B, both K-major, N = nt, M = kTcM
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nt >> 3) << 17) |
+                         ((uint32_t)(kTcM >> 4) << 24);
+  uint32_t ph[4] = {0u, 0u, 0u, 0u};                // parity of each mbarrier's next completion
+  int fail = 0;
+  const int n_chunks = n_k / kTcKC, n_groups = (n_chunks + kTcG - 1) / kTcG;
+  const int n_tiles = (n_spec + kTcM - 1) / kTcM;
+  const int r = tid >> 2, qb = tid & 3;             // A fill: row r, bins 8 qb .. 8 qb + 7
+  auto wait = [&](int i) {
+    const bool ok = mbar_wait(&bar[i], ph[i]);
+    ph[i] ^= 1u;
+    return ok;
+  };
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int s0 = tile * kTcM, gs = s0 + r;
+    const double* row = spec + (size_t)(gs < n_spec ? gs : 0) * n;
+    for (int e = tid; e < k2s * kTcM; e += kTcThreads) Cs[(e / kTcM) * kTcAS + e % kTcM] = 0.0f;
+    double ra[8];
+    auto fetch = [&](int c) {
+      const int j0 = c * kTcKC + 8 * qb;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) ra[i] = (gs < n_spec && j0 + i < n) ? __ldcs(row + j0 + i) : 0.0;
+    };
+    fetch(0);
+    for (int c = 0; c < n_chunks; ++c) {
+      const int b = c & 1, g = c / kTcG, set = g & 1;
+      const bool first = c % kTcG == 0;
+      if (c >= 2 && __syncthreads_or(!wait(b))) {   // buffer b's products (chunk c - 2) done
+        fail = 1;
+        break;
+      }
+      if (first && g >= 2) {                         // pair `set` summed group g - 2: add it up
+        if (__syncthreads_or(!wait(2 + set))) {
+          fail = 1;
+          break;
+        }
+        tc_fence_after();
+        tc_flush(tmem, set, nt, Cs, warp, lane);
+        tc_fence_before();
+      }
+      unsigned char* Ah = As + (2 * b) * a_tile;
+      unsigned char* Al = Ah + a_tile;
+      unsigned char* Bh = Bsm + (2 * b) * b_tile;
+      unsigned char* Bl = Bh + b_tile;
+      // the matrix chunk: rows 0..nt-1, bins c kTcKC .. + kTcKC, 16 bytes (4 bins) a copy
+      for (int e = tid; e < nt * (kTcKC / 4); e += kTcThreads) {
+        const int rr = e >> 3, k4 = e & 7;
+        const size_t src = (size_t)rr * n_k + (size_t)c * kTcKC + 4 * k4;
+        cp_async16(Bh + sw128(rr, k4), FTh + src);
+        cp_async16(Bl + sw128(rr, k4), FTl + src);
+      }
+      cp_async_commit();
+      // the spectra chunk: convert, split, 4 bins of one row a 16-byte store
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const float x = f64_to_f32(ra[4 * u + t]);
+          hi[t] = to_tf32(x);
+          lo[t] = to_tf32(x - __uint_as_float(hi[t]));
+        }
+        const uint32_t off = sw128(r, 2 * qb + u);
+        *reinterpret_cast<uint4*>(Ah + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(Al + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+      if (c + 1 < n_chunks) fetch(c + 1);           // in flight during this chunk's products
+      cp_async_wait_all();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0) {
+        const uint32_t ah = smem_addr(Ah), al = smem_addr(Al), bh = smem_addr(Bh), bl = smem_addr(Bl);
+        const uint32_t dm = tmem + (uint32_t)(set * 2 * nt), dc = dm + (uint32_t)nt;
+#pragma unroll
+        for (int ks = 0; ks < kTcKC / 8; ++ks) {
+          const uint32_t o = (uint32_t)ks * 32;     // 8 bins along the 128-byte row
+          const uint32_t acc = (first && ks == 0) ? 0u : 1u;
+          tc_mma(dm, tc_desc(ah + o), tc_desc(bh + o), idesc, acc);
+          tc_mma(dc, tc_desc(ah + o), tc_desc(bl + o), idesc, acc);
+          tc_mma(dc, tc_desc(al + o), tc_desc(bh + o), idesc, 1u);
+        }
+        tc_commit(&bar[b]);
+        if (c % kTcG == kTcG - 1 || c == n_chunks - 1) tc_commit(&bar[2 + set]);
+      }
+    }
+    if (fail) break;
+    // the buffers' outstanding completions, then the pairs not yet added up
+    bool ok = wait(0);
+    if (n_chunks > 1) ok = wait(1) && ok;
+    for (int g = n_groups >= 2 ? n_groups - 2 : 0; g < n_groups; ++g) {
+      ok = wait(2 + (g & 1)) && ok;
+      if (__syncthreads_or(!ok)) {
+        fail = 1;
+        break;
+      }
+      tc_fence_after();
+      tc_flush(tmem, g & 1, nt, Cs, warp, lane);
+    }
+    if (fail) break;
+    tc_fence_before();
+    __syncthreads();
+    tile_peaks<kTcAS>(Cs + half * kTS, s0 + half * kTS, n_spec, n, k_c, j_lo, j_hi, geom, tw, G,
+                      k2s, nw_p, Bs2, red_v + half * kTS, red_j + half * kTS, out, ltid);
+  }
+  if (fail) {
+    if (tid == 0) atomicExch(err, 1);
+    // the products still in flight, once more with a bound, before the tensor memory is freed
+    for (int i = 0; i < 4; ++i) (void)mbar_wait(&bar[i], ph[i]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols)
+                 : "memory");
 }
 
 }  // namespace
@@ -777,4 +1128,62 @@ cudaError_t launch_extract_tiled(const double* d_spec, int n_spec, int n, int k_
   return cudaGetLastError();
 }
 
+// ---- tensor-core extraction
+static int tc_nt(int k_c) { return pad_to(2 * (k_c + 1), 16); }
+static int tc_k2s(int k_c) { return pad_to(tc_nt(k_c), kJC); }
+
+// the layout plus 1 KB for aligning its base, and at least half an SM's
+// shared memory so that one block (which holds all 512 tensor-memory
+// columns) runs per SM
+size_t tc_smem(int k_c) {
+  const size_t b = tc_layout(tc_nt(k_c), tc_k2s(k_c)).bytes + 1024;
+  return b > 120 * 1024 ? b : 120 * 1024;
+}
+
+bool peak_tc(int k_c, int max_smem) {
+  return tc_nt(k_c) <= 128 && tc_smem(k_c) <= (size_t)max_smem;
+}
+
+size_t peak_mats_tc_bytes(int n, int k_c, int n_w) {
+  const size_t nt = tc_nt(k_c), k2s = tc_k2s(k_c), n_k = pad_to(n, kTcKC);
+  const size_t nw_p = pad_to(n_w > 0 ? n_w : 0, kNT);
+  return sizeof(float) * (2 * nt * n_k + k2s * nw_p) + 64;
+}
+
+cudaError_t tc_occupancy(int k_c, int* blocks_per_sm) {
+  const size_t sm = tc_smem(k_c);
+  cudaError_t e = cudaFuncSetAttribute(k_extract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_extract_tc, kTcThreads, sm);
+  if (*blocks_per_sm > 1) *blocks_per_sm = 1;       // a block holds every tensor-memory column
+  return e;
+}
+
+cudaError_t launch_extract_tc(const double* d_spec, int n_spec, int n, int k_c, int j_lo, int j_hi,
+                              PeakGeom geom, const float2* d_tw, float* d_mats, pdv_peak* d_out,
+                              int* d_err, int blocks_per_sm, int sm_count, cudaStream_t st,
+                              cudaEvent_t e0, cudaEvent_t e1) {
+  const int nt = tc_nt(k_c), k2s = tc_k2s(k_c), n_k = pad_to(n, kTcKC);
+  const int n_w = j_hi - j_lo + 1 > 0 ? j_hi - j_lo + 1 : 0;
+  const int nw_p = pad_to(n_w, kNT);
+  float* FTh = d_mats;
+  float* FTl = FTh + (size_t)nt * n_k;
+  float* G = FTl + (size_t)nt * n_k;
+  const long long nm = 2LL * nt * n_k + (long long)k2s * nw_p;
+  k_peak_mats_tc<<<(int)std::min<long long>((nm + 255) / 256, 4096), 256, 0, st>>>(
+      n, k_c, n_k, nt, k2s, j_lo, n_w, nw_p, FTh, FTl, G);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int n_tiles = (n_spec + kTcM - 1) / kTcM;
+  const int grid = std::min(n_tiles, blocks_per_sm * sm_count);
+  if (e0) cudaEventRecord(e0, st);
+  k_extract_tc<<<grid, kTcThreads, tc_smem(k_c), st>>>(d_spec, n_spec, n, k_c, j_lo, j_hi, geom,
+                                                       d_tw, FTh, FTl, G, n_k, nt, k2s, nw_p, d_out,
+                                                       d_err);
+  if (e1) cudaEventRecord(e1, st);
+  return cudaGetLastError();
+}
+
 }  // namespace pdv
+

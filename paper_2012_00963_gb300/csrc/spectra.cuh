@@ -54,4 +54,14 @@ cudaError_t launch_extract_tiled(const double* d_spec, int n_spec, int n, int k_
                                  int blocks_per_sm, int sm_count, cudaStream_t st,
                                  cudaEvent_t e0, cudaEvent_t e1);
 
+// Tensor-core extraction (128 spectra per block; the DFT product on tcgen05
+// in split TF32, stage 2 as in the tiled kernel), where its shared memory fits.
+bool peak_tc(int k_c, int max_smem);
+size_t peak_mats_tc_bytes(int n, int k_c, int n_w);
+cudaError_t tc_occupancy(int k_c, int* blocks_per_sm);
+cudaError_t launch_extract_tc(const double* d_spec, int n_spec, int n, int k_c, int j_lo, int j_hi,
+                              PeakGeom geom, const float2* d_tw, float* d_mats, pdv_peak* d_out,
+                              int* d_err, int blocks_per_sm, int sm_count, cudaStream_t st,
+                              cudaEvent_t e0, cudaEvent_t e1);
+
 }  // namespace pdv
