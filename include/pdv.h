@@ -57,8 +57,8 @@ enum { PDV_PREC_FP32 = 0, PDV_PREC_FP64 = 1 };
 #define PDV_PER_DV     0x2u   /* spectrum divided by the bin width (per m/s)   */
 #define PDV_IN_DEVICE  0x4u   /* input arrays are device pointers (pdv_ss_spectrum,
                                  pdv_extract_peaks)                            */
-#define PDV_EXTRACT_TENSOR 0x40u /* pdv_extract_peaks: the DFT product on the tensor
-                                   cores (tcgen05, split TF32) where it fits     */
+#define PDV_EXTRACT_SIMT 0x40u /* pdv_extract_peaks: both products as FP32 FMAs on the
+                                 CUDA cores instead of the tensor cores         */
 /* Implicit capture with Russian roulette, in place of the analog absorption
  * of Eq. 11 (Section II.B step (4)); off by default, exact free paths only
  * (n_layers == 0), both precisions. At every particle interaction the packet
@@ -408,12 +408,13 @@ typedef struct {
 /* Extract the main peak of n_spectra spectra of n_bins uniform bins over
  * [v_lo, v_hi] (row-major [n_spectra][n_bins]). Arithmetic is FP32 with
  * cosine / sine tables computed in FP64 and rounded to FP32; inputs are
- * rounded to FP32 (magnitudes below 1.2e-38 flush to zero). The DFT product
- * runs as FP32 FMAs on the CUDA cores; with PDV_EXTRACT_TENSOR and k_c <= 63
- * it runs on the tensor cores instead (TF32 operands split into a high and a
- * low part, three products per step, so each term carries at most about
- * 2^-22 of |x| |F| of error, and short FP32 sums of the truncating
- * accumulators). Accuracy: about 1e-6 relative in x_peak,
+ * rounded to FP32 (magnitudes below 1.2e-38 flush to zero). For k_c <= 63
+ * the two products (the DFT and the window values) run on the tensor cores:
+ * TF32 operands split into a high and a low part, three products per step,
+ * so each term carries at most about 2^-22 of |x| |F| of error, and the
+ * truncating accumulators are summed in short runs and added in FP32. Larger
+ * cut-offs, and every cut-off with PDV_EXTRACT_SIMT, run them as FP32 FMAs on
+ * the CUDA cores. Accuracy: about 1e-6 relative in x_peak,
  * I''/I, beta and tau0 while the cut-off smooths
  * (k_c well below n_bins / 2); as k_c nears n_bins / 2 the
  * FP32 rounding of the input itself, amplified by up to pi^2 per bin in the

@@ -1971,7 +1971,7 @@ extern "C" pdv_status pdv_extract_peaks(pdv_ctx* c, const double* spectra, int n
   if (!(v_hi > v_lo) || !std::isfinite(v_lo) || !std::isfinite(v_hi) || !(v_fs > 0.0) || !std::isfinite(v_fs))
     return fail(PDV_EINVAL, "need finite v_lo < v_hi and v_fs > 0");
   if (std::isnan(opts->x_min) || std::isnan(opts->x_max)) return fail(PDV_EINVAL, "window bounds are NaN");
-  if (flags & ~(PDV_IN_DEVICE | PDV_OUT_DEVICE | PDV_EXTRACT_TENSOR)) return fail(PDV_EINVAL, "unknown flags");
+  if (flags & ~(PDV_IN_DEVICE | PDV_OUT_DEVICE | PDV_EXTRACT_SIMT)) return fail(PDV_EINVAL, "unknown flags");
   if (n_spectra == 0) return PDV_OK;
   if (!spectra || !out) return fail(PDV_EINVAL, "spectra and out must not be NULL");
   const bool dev_in = (flags & PDV_IN_DEVICE) != 0, dev_out = (flags & PDV_OUT_DEVICE) != 0;
@@ -1986,10 +1986,10 @@ extern "C" pdv_status pdv_extract_peaks(pdv_ctx* c, const double* spectra, int n
   CK(enter(c->device));
   std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t st = c->stream;
-  // with PDV_EXTRACT_TENSOR the tensor-core kernel (128 spectra per block)
-  // where it fits; else cut-offs up to 95 modes take the tiled kernel (64
+  // the tensor-core kernel (128 spectra per block) where it fits, unless
+  // PDV_EXTRACT_SIMT; else cut-offs up to 95 modes take the tiled kernel (64
   // spectra per block), larger ones the one-spectrum-per-block kernel
-  const bool tc = (flags & PDV_EXTRACT_TENSOR) && peak_tc(opts->k_c, c->smem_optin);
+  const bool tc = !(flags & PDV_EXTRACT_SIMT) && peak_tc(opts->k_c, c->smem_optin);
   const bool tiled = !tc && peak_tiled(opts->k_c);
   int occ = 0;
   if (tc) CK(tc_occupancy(opts->k_c, &occ));

@@ -246,8 +246,8 @@ __device__ __forceinline__ void smooth_eval(const float2* tw, const float2* ab, 
                                             float* s2) {
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   const float two_over_n = 2.0f / (float)n;
-  int m = (int)(((long long)lane * J) % n);         // (k J) mod n, k = lane + 32 i
-  const int step = (int)((32LL * J) % n);
+  int m = (lane * J) % n;                           // (k J) mod n, k = lane + 32 i (< 2^18: 32 bits)
+  const int step = (32 * J) % n;
   for (int k = lane; k <= k_c; k += 32, m = (m + step >= n) ? m + step - n : m + step) {
     float sp, cp;
     sincospif(two_over_n * (float)k * d, &sp, &cp);
@@ -475,8 +475,8 @@ __device__ __forceinline__ void tile_smooth_eval(const float2* tw, const float* 
                                                  float* s1, float* s2) {
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   const float two_over_n = 2.0f / (float)n;
-  int m = (int)(((long long)lane * J) % n);         // (k J) mod n, k = lane + 32 i
-  const int step = (int)((32LL * J) % n);
+  int m = (lane * J) % n;                           // (k J) mod n, k = lane + 32 i (< 2^18: 32 bits)
+  const int step = (32 * J) % n;
   for (int k = lane; k <= k_c; k += 32, m = (m + step >= n) ? m + step - n : m + step) {
     float sp, cp;
     sincospif(two_over_n * (float)k * d, &sp, &cp);
@@ -519,6 +519,46 @@ __device__ __forceinline__ void load_chunk_async(float* dst, const float* src, s
     cp_async16(dst + 4 * e, src + (size_t)r * ld + 4 * c4);
   }
   cp_async_commit();
+}
+
+// The per-spectrum end of stage 2 for n_sp spectra (the first at global index
+// s0): status, Newton refinement from the coefficients (Cs mode-major, row
+// stride AS) and Eq. 35, from each spectrum's first window maximum (red_v,
+// red_j: value and absolute bin). One warp per spectrum; warps warp,
+// warp + n_warps, ... of the calling group.
+template <int AS>
+__device__ __forceinline__ void tile_finish(const float* Cs, const float* red_v, const int* red_j,
+                                            int n_sp, int s0, int n_spec, int n, int k_c, int j_lo,
+                                            int j_hi, PeakGeom geom, const float2* tw,
+                                            pdv_peak* out, int warp, int n_warps, int lane) {
+  const int n_w = j_hi - j_lo + 1;
+  for (int s = warp; s < n_sp; s += n_warps) {
+    const int gs = s0 + s;
+    if (gs >= n_spec) break;
+    const float bv = red_v[s];
+    const int J = red_j[s];
+    pdv_peak r;
+    r.x_peak = r.i_peak = r.curvature = r.beta = r.tau0 = NAN;
+    r.j_max = (n_w >= 1) ? J : -1;
+    r.status = PDV_PEAK_NO_PEAK;
+    if (n_w >= 1 && bv > 0.0f) {
+      if (J == j_lo || J == j_hi) {
+        r.status = PDV_PEAK_EDGE;
+      } else {
+        float d = 0.f, q0, q1, q2;
+        tile_smooth_eval<AS>(tw, Cs, s, n, k_c, J, d, lane, &q0, &q1, &q2);
+        for (int it = 0; it < kPeakNewton && q2 < 0.0f; ++it) {
+          const float nd = fminf(fmaxf(d - q1 / q2, -1.0f), 1.0f);
+          const bool done = fabsf(nd - d) <= 1e-6f;
+          d = nd;
+          if (done) break;
+          tile_smooth_eval<AS>(tw, Cs, s, n, k_c, J, d, lane, &q0, &q1, &q2);
+        }
+        peak_finish(r, J, d, q0, q2, 1.0f / (float)n, geom);
+      }
+    }
+    if (lane == 0) out[gs] = r;
+  }
 }
 
 // Stage 2 of a tile of kTS spectra (the first at global index s0): smoothed
@@ -601,34 +641,8 @@ __device__ __forceinline__ void tile_peaks(const float* Cs, int s0, int n_spec, 
     }
   }
   __syncthreads();
-  // ---- per spectrum: status, Newton refinement, Eq. 35
-  for (int s = warp; s < kTS; s += 256 / 32) {
-    const int gs = s0 + s;
-    if (gs >= n_spec) break;
-    const float bv = red_v[s];
-    const int J = red_j[s];
-    pdv_peak r;
-    r.x_peak = r.i_peak = r.curvature = r.beta = r.tau0 = NAN;
-    r.j_max = (n_w >= 1) ? J : -1;
-    r.status = PDV_PEAK_NO_PEAK;
-    if (n_w >= 1 && bv > 0.0f) {
-      if (J == j_lo || J == j_hi) {
-        r.status = PDV_PEAK_EDGE;
-      } else {
-        float d = 0.f, q0, q1, q2;
-        tile_smooth_eval<AS>(tw, Cs, s, n, k_c, J, d, lane, &q0, &q1, &q2);
-        for (int it = 0; it < kPeakNewton && q2 < 0.0f; ++it) {
-          const float nd = fminf(fmaxf(d - q1 / q2, -1.0f), 1.0f);
-          const bool done = fabsf(nd - d) <= 1e-6f;
-          d = nd;
-          if (done) break;
-          tile_smooth_eval<AS>(tw, Cs, s, n, k_c, J, d, lane, &q0, &q1, &q2);
-        }
-        peak_finish(r, J, d, q0, q2, 1.0f / (float)n, geom);
-      }
-    }
-    if (lane == 0) out[gs] = r;
-  }
+  tile_finish<AS>(Cs, red_v, red_j, kTS, s0, n_spec, n, k_c, j_lo, j_hi, geom, tw, out, warp,
+                  256 / 32, lane);
   __syncthreads();
 }
 
@@ -724,15 +738,19 @@ __global__ void __launch_bounds__(256, 3) k_extract_tiled(
 //    on free buffers and accumulator pairs. Every wait is bounded; a timeout
 //    sets the error word, waits once more for the products in flight, frees
 //    the tensor memory and returns.
-//  * Stage 2 (window product, maximum, Newton refinement, Eq. 35) runs on the
-//    CUDA cores as in the tiled kernel, its two halves of kTS spectra side by
-//    side on the block's two groups of 256 threads.
+//  * Stage 2: the smoothed window values W = C G (coefficients times the
+//    window's cosine/sine matrix) are a second product on the tensor cores,
+//    in passes of kTcN2 window bins with the coefficients split the same way
+//    and their own pair of accumulators; each thread then scans its
+//    spectrum's row of W in tensor memory for the first maximum, and one warp
+//    per spectrum runs the Newton refinement and Eq. 35 on the CUDA cores.
 constexpr int kTcM = 128;                  // spectra per tile: the products' M
 constexpr int kTcKC = 32;                  // bins per chunk: one 128-byte row, four steps of K = 8
 constexpr int kTcG = 4;                    // chunks an accumulator pair sums before it is added up
 constexpr int kTcThreads = 512;
 constexpr int kTcAS = kTcM + 4;            // row stride of the coefficient array
 constexpr uint32_t kTcCols = 512;          // tensor-memory columns: two pairs of nt <= 128
+constexpr int kTcN2 = 256;                 // most window bins in a pass of the second product
 constexpr int kTcWaitLimit = 1 << 20;      // polls of an mbarrier before a wait gives up
 
 struct TcSmem {
@@ -749,10 +767,11 @@ __host__ __device__ inline TcSmem tc_layout(int nt, int k2s) {
   const size_t a_tile = sizeof(float) * kTcM * kTcKC, b_tile = sizeof(float) * (size_t)nt * kTcKC;
   L.o_a = 0;                                         // [buffer][hi, lo] spectra tiles
   L.o_b = align1k(L.o_a + 4 * a_tile);               // [buffer][hi, lo] matrix tiles
-  L.o_c = align1k(L.o_b + 4 * b_tile);               // [k2s][kTcAS] coefficients
-  L.o_red = L.o_c + sizeof(float) * (size_t)k2s * kTcAS;
-  L.o_bar = (L.o_red + 2 * (sizeof(float) + sizeof(int)) * kTS + 15) & ~(size_t)15;
-  L.bytes = L.o_bar + 48;                            // four mbarriers, the tensor-memory address
+  // the B tiles' space also holds stage 2's split coefficient tiles (2 a_tile)
+  L.o_c = align1k(L.o_b + (4 * b_tile > 2 * a_tile ? 4 * b_tile : 2 * a_tile));
+  L.o_red = L.o_c + sizeof(float) * (size_t)k2s * kTcAS;      // window maxima: 5 x kTcM pairs
+  L.o_bar = (L.o_red + 5 * (sizeof(float) + sizeof(int)) * kTcM + 15) & ~(size_t)15;
+  L.bytes = L.o_bar + 64;                            // five mbarriers, the tensor-memory address
   return L;
 }
 
@@ -832,9 +851,10 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 
 // FTh / FTl: [nt][n_k], row r = 2k the cosine and 2k + 1 the sine of
 // 2 pi j k / n (zero for k > k_c or j >= n), split into TF32 hi + lo from FP64.
-// G: [k2s][nw_p] as in k_peak_mats.
+// GTh / GTl: [nw_p][k2s], the window matrix of k_peak_mats transposed (row =
+// window bin, column = coefficient row), split the same way.
 __global__ void k_peak_mats_tc(int n, int k_c, int n_k, int nt, int k2s, int j_lo, int n_w,
-                               int nw_p, float* FTh, float* FTl, float* G) {
+                               int nw_p, float* FTh, float* FTl, float* GTh, float* GTl) {
   const long long nF = (long long)nt * n_k, nG = (long long)k2s * nw_p;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nF + nG;
        t += (long long)gridDim.x * blockDim.x) {
@@ -851,14 +871,16 @@ __global__ void k_peak_mats_tc(int n, int k_c, int n_k, int nt, int k2s, int j_l
       FTl[t] = __uint_as_float(to_tf32((float)(v - (double)hi)));
     } else {
       const long long u = t - nF;
-      const int r = (int)(u / nw_p), j = (int)(u % nw_p), k = r >> 1;
-      float v = 0.0f;
+      const int j = (int)(u / k2s), r = (int)(u % k2s), k = r >> 1;
+      double v = 0.0;
       if (j < n_w && k <= k_c && !(k == 0 && (r & 1))) {
         double sn, cs;
         sincospi(2.0 * (double)(((long long)(j_lo + j) * k) % n) / n, &sn, &cs);
-        v = (float)(((r & 1) ? sn : cs) * (k == 0 ? 1.0 : 2.0) / n);
+        v = ((r & 1) ? sn : cs) * (k == 0 ? 1.0 : 2.0) / n;
       }
-      G[u] = v;
+      const float hi = __uint_as_float(to_tf32((float)v));
+      GTh[u] = hi;
+      GTl[u] = __uint_as_float(to_tf32((float)(v - (double)hi)));
     }
   }
 }
@@ -881,8 +903,8 @@ __device__ __forceinline__ void tc_flush(uint32_t tmem, int set, int nt, float* 
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_extract_tc(
     const double* spec, int n_spec, int n, int k_c, int j_lo, int j_hi, PeakGeom geom,
-    const float2* tw, const float* FTh, const float* FTl, const float* G, int n_k, int nt, int k2s,
-    int nw_p, pdv_peak* out, int* err) {
+    const float2* tw, const float* FTh, const float* FTl, const float* GTh, const float* GTl,
+    int n_k, int nt, int k2s, int nw_p, pdv_peak* out, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // the swizzled tiles need 1024-byte alignment of their shared-memory addresses
   unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
@@ -890,14 +912,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_extract_tc(
   unsigned char* As = smem + L.o_a;
   unsigned char* Bsm = smem + L.o_b;
   float* Cs = reinterpret_cast<float*>(smem + L.o_c);
-  float* red_v = reinterpret_cast<float*>(smem + L.o_red);
-  int* red_j = reinterpret_cast<int*>(red_v + 2 * kTS);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.o_bar);     // [0, 1]: buffers; [2, 3]: pairs
-  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(smem + L.o_bar + 32);
+  float* red_v = reinterpret_cast<float*>(smem + L.o_red);         // [kTcM] first window maximum
+  int* red_j = reinterpret_cast<int*>(red_v + kTcM);
+  float* red4_v = reinterpret_cast<float*>(red_j + kTcM);          // [4][kTcM] per column group
+  int* red4_j = reinterpret_cast<int*>(red4_v + 4 * kTcM);
+  // [0, 1]: buffers; [2, 3]: accumulator pairs; [4]: the second product
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.o_bar);
+  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(smem + L.o_bar + 48);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int half = tid >> 8, ltid = tid & 255;
-  // stage 2's G buffers (two per half) reuse the spectra tiles
-  float* Bs2 = reinterpret_cast<float*>(smem + L.o_a) + half * (2 * kJC * kNT);
   const size_t a_tile = sizeof(float) * kTcM * kTcKC, b_tile = sizeof(float) * (size_t)nt * kTcKC;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -907,7 +929,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_extract_tc(
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 5; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[i])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -918,7 +940,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_extract_tc(
   // F32 accumulator, TF32 A and B, both K-major, N = nt, M = kTcM
   const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nt >> 3) << 17) |
                          ((uint32_t)(kTcM >> 4) << 24);
-  uint32_t ph[4] = {0u, 0u, 0u, 0u};                // parity of each mbarrier's next completion
+  uint32_t ph[5] = {0u, 0u, 0u, 0u, 0u};            // parity of each mbarrier's next completion
+  const int n_w = j_hi - j_lo + 1;
   int fail = 0;
   const int n_chunks = n_k / kTcKC, n_groups = (n_chunks + kTcG - 1) / kTcG;
   const int n_tiles = (n_spec + kTcM - 1) / kTcM;
@@ -1018,13 +1041,112 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_extract_tc(
     if (fail) break;
     tc_fence_before();
     __syncthreads();
-    tile_peaks<kTcAS>(Cs + half * kTS, s0 + half * kTS, n_spec, n, k_c, j_lo, j_hi, geom, tw, G,
-                      k2s, nw_p, Bs2, red_v + half * kTS, red_j + half * kTS, out, ltid);
+    // ---- stage 2: W = C G in passes of kTcN2 window bins, K-chunks of kTcKC
+    // coefficient rows; the split tiles reuse the spectra tiles' buffer
+    const int q = warp & 3, cg = warp >> 2, srow = q * 32 + lane;   // scan: row srow, columns cg + 4 i
+    float bv = -INFINITY;
+    int bjx = 0x7fffffff;
+    unsigned char* A2h = Bsm;                        // split coefficients: 128 rows x 32 coefficient rows
+    unsigned char* A2l = Bsm + a_tile;
+    unsigned char* B2h = As;                         // split window matrix: up to kTcN2 rows
+    unsigned char* B2l = As + sizeof(float) * kTcN2 * kTcKC;     // 32 KB further: 256 rows x 128 B
+    for (int j0 = 0; j0 < nw_p && !fail; j0 += kTcN2) {
+      const int n2 = nw_p - j0 < kTcN2 ? nw_p - j0 : kTcN2;     // this pass's N (a multiple of 16)
+      const uint32_t idesc2 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n2 >> 3) << 17) |
+                              ((uint32_t)(kTcM >> 4) << 24);
+      for (int kc = 0; kc < k2s; kc += kTcKC) {
+        for (int e = tid; e < n2 * (kTcKC / 4); e += kTcThreads) {
+          const int rr = e >> 3, k4 = e & 7;
+          const size_t src = (size_t)(j0 + rr) * k2s + kc + 4 * k4;
+          cp_async16(B2h + sw128(rr, k4), GTh + src);
+          cp_async16(B2l + sw128(rr, k4), GTl + src);
+        }
+        cp_async_commit();
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const float x = Cs[(kc + 8 * qb + 4 * u + t) * kTcAS + r];
+            hi[t] = to_tf32(x);
+            lo[t] = to_tf32(x - __uint_as_float(hi[t]));
+          }
+          const uint32_t off = sw128(r, 2 * qb + u);
+          *reinterpret_cast<uint4*>(A2h + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(A2l + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+          const uint32_t ah = smem_addr(A2h), al = smem_addr(A2l), bh = smem_addr(B2h),
+                         bl = smem_addr(B2l);
+#pragma unroll
+          for (int ks = 0; ks < kTcKC / 8; ++ks) {
+            const uint32_t o = (uint32_t)ks * 32;
+            const uint32_t acc = (kc == 0 && ks == 0) ? 0u : 1u;
+            tc_mma(tmem, tc_desc(ah + o), tc_desc(bh + o), idesc2, acc);
+            tc_mma(tmem + kTcN2, tc_desc(ah + o), tc_desc(bl + o), idesc2, acc);
+            tc_mma(tmem + kTcN2, tc_desc(al + o), tc_desc(bh + o), idesc2, 1u);
+          }
+          tc_commit(&bar[4]);
+        }
+        if (__syncthreads_or(!wait(4))) {            // the split tiles are free again
+          fail = 1;
+          break;
+        }
+      }
+      if (fail) break;
+      tc_fence_after();
+      // this thread's groups of 16 window bins of spectrum srow (groups cg, cg + 4, ...):
+      // the first maximum, in bin order
+      for (int c0 = cg * 16; c0 < n2; c0 += 64) {
+        uint32_t m[16], e[16];
+        const uint32_t a = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+        tc_ld16(a, m);
+        tc_ld16(a + kTcN2, e);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int jj = j0 + c0 + j;
+          const float v = __uint_as_float(m[j]) + __uint_as_float(e[j]);
+          if (jj < n_w && v > bv) {
+            bv = v;
+            bjx = j_lo + jj;
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();                               // before the next pass writes the accumulators
+    }
+    if (fail) break;
+    red4_v[cg * kTcM + srow] = bv;
+    red4_j[cg * kTcM + srow] = bjx;
+    __syncthreads();
+    if (tid < kTcM) {                                // first maximum over the four column groups
+      float v = red4_v[tid];
+      int jx = red4_j[tid];
+      for (int g = 1; g < 4; ++g) {
+        const float ov = red4_v[g * kTcM + tid];
+        const int oj = red4_j[g * kTcM + tid];
+        if (ov > v || (ov == v && oj < jx)) {
+          v = ov;
+          jx = oj;
+        }
+      }
+      red_v[tid] = v;
+      red_j[tid] = jx;
+    }
+    __syncthreads();
+    tile_finish<kTcAS>(Cs, red_v, red_j, kTcM, s0, n_spec, n, k_c, j_lo, j_hi, geom, tw, out, warp,
+                       kTcThreads / 32, lane);
+    __syncthreads();                                 // Cs and the tiles free for the next tile
   }
   if (fail) {
     if (tid == 0) atomicExch(err, 1);
     // the products still in flight, once more with a bound, before the tensor memory is freed
-    for (int i = 0; i < 4; ++i) (void)mbar_wait(&bar[i], ph[i]);
+    for (int i = 0; i < 5; ++i) (void)mbar_wait(&bar[i], ph[i]);
   }
   tc_fence_before();
   __syncthreads();
@@ -1146,8 +1268,8 @@ bool peak_tc(int k_c, int max_smem) {
 
 size_t peak_mats_tc_bytes(int n, int k_c, int n_w) {
   const size_t nt = tc_nt(k_c), k2s = tc_k2s(k_c), n_k = pad_to(n, kTcKC);
-  const size_t nw_p = pad_to(n_w > 0 ? n_w : 0, kNT);
-  return sizeof(float) * (2 * nt * n_k + k2s * nw_p) + 64;
+  const size_t nw_p = pad_to(n_w > 0 ? n_w : 0, 16);
+  return sizeof(float) * (2 * nt * n_k + 2 * nw_p * k2s) + 64;
 }
 
 cudaError_t tc_occupancy(int k_c, int* blocks_per_sm) {
@@ -1166,21 +1288,22 @@ cudaError_t launch_extract_tc(const double* d_spec, int n_spec, int n, int k_c, 
                               cudaEvent_t e0, cudaEvent_t e1) {
   const int nt = tc_nt(k_c), k2s = tc_k2s(k_c), n_k = pad_to(n, kTcKC);
   const int n_w = j_hi - j_lo + 1 > 0 ? j_hi - j_lo + 1 : 0;
-  const int nw_p = pad_to(n_w, kNT);
+  const int nw_p = pad_to(n_w, 16);
   float* FTh = d_mats;
   float* FTl = FTh + (size_t)nt * n_k;
-  float* G = FTl + (size_t)nt * n_k;
+  float* GTh = FTl + (size_t)nt * n_k;
+  float* GTl = GTh + (size_t)nw_p * k2s;
   const long long nm = 2LL * nt * n_k + (long long)k2s * nw_p;
   k_peak_mats_tc<<<(int)std::min<long long>((nm + 255) / 256, 4096), 256, 0, st>>>(
-      n, k_c, n_k, nt, k2s, j_lo, n_w, nw_p, FTh, FTl, G);
+      n, k_c, n_k, nt, k2s, j_lo, n_w, nw_p, FTh, FTl, GTh, GTl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int n_tiles = (n_spec + kTcM - 1) / kTcM;
   const int grid = std::min(n_tiles, blocks_per_sm * sm_count);
   if (e0) cudaEventRecord(e0, st);
   k_extract_tc<<<grid, kTcThreads, tc_smem(k_c), st>>>(d_spec, n_spec, n, k_c, j_lo, j_hi, geom,
-                                                       d_tw, FTh, FTl, G, n_k, nt, k2s, nw_p, d_out,
-                                                       d_err);
+                                                       d_tw, FTh, FTl, GTh, GTl, n_k, nt, k2s, nw_p,
+                                                       d_out, d_err);
   if (e1) cudaEventRecord(e1, st);
   return cudaGetLastError();
 }

@@ -30,7 +30,7 @@ from . import build as _build
 PDV_OK, PDV_EINVAL, PDV_ENOMEM, PDV_ECUDA, PDV_EAGAIN = 0, -1, -2, -3, -4
 PDV_ENOTREADY, PDV_ETIMEOUT, PDV_ECANCELLED, PDV_EDEBUG = -5, -6, -7, -8
 PDV_OUT_DEVICE, PDV_PER_DV, PDV_IN_DEVICE, PDV_IMPLICIT_CAPTURE = 0x1, 0x2, 0x4, 0x8
-PDV_TEST_HORIZONTAL_LAUNCH, PDV_TEST_DEBUG_CHECK, PDV_EXTRACT_TENSOR = 0x10, 0x20, 0x40
+PDV_TEST_HORIZONTAL_LAUNCH, PDV_TEST_DEBUG_CHECK, PDV_EXTRACT_SIMT = 0x10, 0x20, 0x40
 DEBUG_SITES = ["none", "mass_guide", "mass_node", "phase_guide", "phase_node", "turn", "snapshot",
                "histogram", "packet", "selftest"]
 PDV_PEAK_OK, PDV_PEAK_NO_PEAK, PDV_PEAK_NOT_MAX, PDV_PEAK_EDGE = 0, 1, 2, 3
@@ -400,15 +400,15 @@ def pdv_ss_spectrum(ctx: int, sets, n_sets: int, n_bins: int, v_lo: float, v_hi:
 
 def pdv_extract_peaks(ctx: int, spectra, n_spectra: int, n_bins: int, v_lo: float, v_hi: float,
                       v_fs: float, k_c: int, x_min: float, x_max: float, out,
-                      tensor: bool = False):
+                      simt: bool = False):
     """Main-peak extraction (Eq. 29-35). ``spectra``: float64 [n_spectra, n_bins]
     (numpy or CUDA tensor); ``out``: PEAK_DTYPE array, or a CUDA uint8 tensor of
-    n_spectra * 48 bytes. ``tensor``: the DFT product on the tensor cores
-    (PDV_EXTRACT_TENSOR) where it fits."""
+    n_spectra * 48 bytes. ``simt``: both products as FP32 FMAs on the CUDA
+    cores (PDV_EXTRACT_SIMT) instead of the tensor cores."""
     ps, dev_in = _addr(spectra)
     po, dev_out = _addr(out)
     flags = (PDV_IN_DEVICE if dev_in else 0) | (PDV_OUT_DEVICE if dev_out else 0) | \
-        (PDV_EXTRACT_TENSOR if tensor else 0)
+        (PDV_EXTRACT_SIMT if simt else 0)
     o = pdv_peak_opts(k_c=k_c, reserved=0, x_min=x_min, x_max=x_max)
     _check(lib().pdv_extract_peaks(C.c_void_p(ctx), C.c_void_p(ps), n_spectra, n_bins, v_lo,
                                    v_hi, v_fs, C.byref(o), flags, C.c_void_p(po)))
@@ -434,14 +434,14 @@ def ss_spectrum(ctx: "Context", params, n_bins: int, v_lo: float, v_hi: float,
 
 def extract_peaks(ctx: "Context", spectra, v_lo: float, v_hi: float, v_fs: float, k_c: int,
                   x_min: float = -math.inf, x_max: float = math.inf,
-                  tensor: bool = False) -> np.ndarray:
+                  simt: bool = False) -> np.ndarray:
     """Host convenience: spectra float64 [n_spectra, n_bins] -> PEAK_DTYPE array."""
     s = np.ascontiguousarray(spectra, dtype=np.float64)
     if s.ndim == 1:
         s = s[None, :]
     out = np.zeros(s.shape[0], dtype=PEAK_DTYPE)
     pdv_extract_peaks(ctx.handle, s, s.shape[0], s.shape[1], v_lo, v_hi, v_fs, k_c, x_min, x_max,
-                      out, tensor)
+                      out, simt)
     return out
 
 

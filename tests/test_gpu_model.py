@@ -162,17 +162,17 @@ def check_jmax(g, o, s, k_c, lo, hi):
         assert abs(int(g["j_max"]) - o["j_max"]) <= 1
 
 
-# the DFT product as FP32 FMAs on the CUDA cores (the default) and on the
-# tensor cores (PDV_EXTRACT_TENSOR: split TF32, cut-offs up to 63 modes)
-PATHS = pytest.mark.parametrize("tensor", [False, True], ids=["simt", "tensor"])
+# both products on the tensor cores (split TF32; the default for cut-offs up
+# to 63 modes) and as FP32 FMAs on the CUDA cores (PDV_EXTRACT_SIMT)
+PATHS = pytest.mark.parametrize("simt", [False, True], ids=["tensor", "simt"])
 
 
 @PATHS
 @pytest.mark.parametrize("k_c,x_min,x_max", [(40, 1.02, 3.5), (60, -math.inf, math.inf),
                                              (25, 1.1, 2.2), (71, 1.02, 3.5), (80, 1.02, 3.5)])
-def test_extract_matches_oracle(ctx, k_c, x_min, x_max, tensor):
+def test_extract_matches_oracle(ctx, k_c, x_min, x_max, simt):
     spec = extraction_cases()
-    g = pdv.extract_peaks(ctx, spec, 0.0, 8000.0, 2000.0, k_c, x_min, x_max, tensor=tensor)
+    g = pdv.extract_peaks(ctx, spec, 0.0, 8000.0, 2000.0, k_c, x_min, x_max, simt=simt)
     xc = (0.0 + (np.arange(600) + 0.5) * (8000.0 / 600)) / 2000.0
     lo = int(np.searchsorted(xc, x_min)) if math.isfinite(x_min) else 0
     hi = int(np.searchsorted(xc, x_max, side="right")) - 1 if math.isfinite(x_max) else 599
@@ -185,12 +185,12 @@ def test_extract_matches_oracle(ctx, k_c, x_min, x_max, tensor):
 
 
 @PATHS
-def test_extract_status_and_edge_cases(ctx, tensor):
+def test_extract_status_and_edge_cases(ctx, simt):
     n = 300
     cases = [np.zeros(n),                                                  # no peak
              1.0 + np.cos(2 * math.pi * (np.arange(n) - 50) / n),          # falls over the window
              -np.ones(n)]                                                  # negative
-    g = pdv.extract_peaks(ctx, np.array(cases), 0.0, 6000.0, 2000.0, 4, 1.2, 2.0, tensor=tensor)
+    g = pdv.extract_peaks(ctx, np.array(cases), 0.0, 6000.0, 2000.0, 4, 1.2, 2.0, simt=simt)
     for i, s in enumerate(cases):
         o = O.extract_peak(s, 0.0, 6000.0, 2000.0, 4, 1.2, 2.0)
         compare_peak(g[i], o)
@@ -199,11 +199,11 @@ def test_extract_status_and_edge_cases(ctx, tensor):
     assert [int(x) for x in g["status"]] == [pdv.PDV_PEAK_NO_PEAK, pdv.PDV_PEAK_EDGE,
                                             pdv.PDV_PEAK_NO_PEAK]
     # empty window
-    g = pdv.extract_peaks(ctx, np.array(cases[1:2]), 0.0, 6000.0, 2000.0, 4, 5.0, 4.0, tensor=tensor)
+    g = pdv.extract_peaks(ctx, np.array(cases[1:2]), 0.0, 6000.0, 2000.0, 4, 5.0, 4.0, simt=simt)
     assert int(g[0]["status"]) == pdv.PDV_PEAK_NO_PEAK and int(g[0]["j_max"]) == -1
     # smallest size: 3 bins, one mode
     s = np.array([0.2, 1.0, 0.3])
-    g = pdv.extract_peaks(ctx, s, 0.0, 3.0, 1.0, 1, tensor=tensor)
+    g = pdv.extract_peaks(ctx, s, 0.0, 3.0, 1.0, 1, simt=simt)
     compare_peak(g[0], O.extract_peak(s, 0.0, 3.0, 1.0, 1))
     # invalid arguments
     for kw in (dict(k_c=0), dict(k_c=150)):
@@ -217,24 +217,24 @@ def test_extract_status_and_edge_cases(ctx, tensor):
 
 
 @PATHS
-def test_extract_ragged_batches_and_device_buffers(ctx, tensor):
+def test_extract_ragged_batches_and_device_buffers(ctx, simt):
     torch = pytest.importorskip("torch")
     base = extraction_cases()
     rng = np.random.default_rng(3)
     big = base[rng.integers(0, len(base), 2000)] * (1.0 + 0.01 * rng.standard_normal((2000, 600)))
-    g = pdv.extract_peaks(ctx, big, 0.0, 8000.0, 2000.0, 40, 1.02, 3.5, tensor=tensor)
+    g = pdv.extract_peaks(ctx, big, 0.0, 8000.0, 2000.0, 40, 1.02, 3.5, simt=simt)
     for i in rng.choice(2000, 40, replace=False):
         compare_peak(g[i], O.extract_peak(big[i], 0.0, 8000.0, 2000.0, 40, 1.02, 3.5))
     # a tile's other spectra do not change a spectrum's result: alone, at a
     # ragged tail, and as the last of a full tile
     for lo, hi in ((0, 1), (1990, 2000), (1873, 2000)):
-        part = pdv.extract_peaks(ctx, big[lo:hi], 0.0, 8000.0, 2000.0, 40, 1.02, 3.5, tensor=tensor)
+        part = pdv.extract_peaks(ctx, big[lo:hi], 0.0, 8000.0, 2000.0, 40, 1.02, 3.5, simt=simt)
         assert part.tobytes() == g[lo:hi].tobytes()
     d_in = torch.tensor(big, device="cuda")
     d_out = torch.zeros(2000 * pdv.PEAK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     pdv.pdv_extract_peaks(ctx.handle, d_in, 2000, 600, 0.0, 8000.0, 2000.0, 40, 1.02, 3.5, d_out,
-                          tensor=tensor)
+                          simt=simt)
     torch.cuda.synchronize()
     assert d_out.cpu().numpy().tobytes() == g.tobytes()
 
@@ -246,8 +246,8 @@ def test_extract_paths_agree(ctx):
     base = extraction_cases()
     rng = np.random.default_rng(4)
     big = base[rng.integers(0, len(base), 2000)] * (1.0 + 0.01 * rng.standard_normal((2000, 600)))
-    a = pdv.extract_peaks(ctx, big, 0.0, 8000.0, 2000.0, 40, 1.02, 3.5, tensor=True)
-    b = pdv.extract_peaks(ctx, big, 0.0, 8000.0, 2000.0, 40, 1.02, 3.5)
+    a = pdv.extract_peaks(ctx, big, 0.0, 8000.0, 2000.0, 40, 1.02, 3.5)
+    b = pdv.extract_peaks(ctx, big, 0.0, 8000.0, 2000.0, 40, 1.02, 3.5, simt=True)
     ok = a["status"] == pdv.PDV_PEAK_OK
     assert np.array_equal(a["status"], b["status"]) and ok.mean() > 0.5
     assert np.max(np.abs(a["x_peak"][ok] - b["x_peak"][ok])) < 4e-6
@@ -271,8 +271,8 @@ def test_extract_maximum_size(ctx):
     assert abs(int(g["j_max"]) - o["j_max"]) <= 1     # the peak sits half-way between bins
     assert g["x_peak"] == pytest.approx(o["x_peak"], abs=1e-4)
     assert g["curvature"] == pytest.approx(o["curvature"], rel=5e-2)
-    for tensor in (False, True):
-        g = pdv.extract_peaks(ctx, s, 0.0, 8192.0, 2000.0, 64, tensor=tensor)
+    for simt in (False, True):
+        g = pdv.extract_peaks(ctx, s, 0.0, 8192.0, 2000.0, 64, simt=simt)
         compare_peak(g[0], O.extract_peak(s, 0.0, 8192.0, 2000.0, 64), scale=10.0)
 
 
@@ -321,9 +321,9 @@ def test_bench_size_sampled():
         d_pk = torch.zeros(n * pdv.PEAK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
         torch.cuda.synchronize()
         sample = rng.choice(n, 40, replace=False)
-        for tensor in (False, True):
+        for simt in (False, True):
             pdv.pdv_extract_peaks(ctx.handle, d_in, n, nb, 0.0, 8000.0, 2000.0, 40, 1.02, 3.5, d_pk,
-                                  tensor=tensor)
+                                  simt=simt)
             torch.cuda.synchronize()
             got = np.frombuffer(d_pk.cpu().numpy().tobytes(), dtype=pdv.PEAK_DTYPE)
             for i in sample:
