@@ -954,7 +954,9 @@ def model_mode(args):
                          if args.extract_simt else
                          {"bound": "hbm", "achieved": pk_bytes / (pk_kms / 1e3) / 1e9, "peak": hbm,
                           "unit": "GB/s", "frac": pk_bytes / (pk_kms / 1e3) / 1e9 / hbm,
-                          "traffic": None, "kernel": "k_extract_tc", "peak_source": "measured",
+                          "traffic": (prof["k_extract_tc"]["dram_bytes_per_launch"] * n / 1e5
+                                      if prof and "k_extract_tc" in prof else None),
+                          "kernel": "k_extract_tc", "peak_source": "measured",
                           "algorithmic_bytes_per_spectrum": pk_bytes / n,
                           "tensor_flop_per_spectrum": 3 * pk_flop / n}),
             "e2e": {"value": n / e2e["pk"], "unit": "spectra/s", "h2d_bytes_per_step": n * nb * 8,
