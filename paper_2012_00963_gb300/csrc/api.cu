@@ -797,10 +797,10 @@ static int pick_hist_mode(const pdv_ctx* c, const SetDesc& d) {
 
 // Launch geometry of the persistent FP32 kernel for given shared memory.
 static pdv_status f32_geometry(pdv_ctx* c, size_t smem, int hist_mode, bool dump, bool impl,
-                               int* grid, int* block, bool one = false) {
+                               bool fast, int* grid, int* block, bool one = false) {
   const int bt = c->tuning.block_threads ? c->tuning.block_threads : 256;
   int occ = 0;
-  CK(transport_f32_occupancy(bt, smem, hist_mode, dump, impl, one, &occ));
+  CK(transport_f32_occupancy(bt, smem, hist_mode, dump, impl, one, fast, &occ));
   if (occ < 1) return fail(PDV_EINVAL, "tables need %zu bytes of shared memory, too many for one block", smem);
   int bps = c->tuning.blocks_per_sm ? std::min(c->tuning.blocks_per_sm, occ) : occ;
   *grid = c->sm_count * bps;
@@ -878,10 +878,11 @@ static pdv_status enqueue_transport(pdv_ctx* c, const pdv_request* r, const SetD
     if (smem > (size_t)c->max_smem) return fail(PDV_EINVAL, "tables need %zu bytes of shared memory (max %d)", smem, c->max_smem);
     int grid = 0, block = 0;
     const bool impl = d.implicit != 0;
-    pdv_status s = f32_geometry(c, smem, hm, dump, impl, &grid, &block, true);
+    const bool fast = transport_fast_set(d);
+    pdv_status s = f32_geometry(c, smem, hm, dump, impl, fast, &grid, &block, true);
     if (s != PDV_OK) return s;
     launch_transport_f32_one(d, (unsigned long long*)(base + b.o_ctr), grid, block, smem, hm, dump,
-                             impl, (unsigned)c->tuning.tile_packets, st);
+                             impl, fast, (unsigned)c->tuning.tile_packets, st);
     c->last_grid = grid;
     c->last_block = block;
   } else {
@@ -1063,12 +1064,13 @@ static pdv_status run_batch_f32(pdv_ctx* c, const pdv_request* rs, int n, bool t
   std::vector<SetDesc> sets(n);
   size_t smem = 0;
   int hm = 2;
-  bool dump = false, impl = false;
+  bool dump = false, impl = false, fast = true;
   for (int i = 0; i < n; ++i) {
     sets[i] = make_set(&rs[i]);
     if (pick_hist_mode(c, sets[i]) == 1) hm = 1;
     dump = dump || rs[i].out_packets != nullptr;
     impl = impl || sets[i].implicit != 0;
+    fast = fast && transport_fast_set(sets[i]);
   }
   for (int i = 0; i < n; ++i) {
     const SetDesc& d = sets[i];
@@ -1076,9 +1078,9 @@ static pdv_status run_batch_f32(pdv_ctx* c, const pdv_request* rs, int n, bool t
   }
   if (smem > (size_t)c->max_smem) return fail(PDV_EINVAL, "batch tables need %zu bytes of shared memory", smem);
   int grid = 0, block = 0;
-  pdv_status s = f32_geometry(c, smem, hm, dump, impl, &grid, &block);
+  pdv_status s = f32_geometry(c, smem, hm, dump, impl, fast, &grid, &block);
   if (s != PDV_OK) return s;
-  const std::string key = batch_key(c, rs, n, grid, block, smem, hm, dump);
+  const std::string key = batch_key(c, rs, n, grid, block, smem, hm, dump) + (fast ? "f" : "g");
   pdv_ctx::GraphEntry* ge = nullptr;
   for (auto& g : c->graphs)
     if (g.key == key) ge = &g;
@@ -1112,7 +1114,7 @@ static pdv_status run_batch_f32(pdv_ctx* c, const pdv_request* rs, int n, bool t
       cudaEventRecordWithFlags(c->ev0, cap, cudaEventRecordExternal);
       launch_transport_f32((const SetDesc*)(base + B.o_sets), n,
                            (unsigned long long*)(base + B.o_ctr), grid, block, smem, hm, dump, impl,
-                           (unsigned)c->tuning.tile_packets, cap);
+                           fast, (unsigned)c->tuning.tile_packets, cap);
       cudaEventRecordWithFlags(c->ev1, cap, cudaEventRecordExternal);
       int max_snap = 1;
       for (int i = 0; i < n; ++i) max_snap = std::max(max_snap, rs[i].n_snap);
@@ -1595,14 +1597,15 @@ static void serving_loop(pdv_ctx* c) {
     const int n = (int)items.size();
     size_t smem = 0;
     int hm = 1;
-    bool impl = false;
+    bool impl = false, fast = true;
     for (int k = 0; k < n; ++k) {
       const SetDesc& d = s.h_sets[k];
       smem = std::max(smem, set_smem(d, 1));
       impl = impl || d.implicit != 0;
+      fast = fast && transport_fast_set(d);
     }
     int grid = 0, block = 0;
-    if (f32_geometry(c, smem, hm, false, impl, &grid, &block) != PDV_OK) {
+    if (f32_geometry(c, smem, hm, false, impl, fast, &grid, &block) != PDV_OK) {
       std::lock_guard<std::mutex> lk(c->smu);
       for (auto& it : items) {
         it.first->state = 3;
@@ -1615,7 +1618,7 @@ static void serving_loop(pdv_ctx* c) {
     cudaMemcpyAsync(s.d_mem, s.h_sets, sizeof(SetDesc) * n, cudaMemcpyHostToDevice, c->serve_stream);
     unsigned long long* ctr = (unsigned long long*)(s.d_mem + sizeof(SetDesc) * kMaxLaunchSets);
     cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * n, c->serve_stream);
-    launch_transport_f32((const SetDesc*)s.d_mem, n, ctr, grid, block, smem, hm, false, impl,
+    launch_transport_f32((const SetDesc*)s.d_mem, n, ctr, grid, block, smem, hm, false, impl, fast,
                          (unsigned)c->tuning.tile_packets, c->serve_stream);
     c->launches += 1;
     cudaEventRecord(s.ev, c->serve_stream);
@@ -1886,10 +1889,11 @@ extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request
   if (smem > (size_t)c->max_smem) return fail(PDV_EINVAL, "tables need %zu bytes of shared memory", smem);
   int grid = 0, block = 0;
   const bool impl = d.implicit != 0;
-  s = f32_geometry(c, smem, hm, dump, impl, &grid, &block, true);
+  const bool fast = transport_fast_set(d);
+  s = f32_geometry(c, smem, hm, dump, impl, fast, &grid, &block, true);
   if (s != PDV_OK) return s;
   launch_transport_f32_one(d, (unsigned long long*)(base + o_ctr), grid, block, smem, hm, dump, impl,
-                           (unsigned)c->tuning.tile_packets, st);
+                           fast, (unsigned)c->tuning.tile_packets, st);
   launch_normalise((const SetDesc*)(base + o_set), 1, (double* const*)(base + o_ptr),
                    (pdv_counters* const*)(base + o_ptr + sizeof(void*)),
                    (unsigned long long* const*)(base + o_ptr + 2 * sizeof(void*)),

@@ -257,15 +257,18 @@ __device__ __forceinline__ float u64_to_f(unsigned long long d) {
 // Kernel entry points (defined in the .cu files).
 // impl: some set of the launch has PDV_IMPLICIT_CAPTURE (a kernel build that
 // holds the implicit-capture branch; the analog build leaves it out).
+// fast: every set of the launch passes transport_fast_set (the build that
+// takes those sets' branches at compile time; dumps use the generic build).
 // chunk: packets a warp claims at a time (0: the default, 64)
+bool transport_fast_set(const SetDesc& d);
 void launch_transport_f32(const SetDesc* d_sets, int n_sets, unsigned long long* d_set_ctr,
                           int grid, int block, size_t smem, int hist_mode, bool dump, bool impl,
-                          unsigned chunk, cudaStream_t st);
+                          bool fast, unsigned chunk, cudaStream_t st);
 // One set whose descriptor (host copy, device pointers inside) is passed by
 // value as a kernel parameter.
 void launch_transport_f32_one(const SetDesc& sd, unsigned long long* d_ctr, int grid, int block,
-                              size_t smem, int hist_mode, bool dump, bool impl, unsigned chunk,
-                              cudaStream_t st);
+                              size_t smem, int hist_mode, bool dump, bool impl, bool fast,
+                              unsigned chunk, cudaStream_t st);
 void launch_transport_f64(const SetDesc* d_set, int grid, int block, cudaStream_t st);
 void launch_normalise(const SetDesc* d_sets, int n_sets, double* const* d_spec,
                       pdv_counters* const* d_cnt_out, unsigned long long* const* d_raw,
@@ -277,7 +280,7 @@ int transport_f32_max_smem();
 // device now (the runtime otherwise loads a kernel at its first launch).
 cudaError_t transport_preload();
 cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, bool impl,
-                                    bool one, int* blocks);
+                                    bool one, bool fast, int* blocks);
 // The debug words of the transport and the layer-stepping translation units
 // (all zero in the release build).
 cudaError_t transport_debug_io(DebugWord* out, bool reset, cudaStream_t st);

@@ -234,8 +234,11 @@ __device__ __forceinline__ SmemTables stage_set(const SetDesc& sd, unsigned char
 }
 
 // The walks of one set by this block's warps (Section II.B steps (1)-(7)),
-// with the per-set sums added to the block's counters s_cnt.
-template <bool DUMP, int HMODE, bool IMPL>
+// with the per-set sums added to the block's counters s_cnt. FAST: every set
+// of the launch has the configuration transport_fast_set names, so the walk
+// takes its branches at compile time instead of testing the set's switches
+// every flight.
+template <bool DUMP, int HMODE, bool IMPL, bool FAST>
 __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb,
                                          unsigned long long* __restrict__ ctr, unsigned chunk,
                                          unsigned long long* s_cnt) {
@@ -299,7 +302,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
         // Step (1): a new packet at the top of the cloud moving along -z
         pk = base_pk + (pool_next + rank);
         ux = 0.f; uy = 0.f; uz = -1.f; iuz = -1.f;
-        if (sd.launch_horizontal) {      // test hook: the horizontal-flight rule
+        if (!FAST && sd.launch_horizontal) {      // test hook: the horizontal-flight rule
           ux = 1.f; uz = 0.f; iuz = 0.f;
         }
         Sq = (long long)kOneQ;
@@ -344,7 +347,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
                                                                       : ((dS <= -1.0f || Sn <= 0) ? 2 : 0));
     // velocity coordinate z/t where the flight ends
     float vn = vcur;
-    if (sd.expo) {
+    if (FAST || sd.expo) {
       // Eq. 20 inverted in closed form: v = v_fs (1 - ln((1 - S) + S eps) / beta); 1 - S is
       // exact in the fixed-point state, so the top of the cloud keeps its relative precision
       // (32-bit conversions: the 64-bit ones run on the FP64 pipe)
@@ -369,7 +372,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     } else {
       // horizontal packet: lateral path tau / mu(z), in velocity units tau / tau_tot dv/dS
       float dvds;
-      if (sd.expo) {
+      if (FAST || sd.expo) {
         const unsigned long long sq = (unsigned long long)Sq, oms = kOneQ - sq;
         const float om = fmaf(__uint2float_rn((unsigned)(oms >> 32)), kTwoM30f,
                               __uint2float_rn((unsigned)oms) * kTwoM62f);
@@ -461,7 +464,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     // round(W R_q / 2^32). W <= 2^32, and R_q < 2^32 unless R = 1, so the
     // product is one 32 x 32 -> 64-bit multiply-add; W = 2^32 gives R_q.
     const unsigned long long Wr =
-        sd.R_q >= (1ull << 32)
+        (!FAST && sd.R_q >= (1ull << 32))
             ? W
             : ((W >> 32) ? sd.R_q
                          : (((unsigned long long)(unsigned)W * (unsigned)sd.R_q + (1ull << 31)) >> 32));
@@ -522,7 +525,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
       }
       const uint2 nd = PDV_LD(tb.node, lo, n_p, PDV_DEBUG_SITE_PHASE_NODE);
       const float fm = (float)(m2 - nd.x) + 0.5f;
-      if (sd.angle_table) {
+      if (FAST || sd.angle_table) {
         // theta = theta_i + d with d = (m - Cq_i + 1/2) times the bin's slope
         const float dp = fm * __uint_as_float(nd.y);
         // theta' = 2 pi f with f = u / 4 = ((r1 >> 9) + 1/2) 2^-25: the nearest
@@ -553,7 +556,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
       const float dphi = (float)(2 * (mp - (jp << 13)) + 1) * kPi2m23f;
       cos_sin_add(tb.turn[jp & (kTurn - 1)], dphi, &cp, &sp);
     }
-    if (sd.surface_mode == PDV_SURFACE_LAMBERT) {
+    if (!FAST && sd.surface_mode == PDV_SURFACE_LAMBERT) {
       const float a = u23f(r.y);
       ct = surf ? sqrtf(a) : ct;
       st = surf ? sqrtf(1.0f - a) : st;
@@ -572,7 +575,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     nx = vert ? st * cp : nx;
     ny = vert ? st * sp : ny;
     nz = vert ? ((surf || uz >= 0.0f) ? ct : -ct) : nz;
-    const bool spec = surf && sd.surface_mode == PDV_SURFACE_SPECULAR;
+    const bool spec = !FAST && surf && sd.surface_mode == PDV_SURFACE_SPECULAR;
     const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
     nx = spec ? ux : nx * inv_n;
     ny = spec ? uy : ny * inv_n;
@@ -671,7 +674,7 @@ __device__ __forceinline__ void flush_set(const SetDesc& sd, const SmemTables& t
 
 // Persistent launch over a list of sets (batches and serving): blocks walk the
 // list from their own offset and stay on a set until its packets are claimed.
-template <bool DUMP, int HMODE, bool IMPL>
+template <bool DUMP, int HMODE, bool IMPL, bool FAST>
 __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restrict__ sets,
                                                           int n_sets,
                                                           unsigned long long* __restrict__ set_ctr,
@@ -701,7 +704,7 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
     __syncthreads();
     const SmemTables tb = stage_set<HMODE>(sd, smem);
     __syncthreads();
-    walk_set<DUMP, HMODE, IMPL>(sd, tb, &set_ctr[si], chunk, s_cnt);
+    walk_set<DUMP, HMODE, IMPL, FAST>(sd, tb, &set_ctr[si], chunk, s_cnt);
     __syncthreads();
     flush_set<HMODE>(sd, tb, s_cnt);
     __syncthreads();
@@ -711,7 +714,7 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32(const SetDesc* __restr
 // Persistent launch of one set whose descriptor is a kernel parameter: the
 // walk reads its constants (and Philox's round keys) as constant-bank
 // operands instead of shared-memory loads and registers.
-template <bool DUMP, int HMODE, bool IMPL>
+template <bool DUMP, int HMODE, bool IMPL, bool FAST>
 __global__ void __launch_bounds__(256, 4) k_transport_f32_one(const __grid_constant__ SetDesc sd,
                                                               unsigned long long* __restrict__ ctr,
                                                               unsigned chunk) {
@@ -720,27 +723,43 @@ __global__ void __launch_bounds__(256, 4) k_transport_f32_one(const __grid_const
   if (threadIdx.x < C_NCOUNT) s_cnt[threadIdx.x] = 0ull;
   const SmemTables tb = stage_set<HMODE>(sd, smem);
   __syncthreads();
-  walk_set<DUMP, HMODE, IMPL>(sd, tb, ctr, chunk, s_cnt);
+  walk_set<DUMP, HMODE, IMPL, FAST>(sd, tb, ctr, chunk, s_cnt);
   __syncthreads();
   flush_set<HMODE>(sd, tb, s_cnt);
 }
 
-template <bool IMPL>
-static const void* f32_kernel_impl(int hist_mode, bool dump, bool one) {
-  if (one) {
-    if (dump)
-      return hist_mode == 2 ? (const void*)k_transport_f32_one<true, 2, IMPL>
-                            : (const void*)k_transport_f32_one<true, 1, IMPL>;
-    return hist_mode == 2 ? (const void*)k_transport_f32_one<false, 2, IMPL>
-                          : (const void*)k_transport_f32_one<false, 1, IMPL>;
-  }
-  if (dump)
-    return hist_mode == 2 ? (const void*)k_transport_f32<true, 2, IMPL> : (const void*)k_transport_f32<true, 1, IMPL>;
-  return hist_mode == 2 ? (const void*)k_transport_f32<false, 2, IMPL> : (const void*)k_transport_f32<false, 1, IMPL>;
+// The configuration the FAST builds take at compile time: the exponential law
+// (closed-form velocity), sin/cos from the node table, the diffuse wall with
+// the polar angle uniform in [0, pi/2) and R < 1, no horizontal launch.
+bool transport_fast_set(const SetDesc& d) {
+  return d.expo && d.angle_table && !d.launch_horizontal &&
+         d.surface_mode == PDV_SURFACE_UNIFORM_THETA && d.R_q < (1ull << 32);
 }
 
-static const void* f32_kernel(int hist_mode, bool dump, bool impl, bool one = false) {
-  return impl ? f32_kernel_impl<true>(hist_mode, dump, one) : f32_kernel_impl<false>(hist_mode, dump, one);
+template <bool IMPL, bool FAST>
+static const void* f32_kernel_hm(int hist_mode, bool one) {
+  if (one)
+    return hist_mode == 2 ? (const void*)k_transport_f32_one<false, 2, IMPL, FAST>
+                          : (const void*)k_transport_f32_one<false, 1, IMPL, FAST>;
+  return hist_mode == 2 ? (const void*)k_transport_f32<false, 2, IMPL, FAST>
+                        : (const void*)k_transport_f32<false, 1, IMPL, FAST>;
+}
+
+template <bool IMPL>
+static const void* f32_kernel_impl(int hist_mode, bool dump, bool one, bool fast) {
+  if (dump) {                      // packet dumps: the generic build
+    if (one)
+      return hist_mode == 2 ? (const void*)k_transport_f32_one<true, 2, IMPL, false>
+                            : (const void*)k_transport_f32_one<true, 1, IMPL, false>;
+    return hist_mode == 2 ? (const void*)k_transport_f32<true, 2, IMPL, false>
+                          : (const void*)k_transport_f32<true, 1, IMPL, false>;
+  }
+  return fast ? f32_kernel_hm<IMPL, true>(hist_mode, one) : f32_kernel_hm<IMPL, false>(hist_mode, one);
+}
+
+static const void* f32_kernel(int hist_mode, bool dump, bool impl, bool one, bool fast) {
+  return impl ? f32_kernel_impl<true>(hist_mode, dump, one, fast)
+              : f32_kernel_impl<false>(hist_mode, dump, one, fast);
 }
 
 __global__ void k_normalise(const SetDesc* __restrict__ sets, double* const* spec,
@@ -752,11 +771,12 @@ cudaError_t transport_preload() {
   for (int one = 0; one < 2; ++one)
     for (int impl = 0; impl < 2; ++impl)
       for (int dump = 0; dump < 2; ++dump)
-        for (int hm = 1; hm <= 2; ++hm) {
-          const cudaError_t e =
-              cudaFuncGetAttributes(&a, f32_kernel(hm, dump != 0, impl != 0, one != 0));
-          if (e != cudaSuccess) return e;
-        }
+        for (int hm = 1; hm <= 2; ++hm)
+          for (int fast = 0; fast < 2; ++fast) {
+            const cudaError_t e = cudaFuncGetAttributes(
+                &a, f32_kernel(hm, dump != 0, impl != 0, one != 0, fast != 0));
+            if (e != cudaSuccess) return e;
+          }
   return cudaFuncGetAttributes(&a, (const void*)k_normalise);
 }
 
@@ -768,8 +788,8 @@ int transport_f32_max_smem() {
 }
 
 cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool dump, bool impl,
-                                    bool one, int* blocks) {
-  const void* k = f32_kernel(hist_mode, dump, impl, one);
+                                    bool one, bool fast, int* blocks) {
+  const void* k = f32_kernel(hist_mode, dump, impl, one, fast);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, block, smem);
@@ -777,8 +797,8 @@ cudaError_t transport_f32_occupancy(int block, size_t smem, int hist_mode, bool 
 
 void launch_transport_f32(const SetDesc* d_sets, int n_sets, unsigned long long* d_set_ctr,
                           int grid, int block, size_t smem, int hist_mode, bool dump, bool impl,
-                          unsigned chunk, cudaStream_t st) {
-  const void* k = f32_kernel(hist_mode, dump, impl);
+                          bool fast, unsigned chunk, cudaStream_t st) {
+  const void* k = f32_kernel(hist_mode, dump, impl, false, fast);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (chunk == 0) chunk = kChunkDefault;
   void* args[] = {(void*)&d_sets, (void*)&n_sets, (void*)&d_set_ctr, (void*)&chunk};
@@ -786,9 +806,9 @@ void launch_transport_f32(const SetDesc* d_sets, int n_sets, unsigned long long*
 }
 
 void launch_transport_f32_one(const SetDesc& sd, unsigned long long* d_ctr, int grid, int block,
-                              size_t smem, int hist_mode, bool dump, bool impl, unsigned chunk,
-                              cudaStream_t st) {
-  const void* k = f32_kernel(hist_mode, dump, impl, true);
+                              size_t smem, int hist_mode, bool dump, bool impl, bool fast,
+                              unsigned chunk, cudaStream_t st) {
+  const void* k = f32_kernel(hist_mode, dump, impl, true, fast);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (chunk == 0) chunk = kChunkDefault;
   SetDesc arg = sd;
