@@ -85,7 +85,7 @@ constexpr int kMaxTableNodes = 16384;
 constexpr int kMaxPhase = 65536;
 constexpr int kMaxSnap = 4096;
 constexpr int kMaxBins = 65536;
-constexpr int kGuidePhaseLog = 12;                   // 4096 guide cells over the 2^24 CDF
+constexpr int kGuidePhaseLog = 13;                   // 8192 guide cells over the 2^24 CDF
 
 // Snapshot-independent counter slots of one request (device array of u64).
 enum Counter {
