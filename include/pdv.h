@@ -216,6 +216,13 @@ typedef struct {
   double last_model_ms;            /* CUDA-event time of the last pdv_ss_spectrum /
                                       pdv_extract_peaks main kernel      */
   uint64_t last_steps;             /* layer steps of the last layer-stepping call */
+  int32_t transport_fast;          /* 1: the last FP32 transport launch ran the build for
+                                      the common set configuration (exponential law, phase
+                                      angles from the node table, vertical launch, uniform-
+                                      angle wall with R < 1, no packet records) on every
+                                      set; 0: the generic build, or not an FP32 launch
+                                      (the serving thread's launches do not set it) */
+  int32_t reserved;
 } pdv_stats;
 
 /* ---------------------------------------------------------------- context */

@@ -85,6 +85,7 @@ struct pdv_ctx {
   unsigned long long last_steps = 0;
   unsigned long long last_events = 0;
   int last_grid = 0, last_block = 0;
+  int last_fast = 0;      // 1: the last FP32 transport launch ran the common-configuration build
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // batched-graph cache
   struct GraphEntry {
@@ -309,6 +310,8 @@ extern "C" pdv_status pdv_get_stats(pdv_ctx* c, pdv_stats* out) {
   out->transport_block = c->last_block;
   out->last_model_ms = c->last_model_ms;
   out->last_steps = c->last_steps;
+  out->transport_fast = c->last_fast;
+  out->reserved = 0;
   return PDV_OK;
 }
 
@@ -867,6 +870,7 @@ static pdv_status enqueue_transport(pdv_ctx* c, const pdv_request* r, const SetD
     if (timed) cudaEventRecord(c->ev1, st);
     c->last_grid = std::max(grid, 1);
     c->last_block = 256;
+    c->last_fast = 0;
     c->launches += 1;
     return PDV_OK;
   }
@@ -885,12 +889,14 @@ static pdv_status enqueue_transport(pdv_ctx* c, const pdv_request* r, const SetD
                              impl, fast, (unsigned)c->tuning.tile_packets, st);
     c->last_grid = grid;
     c->last_block = block;
+    c->last_fast = fast && !dump;
   } else {
     const unsigned long long want = (r->n_packets + 255) / 256;
     const int grid = (int)std::min<unsigned long long>(want, (unsigned long long)c->sm_count * 8);
     launch_transport_f64((const SetDesc*)(base + b.o_set), std::max(grid, 1), 256, st);
     c->last_grid = std::max(grid, 1);
     c->last_block = 256;
+    c->last_fast = 0;
   }
   c->launches += 1;
   CK(cudaGetLastError());
@@ -1166,6 +1172,7 @@ static pdv_status run_batch_f32(pdv_ctx* c, const pdv_request* rs, int n, bool t
   c->launches += 2;
   c->last_grid = grid;
   c->last_block = block;
+  c->last_fast = fast && !dump;
   for (int i = 0; i < n; ++i) {
     const pdv_request& r = rs[i];
     if (r.flags & PDV_OUT_DEVICE) continue;
@@ -1894,6 +1901,7 @@ extern "C" pdv_status pdv_simulate_spectrum_static(pdv_ctx* c, const pdv_request
   if (s != PDV_OK) return s;
   launch_transport_f32_one(d, (unsigned long long*)(base + o_ctr), grid, block, smem, hm, dump, impl,
                            fast, (unsigned)c->tuning.tile_packets, st);
+  c->last_fast = fast && !dump;
   launch_normalise((const SetDesc*)(base + o_set), 1, (double* const*)(base + o_ptr),
                    (pdv_counters* const*)(base + o_ptr + sizeof(void*)),
                    (unsigned long long* const*)(base + o_ptr + 2 * sizeof(void*)),

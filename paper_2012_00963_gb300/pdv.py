@@ -117,7 +117,7 @@ class pdv_stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("last_transport_ms", C.c_double),
                 ("last_events", C.c_uint64), ("transport_grid", C.c_int),
                 ("transport_block", C.c_int), ("last_model_ms", C.c_double),
-                ("last_steps", C.c_uint64)]
+                ("last_steps", C.c_uint64), ("transport_fast", C.c_int32), ("reserved", C.c_int32)]
 
 
 class pdv_ss_set(C.Structure):

@@ -177,13 +177,54 @@ def test_runs_are_bit_identical(ctx):
     assert np.array_equal(r1["counters"], r2["counters"])
 
 
-def test_dump_variant_does_not_change_tallies(ctx):
-    wl = W.cfg1(n_packets=100000, **WIDE)
+# Request variants for the build check below: whether the FP32 transport
+# without packet records runs the build compiled for the common configuration
+# (exponential law, node angle table, vertical launch, uniform-angle wall with
+# R < 1), and the workload change.
+BUILDS = {
+    "cfg1": (True, lambda: W.cfg1(n_packets=100000, **WIDE)),
+    "cfg2_mie_5t": (True, lambda: W.cfg2(n_packets=100000, t_snap=(0.5e-6, 1e-6, 2e-6, 3.5e-6, 5e-6),
+                                         **WIDE)),
+    "detect_all_3t": (True, lambda: W.cfg1(n_packets=100000, r_ap=0.0, cone_alpha=2.0,
+                                           t_snap=(0.5e-6, 1e-6, 3e-6))),
+    "implicit": (True, lambda: W.cfg1(n_packets=100000, implicit_capture=True, **WIDE)),
+    "albedo0": (True, lambda: W.cfg1(n_packets=100000, phase=W.Phase(albedo=0.0), **WIDE)),
+    "R1": (False, lambda: W.cfg1(n_packets=100000, reflectivity=1.0, **WIDE)),
+    "coarse_table": (False, lambda: W.cfg1(n_packets=100000, phase=W.Phase(
+        kind="table", theta=np.linspace(0.0, np.pi, 181),
+        p=0.51 / (1.49 - 1.4 * np.cos(np.linspace(0.0, np.pi, 181))) ** 1.5, albedo=0.8, q_ext=2.0),
+        **WIDE)),
+    "specular": (False, lambda: W.cfg1(n_packets=100000, surface_mode=2, reflectivity=0.3, **WIDE)),
+    "lambert": (False, lambda: W.cfg1(n_packets=100000, surface_mode=1, reflectivity=0.6, **WIDE)),
+    "horizontal": (False, lambda: W.cfg1(n_packets=100000, horizontal_launch=True, r_ap=0.0,
+                                         cone_alpha=2.0)),
+    "tabulated": (False, lambda: W.cfg1(n_packets=100000, profile_kind="tabulated",
+                                        prof_v=[2100.0, 2600.0, 3000.0, 4200.0],
+                                        prof_f=[3.0, 1.0, 2.0, 0.2], v_max=0.0,
+                                        m0=1 * W.MG_CM2, **WIDE)),
+}
+
+
+@pytest.mark.parametrize("name", list(BUILDS))
+def test_common_configuration_build_matches_generic_build(ctx, name):
+    """A request with packet records runs the generic build of the FP32
+    transport (every switch of the set tested at run time); the same request
+    without them runs the build compiled for the common configuration where
+    the set has it. Both walk the same packets with the same arithmetic, so
+    tallies and counters agree bit for bit, and the library reports which
+    build ran."""
+    fast, make = BUILDS[name]
+    wl = make()
     cloud = pdv.Cloud(ctx, wl)
     plain = pdv.simulate_spectrum(ctx, cloud, wl)
+    st_plain = ctx.stats()
     dump = pdv.simulate_spectrum(ctx, cloud, wl, packets=True)
+    st_dump = ctx.stats()
     cloud.close()
+    assert st_plain["transport_fast"] == int(fast) and st_dump["transport_fast"] == 0
     assert np.array_equal(plain["raw"], dump["raw"])
+    assert np.array_equal(plain["counters"], dump["counters"])
+    assert np.array_equal(plain["spectrum"], dump["spectrum"])
 
 
 def test_device_outputs_match_host_outputs(ctx):
