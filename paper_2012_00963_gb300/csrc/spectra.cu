@@ -467,22 +467,27 @@ __device__ __forceinline__ void tile_fma(const float* A, const float* B, int len
   }
 }
 
-// smooth_eval with the coefficients of spectrum s read from the tile's
-// mode-major shared array (row stride AS) and the twiddles from global memory.
+// smooth_eval for spectrum s of a tile, by a quad of lanes (the four lanes
+// 4 (lane / 4) .. + 3 of a warp, mask qmask): lane l4 = lane % 4 of the quad
+// takes the modes k = l4, l4 + 4, ...; the coefficients come from the tile's
+// mode-major shared array (row stride AS), the twiddles from global memory.
+// The butterfly leaves the same bits in all four lanes (each lane adds the
+// same two partial sums, in either order), so a quad takes its Newton
+// branches together.
 template <int AS = kAS>
-__device__ __forceinline__ void tile_smooth_eval(const float2* tw, const float* Cs, int s, int n,
-                                                 int k_c, int J, float d, int lane, float* s0,
-                                                 float* s1, float* s2) {
+__device__ __forceinline__ void quad_smooth_eval(const float2* tw, const float* Cs, int s, int n,
+                                                 int k_c, int J, float d, int l4, unsigned qmask,
+                                                 float* s0, float* s1, float* s2) {
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   const float two_over_n = 2.0f / (float)n;
-  int m = (lane * J) % n;                           // (k J) mod n, k = lane + 32 i (< 2^18: 32 bits)
-  const int step = (32 * J) % n;
-  for (int k = lane; k <= k_c; k += 32, m = (m + step >= n) ? m + step - n : m + step) {
+  int m = (l4 * J) % n;                             // (k J) mod n, k = l4 + 4 i
+  const int step = (4 * J) % n;
+  for (int k = l4; k <= k_c; k += 4, m = (m + step >= n) ? m + step - n : m + step) {
     float sp, cp;
     sincospif(two_over_n * (float)k * d, &sp, &cp);
     const float2 t = __ldg(&tw[m]);
-    const float c = t.x * cp - t.y * sp;
-    const float sn = t.y * cp + t.x * sp;
+    const float c = t.x * cp - t.y * sp;             // cos(2 pi k (J + d) / n)
+    const float sn = t.y * cp + t.x * sp;            // sin(2 pi k (J + d) / n)
     const float qa = Cs[(2 * k) * AS + s], qb = Cs[(2 * k + 1) * AS + s];
     const float g = k == 0 ? 1.0f : 2.0f;
     const float w = 3.14159265358979f * two_over_n * (float)k;
@@ -491,10 +496,10 @@ __device__ __forceinline__ void tile_smooth_eval(const float2* tw, const float* 
     a1 = fmaf(g * w, qb * c - qa * sn, a1);
     a2 = fmaf(-g * w * w, e, a2);
   }
-  for (int o = 16; o; o >>= 1) {
-    a0 += __shfl_xor_sync(kFull, a0, o);
-    a1 += __shfl_xor_sync(kFull, a1, o);
-    a2 += __shfl_xor_sync(kFull, a2, o);
+  for (int o = 1; o <= 2; o <<= 1) {
+    a0 += __shfl_xor_sync(qmask, a0, o);
+    a1 += __shfl_xor_sync(qmask, a1, o);
+    a2 += __shfl_xor_sync(qmask, a2, o);
   }
   *s0 = a0;
   *s1 = a1;
@@ -524,15 +529,18 @@ __device__ __forceinline__ void load_chunk_async(float* dst, const float* src, s
 // The per-spectrum end of stage 2 for n_sp spectra (the first at global index
 // s0): status, Newton refinement from the coefficients (Cs mode-major, row
 // stride AS) and Eq. 35, from each spectrum's first window maximum (red_v,
-// red_j: value and absolute bin). One warp per spectrum; warps warp,
-// warp + n_warps, ... of the calling group.
+// red_j: value and absolute bin). One quad of lanes per spectrum, so a warp
+// runs eight spectra's Newton steps side by side; thread tid of the calling
+// group of n_threads (a multiple of 32) is lane tid % 4 of quad tid / 4.
 template <int AS>
 __device__ __forceinline__ void tile_finish(const float* Cs, const float* red_v, const int* red_j,
                                             int n_sp, int s0, int n_spec, int n, int k_c, int j_lo,
                                             int j_hi, PeakGeom geom, const float2* tw,
-                                            pdv_peak* out, int warp, int n_warps, int lane) {
+                                            pdv_peak* out, int tid, int n_threads) {
   const int n_w = j_hi - j_lo + 1;
-  for (int s = warp; s < n_sp; s += n_warps) {
+  const int lane = tid & 31, l4 = lane & 3;
+  const unsigned qmask = 0xFu << (lane & ~3);
+  for (int s = tid >> 2; s < n_sp; s += n_threads >> 2) {
     const int gs = s0 + s;
     if (gs >= n_spec) break;
     const float bv = red_v[s];
@@ -546,18 +554,18 @@ __device__ __forceinline__ void tile_finish(const float* Cs, const float* red_v,
         r.status = PDV_PEAK_EDGE;
       } else {
         float d = 0.f, q0, q1, q2;
-        tile_smooth_eval<AS>(tw, Cs, s, n, k_c, J, d, lane, &q0, &q1, &q2);
+        quad_smooth_eval<AS>(tw, Cs, s, n, k_c, J, d, l4, qmask, &q0, &q1, &q2);
         for (int it = 0; it < kPeakNewton && q2 < 0.0f; ++it) {
           const float nd = fminf(fmaxf(d - q1 / q2, -1.0f), 1.0f);
           const bool done = fabsf(nd - d) <= 1e-6f;
           d = nd;
           if (done) break;
-          tile_smooth_eval<AS>(tw, Cs, s, n, k_c, J, d, lane, &q0, &q1, &q2);
+          quad_smooth_eval<AS>(tw, Cs, s, n, k_c, J, d, l4, qmask, &q0, &q1, &q2);
         }
         peak_finish(r, J, d, q0, q2, 1.0f / (float)n, geom);
       }
     }
-    if (lane == 0) out[gs] = r;
+    if (l4 == 0) out[gs] = r;
   }
 }
 
@@ -573,7 +581,6 @@ __device__ __forceinline__ void tile_peaks(const float* Cs, int s0, int n_spec, 
                                            const float* G, int k2p, int nw_p, float* Bs,
                                            float* red_v, int* red_j, pdv_peak* out, int tid) {
   const int ty = tid >> 4, tx = tid & 15;
-  const int warp = tid >> 5, lane = tid & 31;
   const int n_w = j_hi - j_lo + 1;
   // ---- smoothed window values (tile x G), running first maximum per spectrum
   float best[4];
@@ -641,8 +648,7 @@ __device__ __forceinline__ void tile_peaks(const float* Cs, int s0, int n_spec, 
     }
   }
   __syncthreads();
-  tile_finish<AS>(Cs, red_v, red_j, kTS, s0, n_spec, n, k_c, j_lo, j_hi, geom, tw, out, warp,
-                  256 / 32, lane);
+  tile_finish<AS>(Cs, red_v, red_j, kTS, s0, n_spec, n, k_c, j_lo, j_hi, geom, tw, out, tid, 256);
   __syncthreads();
 }
 
@@ -1139,8 +1145,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_extract_tc(
       red_j[tid] = jx;
     }
     __syncthreads();
-    tile_finish<kTcAS>(Cs, red_v, red_j, kTcM, s0, n_spec, n, k_c, j_lo, j_hi, geom, tw, out, warp,
-                       kTcThreads / 32, lane);
+    tile_finish<kTcAS>(Cs, red_v, red_j, kTcM, s0, n_spec, n, k_c, j_lo, j_hi, geom, tw, out, tid,
+                       kTcThreads);
     __syncthreads();                                 // Cs and the tiles free for the next tile
   }
   if (fail) {
