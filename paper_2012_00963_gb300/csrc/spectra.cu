@@ -951,7 +951,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_extract_tc(
   int fail = 0;
   const int n_chunks = n_k / kTcKC, n_groups = (n_chunks + kTcG - 1) / kTcG;
   const int n_tiles = (n_spec + kTcM - 1) / kTcM;
-  const int r = tid >> 2, qb = tid & 3;             // A fill: row r, bins 8 qb .. 8 qb + 7
+  const int r = tid >> 2, qb = tid & 3;             // A fill: row r, 16-byte units qb and qb + 4
   auto wait = [&](int i) {
     const bool ok = mbar_wait(&bar[i], ph[i]);
     ph[i] ^= 1u;
@@ -961,11 +961,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_extract_tc(
     const int s0 = tile * kTcM, gs = s0 + r;
     const double* row = spec + (size_t)(gs < n_spec ? gs : 0) * n;
     for (int e = tid; e < k2s * kTcM; e += kTcThreads) Cs[(e / kTcM) * kTcAS + e % kTcM] = 0.0f;
+    // a thread's 8 bins of a chunk are bins 4 qb .. 4 qb + 3 and 16 + 4 qb .. 16 + 4 qb + 3
+    // of its row, so the four threads of a row read 128 contiguous bytes per load. With
+    // every row on a 16-byte boundary (n even, aligned base) the loads are 16 bytes wide:
+    // a warp's load then asks for whole 32-byte sectors, each once
     double ra[8];
+    const bool v2 = ((n & 1) == 0) && ((reinterpret_cast<uintptr_t>(spec) & 15) == 0);
     auto fetch = [&](int c) {
-      const int j0 = c * kTcKC + 8 * qb;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) ra[i] = (gs < n_spec && j0 + i < n) ? __ldcs(row + j0 + i) : 0.0;
+      for (int u = 0; u < 2; ++u) {
+        const int j0 = c * kTcKC + 16 * u + 4 * qb;
+        if (v2) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int j = j0 + 2 * h;
+            double2 x = make_double2(0.0, 0.0);
+            if (gs < n_spec && j < n) x = __ldcs(reinterpret_cast<const double2*>(row + j));
+            ra[4 * u + 2 * h] = x.x;
+            ra[4 * u + 2 * h + 1] = x.y;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            ra[4 * u + i] = (gs < n_spec && j0 + i < n) ? __ldcs(row + j0 + i) : 0.0;
+        }
+      }
     };
     fetch(0);
     for (int c = 0; c < n_chunks; ++c) {
@@ -1006,7 +1026,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_extract_tc(
           hi[t] = to_tf32(x);
           lo[t] = to_tf32(x - __uint_as_float(hi[t]));
         }
-        const uint32_t off = sw128(r, 2 * qb + u);
+        const uint32_t off = sw128(r, qb + 4 * u);
         *reinterpret_cast<uint4*>(Ah + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
         *reinterpret_cast<uint4*>(Al + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
       }

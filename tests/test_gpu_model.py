@@ -239,6 +239,34 @@ def test_extract_ragged_batches_and_device_buffers(ctx, simt):
     assert d_out.cpu().numpy().tobytes() == g.tobytes()
 
 
+@PATHS
+def test_extract_unaligned_rows(ctx, simt):
+    """Rows that do not start on 16-byte boundaries take the 8-byte loads: a
+    device buffer one double past an aligned base gives the same bytes as the
+    aligned one, and an odd bin count (601) over several tiles meets the oracle."""
+    torch = pytest.importorskip("torch")
+    base = extraction_cases()
+    rng = np.random.default_rng(5)
+    big = base[rng.integers(0, len(base), 300)] * (1.0 + 0.01 * rng.standard_normal((300, 600)))
+    d_al = torch.tensor(big, device="cuda")
+    d_off = torch.zeros(big.size + 1, dtype=torch.float64, device="cuda")
+    d_off[1:] = d_al.view(-1)
+    outs = []
+    for d_in in (d_al, d_off[1:]):
+        d_out = torch.zeros(300 * pdv.PEAK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        pdv.pdv_extract_peaks(ctx.handle, d_in, 300, 600, 0.0, 8000.0, 2000.0, 40, 1.02, 3.5,
+                              d_out, simt=simt)
+        torch.cuda.synchronize()
+        outs.append(d_out.cpu().numpy().tobytes())
+    assert outs[0] == outs[1]
+    odd = np.concatenate([big, big[:, -1:]], axis=1)               # 601 bins, same width
+    v_hi = 8000.0 * 601 / 600
+    g = pdv.extract_peaks(ctx, odd, 0.0, v_hi, 2000.0, 40, 1.02, 3.5, simt=simt)
+    for i in rng.choice(300, 30, replace=False):
+        compare_peak(g[i], O.extract_peak(odd[i], 0.0, v_hi, 2000.0, 40, 1.02, 3.5))
+
+
 def test_extract_paths_agree(ctx):
     """The tensor-core and the CUDA-core products give the same peaks within
     twice the oracle bar (each path is held to 2.5e-5 in beta and 5e-5 in tau0
