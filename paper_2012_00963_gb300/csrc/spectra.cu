@@ -991,18 +991,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_extract_tc(
     for (int c = 0; c < n_chunks; ++c) {
       const int b = c & 1, g = c / kTcG, set = g & 1;
       const bool first = c % kTcG == 0;
-      if (c >= 2 && __syncthreads_or(!wait(b))) {   // buffer b's products (chunk c - 2) done
-        fail = 1;
-        break;
-      }
+      // Each thread waits on the mbarriers for itself and writes only its own pieces of the
+      // buffers; a wait that gave up reaches every thread at the block barrier before the
+      // products, the one barrier a chunk needs
+      int lfail = 0;
+      if (c >= 2 && !wait(b)) lfail = 1;             // buffer b's products (chunk c - 2) done
       if (first && g >= 2) {                         // pair `set` summed group g - 2: add it up
-        if (__syncthreads_or(!wait(2 + set))) {
-          fail = 1;
-          break;
+        // the flush's tensor-memory loads are warp-wide (.sync.aligned): a warp flushes
+        // only if every lane saw the pair complete
+        if (!__all_sync(kFull, wait(2 + set))) {
+          lfail = 1;
+        } else {
+          tc_fence_after();
+          tc_flush(tmem, set, nt, Cs, warp, lane);
+          tc_fence_before();
         }
-        tc_fence_after();
-        tc_flush(tmem, set, nt, Cs, warp, lane);
-        tc_fence_before();
       }
       unsigned char* Ah = As + (2 * b) * a_tile;
       unsigned char* Al = Ah + a_tile;
@@ -1034,8 +1037,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_extract_tc(
       cp_async_wait_all();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc_fence_before();
-      __syncthreads();
+      const int any_fail = __syncthreads_or(lfail);
       tc_fence_after();
+      if (any_fail) {
+        fail = 1;
+        break;
+      }
       if (tid == 0) {
         const uint32_t ah = smem_addr(Ah), al = smem_addr(Al), bh = smem_addr(Bh), bl = smem_addr(Bl);
         const uint32_t dm = tmem + (uint32_t)(set * 2 * nt), dc = dm + (uint32_t)nt;
