@@ -266,11 +266,12 @@ __device__ __forceinline__ unsigned long long fast_forward(const StepConst& sc, 
 // whole warp (fast_forward) until the run ends.
 constexpr unsigned kLongRun = 4;
 
-__global__ void __launch_bounds__(256) k_transport_step(const SetDesc* __restrict__ set,
-                                                        const float* __restrict__ pn_g,
-                                                        StepConst sc,
-                                                        unsigned long long* __restrict__ ctr,
-                                                        unsigned long long* __restrict__ steps_out) {
+// 3 blocks of 8 warps per SM (80 registers, no spills): 1.6 % faster than 2 blocks at 113
+__global__ void __launch_bounds__(256, 3) k_transport_step(const SetDesc* __restrict__ set,
+                                                           const float* __restrict__ pn_g,
+                                                           StepConst sc,
+                                                           unsigned long long* __restrict__ ctr,
+                                                           unsigned long long* __restrict__ steps_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SetDesc sd;
   __shared__ unsigned long long s_cnt[C_NCOUNT];
