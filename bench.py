@@ -883,11 +883,21 @@ def model_mode(args):
     pk_ms, pk_kms = timed(run_pk)
     clk = clocks.stop()
 
-    # end to end through the C ABI with host buffers
-    sets_h = np.ascontiguousarray(sets).view(pdv.SS_SET_DTYPE).ravel()
-    out_h = np.empty(n * nb)
-    spec_h = d_in.cpu().numpy()
-    pk_h = np.zeros(n, dtype=pdv.PEAK_DTYPE)
+    # end to end through the C ABI with host buffers (page-locked, as a serving
+    # host would hold them: numpy views of pinned torch allocations)
+    keep = []
+
+    def pinned(a):
+        t = torch.empty(a.nbytes, dtype=torch.uint8).pin_memory()
+        keep.append(t)
+        v = t.numpy().view(a.dtype).reshape(a.shape)
+        v[...] = a
+        return v
+
+    sets_h = pinned(np.ascontiguousarray(sets).view(pdv.SS_SET_DTYPE).ravel())
+    out_h = pinned(np.zeros(n * nb))
+    spec_h = pinned(d_in.cpu().numpy())
+    pk_h = pinned(np.zeros(n, dtype=pdv.PEAK_DTYPE))
     e2e = {}
     for name, fn in (("ss", lambda: pdv.pdv_ss_spectrum(ctx.handle, sets_h, n, nb, v_lo, v_hi, out_h,
                                                           per_dv=True)),
