@@ -684,7 +684,7 @@ static SetDesc make_set(const pdv_request* r) {
   d.ap_all = !(r->probe.aperture_radius_mm > 0);
   d.omega_q = (unsigned)std::floor(cl->albedo * 16777216.0 + 0.5);
   d.stream_id = r->stream_id;
-  d.max_events = r->max_events ? r->max_events : 1000000u;
+  d.max_events = r->max_events ? std::min(r->max_events, 0xfffffffeu) : 1000000u;
   d.implicit = (r->flags & PDV_IMPLICIT_CAPTURE) ? 1u : 0u;
   d.launch_horizontal = (r->flags & PDV_TEST_HORIZONTAL_LAUNCH) ? 1 : 0;
   d.debug_check = (r->flags & PDV_TEST_DEBUG_CHECK) ? 1 : 0;

@@ -270,11 +270,14 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
   bool exhausted = false, alive = false;
   unsigned long long pk = 0, W = 0;
   long long Sq = 0;
-  unsigned kev = 0, nev = 0, nsca = 0, nsurf = 0;   // nev: events left before the limit
+  // kev: index of the flight's Philox block (1 for the first flight); the
+  // packet has made kev - 1 events when a flight that is an event starts
+  unsigned kev = 0, nsca = 0, nsurf = 0;
   unsigned long long dmask = 0;
   float vcur = 0.f, ux = 0.f, uy = 0.f, uz = -1.f, iuz = -1.f;
   float Xx = 0.f, Xy = 0.f, vapp = 0.f, vcomp = 0.f;
-  unsigned st_launch = 0, st_events = 0, st_scat = 0, st_surf = 0, st_esc = 0;
+  // w_launch: packets this warp launched (the same in every lane)
+  unsigned w_launch = 0, st_events = 0, st_scat = 0, st_surf = 0, st_esc = 0;
   unsigned long long st_wesc = 0, st_wabs = 0, st_wsurf = 0;   // escaped / absorbed weight
 
   const unsigned lt_mask = lanemask_lt();
@@ -309,9 +312,8 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
         vcur = sd.v_top_f;
         Xx = 0.f; Xy = 0.f; vapp = 0.f; vcomp = 0.f;
         W = 1ull << 32;
-        kev = 1; nev = sd.max_events;
+        kev = 1;
         if (DUMP) { nsca = 0; nsurf = 0; dmask = 0; }
-        ++st_launch;
         alive = true;
 #ifdef PDV_DEBUG
         if (sd.debug_check && pk == base_pk)     // PDV_TEST_DEBUG_CHECK: once per set
@@ -325,6 +327,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
 #endif
       }
       pool_next += take;
+      w_launch += take;
     }
     if (!__any_sync(kFull, alive)) break;
 
@@ -367,8 +370,11 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     // lateral displacement in velocity units (x = x0 + t X)
     if (!horiz) {
       const float d = vn - vcur;
-      Xx = fmaf(ux * iuz, d, Xx);
-      Xy = fmaf(uy * iuz, d, Xy);
+      // (x, y) pairs as packed FP32x2 products (each half rounds as fmaf / fmul)
+      const float2 X = __ffma2_rn(__fmul2_rn(make_float2(ux, uy), make_float2(iuz, iuz)),
+                                  make_float2(d, d), make_float2(Xx, Xy));
+      Xx = X.x;
+      Xy = X.y;
     } else {
       // horizontal packet: lateral path tau / mu(z), in velocity units tau / tau_tot dv/dS
       float dvds;
@@ -457,7 +463,6 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     if (ev) {
       Sq = what == 2 ? 0ll : (what == 3 ? Sq : Sn);
       vcur = vn;
-      --nev;
       ++st_events;
     }
     // Step (6): free surface z = v_fs t, reflectivity in 2^32 fixed point:
@@ -569,16 +574,20 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     const float rs = rsqrtf(h2);
     const float sh = h2 * rs;
     const float ah = st * rs;
-    float nx = fmaf(ah, fmaf(ux * uz, cp, -uy * sp), ux * ct);
-    float ny = fmaf(ah, fmaf(uy * uz, cp, ux * sp), uy * ct);
+    // the horizontal part as one complex product, (n_x + i n_y) = (u_x + i u_y)
+    // (ct + ah u_z cp + i ah sp): Eq. 16's terms grouped, three products fewer
+    const float ga = fmaf(ah * uz, cp, ct), gb = ah * sp;
+    float nx = fmaf(ux, ga, -uy * gb);
+    float ny = fmaf(uy, ga, ux * gb);
     float nz = fmaf(-st * cp, sh, uz * ct);
     nx = vert ? st * cp : nx;
     ny = vert ? st * sp : ny;
     nz = vert ? ((surf || uz >= 0.0f) ? ct : -ct) : nz;
     const bool spec = !FAST && surf && sd.surface_mode == PDV_SURFACE_SPECULAR;
     const float inv_n = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
-    nx = spec ? ux : nx * inv_n;
-    ny = spec ? uy : ny * inv_n;
+    const float2 nn = __fmul2_rn(make_float2(nx, ny), make_float2(inv_n, inv_n));
+    nx = spec ? ux : nn.x;
+    ny = spec ? uy : nn.y;
     nz = spec ? -uz : nz * inv_n;
     if (scat) {
       // Eq. 4 / Eq. 18: the moving scatterer (or wall) shifts the frequency
@@ -591,7 +600,9 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     st_scat += part ? 1u : 0u;
     if (DUMP) nsca += part ? 1u : 0u;
     fate = (scat && W == 0) ? 3u : fate;     // the surface absorbed all of the weight
-    if (fate == 0 && ev && nev == 0u) {
+    // the event limit: kev (already advanced) exceeds max_events once the
+    // packet has made max_events events
+    if (fate == 0 && ev && kev > sd.max_events) {
       atomicAdd(&s_cnt[C_W_TRUNCATED], W);
       atomicAdd(&s_cnt[C_TRUNCATED], 1ull);
       fate = 4;
@@ -616,7 +627,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     if (fate) {
       if (DUMP && sd.packets) {
         pdv_packet_record rec;
-        rec.n_events = sd.max_events - nev;
+        rec.n_events = kev - 1u - (fate == 1u ? 1u : 0u);
         rec.n_scatters = nsca;
         rec.n_surface = nsurf;
         rec.fate = fate;
@@ -631,10 +642,9 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
 
   // ---- flush this set's tallies
   {
-    unsigned a = st_launch, b = st_events, c = st_scat, d = st_surf, e = st_esc;
+    unsigned b = st_events, c = st_scat, d = st_surf, e = st_esc;
     unsigned long long we = st_wesc, wa = st_wabs, ws = st_wsurf;
     for (int o = 16; o; o >>= 1) {
-      a += __shfl_xor_sync(kFull, a, o);
       b += __shfl_xor_sync(kFull, b, o);
       c += __shfl_xor_sync(kFull, c, o);
       d += __shfl_xor_sync(kFull, d, o);
@@ -644,7 +654,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
       ws += __shfl_xor_sync(kFull, ws, o);
     }
     if (lane == 0) {
-      atomicAdd(&s_cnt[C_LAUNCHED], (unsigned long long)a);
+      atomicAdd(&s_cnt[C_LAUNCHED], (unsigned long long)w_launch);
       atomicAdd(&s_cnt[C_EVENTS], (unsigned long long)b);
       atomicAdd(&s_cnt[C_SCATTERS], (unsigned long long)c);
       atomicAdd(&s_cnt[C_SURFACE_HITS], (unsigned long long)d);
