@@ -718,6 +718,7 @@ static SetDesc make_set(const pdv_request* r) {
     // 1 - S E = (1 - S) + S eps with eps = 1 - E, and v = v_fs (1 - ln(1 - S E) / beta)
     const double x = cl->desc.beta * (cl->v_top / cl->desc.v_fs - 1.0);
     d.eps_f = (float)std::exp(-x);
+    d.eps30_f = std::ldexp(d.eps_f, -30);
     d.lg_c_f = (float)(cl->desc.v_fs * M_LN2 / cl->desc.beta);
     d.dvds_c_f = (float)(cl->desc.v_fs * -std::expm1(-x) / cl->desc.beta);
     d.vb_d = cl->desc.v_fs / cl->desc.beta;

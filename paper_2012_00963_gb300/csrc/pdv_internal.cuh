@@ -162,6 +162,7 @@ struct SetDesc {
   int angle_table;                    // node spacing <= 3.1e-3: sin/cos from the node table
   // exponential law: v(S) = v_fs - lg_c log2((1 - S) + S eps), dv/dS = dvds_c / ((1 - S) + S eps)
   float lg_c_f, eps_f, dvds_c_f;      // v_fs ln2 / beta, exp(-beta (v_top/v_fs - 1)), v_fs E / beta
+  float eps30_f;                      // eps_f 2^-30 (exact): the factor of the high word of S
   double vb_d, E_d;                   // FP64 path: v_fs / beta and E = 1 - exp(-beta (v_top/v_fs - 1))
   uint2 rk[10];                       // Philox round keys of the seed (philox_round_key)
   // debug build: path trace of the first n_trace packets at snapshot time t_trace

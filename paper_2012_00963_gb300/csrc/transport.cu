@@ -342,12 +342,11 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     // dS 2^62 truncated towards zero, exactly (a power-of-two scaling, then a
     // 64-bit conversion); the largest binary32 magnitude below 1 keeps it in
     // range, and a flight of |dS| >= 1 leaves the cloud whatever its end
-    const long long Sn =
+    long long Sn =
         Sq + __float2ll_rz(fminf(fmaxf(dS, -0.99999994f), 0.99999994f) * 4.611686018427388e18f);
-    // 0 interaction, 1 escape through the top, 2 free surface, 3 horizontal
-    const int what = horiz ? 3
-                           : ((dS >= 1.0f || Sn >= (long long)kOneQ) ? 1
-                                                                      : ((dS <= -1.0f || Sn <= 0) ? 2 : 0));
+    // 0 interaction, 1 escape through the top, 2 free surface; a horizontal
+    // flight is an interaction where it started (set in the lateral move below)
+    int what = (dS >= 1.0f || Sn >= (long long)kOneQ) ? 1 : ((dS <= -1.0f || Sn <= 0) ? 2 : 0);
     // velocity coordinate z/t where the flight ends
     float vn = vcur;
     if (FAST || sd.expo) {
@@ -357,7 +356,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
       const unsigned long long sn = (unsigned long long)Sn, oms = kOneQ - sn;
       const float om = fmaf(__uint2float_rn((unsigned)(oms >> 32)), kTwoM30f,
                             __uint2float_rn((unsigned)oms) * kTwoM62f);
-      const float q = fmaf(__uint2float_rn((unsigned)(sn >> 32)) * kTwoM30f, sd.eps_f, om);
+      const float q = fmaf(__uint2float_rn((unsigned)(sn >> 32)), sd.eps30_f, om);
       vn = fmaf(-sd.lg_c_f, __log2f(q), sd.v_fs_f);
     } else if (what == 0) {
       const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, sd.n_v, (unsigned long long)Sn);
@@ -366,7 +365,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
       vn = fmaf(fd, PDV_LD(tb.w, j, sd.n_v, PDV_DEBUG_SITE_MASS_NODE),
                 fmaf((float)j, sd.dv_f, sd.v_bot_f));
     }
-    vn = what == 1 ? sd.v_top_f : (what == 2 ? sd.v_fs_f : (what == 3 ? vcur : vn));
+    vn = what == 1 ? sd.v_top_f : (what == 2 ? sd.v_fs_f : vn);
     // lateral displacement in velocity units (x = x0 + t X)
     if (!horiz) {
       const float d = vn - vcur;
@@ -382,7 +381,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
         const unsigned long long sq = (unsigned long long)Sq, oms = kOneQ - sq;
         const float om = fmaf(__uint2float_rn((unsigned)(oms >> 32)), kTwoM30f,
                               __uint2float_rn((unsigned)oms) * kTwoM62f);
-        dvds = sd.dvds_c_f / fmaf(__uint2float_rn((unsigned)(sq >> 32)) * kTwoM30f, sd.eps_f, om);
+        dvds = sd.dvds_c_f / fmaf(__uint2float_rn((unsigned)(sq >> 32)), sd.eps30_f, om);
       } else {
         const int j = search_mass(tb.Sq, tb.G, sd.g_shift, sd.n_g, sd.n_v, (unsigned long long)Sq);
         dvds = PDV_LD(tb.w, j, sd.n_v, PDV_DEBUG_SITE_MASS_NODE) * 4.611686018427388e18f;
@@ -390,6 +389,10 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
       const float len = tau * inv_tau * dvds;
       Xx = fmaf(ux, len, Xx);
       Xy = fmaf(uy, len, Xy);
+      // the interaction happens at the starting depth, velocity unchanged
+      Sn = Sq;
+      vn = vcur;
+      what = 0;
     }
 
     // ---- Step (6): out through the top, vacuum flight to the probe plane
@@ -457,11 +460,11 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     st_esc += esc ? 1u : 0u;
     st_wesc += esc ? W : 0ull;
 
-    // ---- an event: interaction (what 0, 3) or the free surface (what 2)
+    // ---- an event: interaction (what 0) or the free surface (what 2)
     const bool ev = alive && what != 1;
     const bool surf = ev && what == 2;
     if (ev) {
-      Sq = what == 2 ? 0ll : (what == 3 ? Sq : Sn);
+      Sq = what == 2 ? 0ll : Sn;
       vcur = vn;
       ++st_events;
     }
@@ -475,8 +478,9 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
                          : (((unsigned long long)(unsigned)W * (unsigned)sd.R_q + (1ull << 31)) >> 32));
     st_surf += surf ? 1u : 0u;
     if (DUMP) nsurf += surf ? 1u : 0u;
-    st_wsurf += surf ? W - Wr : 0ull;
-    W = surf ? Wr : W;
+    const unsigned long long Ws = surf ? Wr : W;   // the weight after the flight's end
+    st_wsurf += W - Ws;
+    W = Ws;
     // Eq. 11: analog absorption (the gate is omega_q). Implicit capture (gate
     // 0): the particle absorbs 1 - omega of the weight and the packet
     // scatters; a light packet plays the roulette on r1. Launches without
