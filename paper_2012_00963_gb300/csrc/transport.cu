@@ -399,7 +399,8 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     const bool esc = alive && what == 1;
     const bool cone = esc && (sd.cone_all || uz >= sd.cos_alpha_f);
     if (cone) {
-      const float fb = floorf((vapp - vcomp - sd.v_lo_f) * sd.inv_dbin_f);
+      // v_app is summed doubled (below); the exact scalings undo it
+      const float fb = floorf((vapp - vcomp - 2.0f * sd.v_lo_f) * (0.5f * sd.inv_dbin_f));
       const int idx = fb < 0.0f ? 0 : (fb >= (float)n_bins ? n_bins + 1 : (int)fb + 1);
       if (sd.ap_all) {
         // Eq. 19 at every snapshot time alike (unlimited aperture): one
@@ -560,10 +561,13 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     }
     {
       // azimuth, Eq. 15: phi = 2 pi u with u = ((r >> 9) + 1/2) 2^-23
-      const int mp = (int)((surf ? r.z : r.w) >> 9);
-      const int jp = (mp + (1 << 12)) >> 13;
-      const float dphi = (float)(2 * (mp - (jp << 13)) + 1) * kPi2m23f;
-      cos_sin_add(tb.turn[jp & (kTurn - 1)], dphi, &cp, &sp);
+      // the nearest of the kTurn steps, jp = ((r >> 9) + 2^12) >> 13 modulo kTurn, and the
+      // remainder (r >> 9) - jp 2^13 in [-2^12, 2^12): bits 9-21 of r, sign-extended
+      const unsigned rw = surf ? r.z : r.w;
+      const unsigned jp = (rw + (1u << 21)) >> 22;
+      const int rem = (int)(rw << 10) >> 19;
+      const float dphi = (float)(2 * rem + 1) * kPi2m23f;
+      cos_sin_add(tb.turn[jp], dphi, &cp, &sp);
     }
     if (!FAST && sd.surface_mode == PDV_SURFACE_LAMBERT) {
       const float a = u23f(r.y);
@@ -597,7 +601,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
       // Eq. 4 / Eq. 18: the moving scatterer (or wall) shifts the frequency
       // (a rounded product: no FMA contraction into the compensated sum,
       // so every instantiation of this kernel computes the same bits)
-      kahan_add(vapp, vcomp, __fmul_rn(0.5f * (nz - uz), vn));
+      kahan_add(vapp, vcomp, __fmul_rn(nz - uz, vn));   // 2 v_app: the half applied at the end
       ux = nx; uy = ny; uz = nz;
       iuz = rcp_approx(nz);
     }
@@ -636,7 +640,7 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
         rec.n_surface = nsurf;
         rec.fate = fate;
         rec.weight = W;
-        rec.v_app = (double)vapp - (double)vcomp;
+        rec.v_app = 0.5 * ((double)vapp - (double)vcomp);
         rec.detect_mask = dmask;
         if (PDV_IN(pk - base_pk, sd.n_packets, PDV_DEBUG_SITE_PACKET)) sd.packets[pk - base_pk] = rec;
       }
