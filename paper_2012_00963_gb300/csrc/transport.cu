@@ -472,11 +472,12 @@ __device__ __forceinline__ void walk_set(const SetDesc& sd, const SmemTables& tb
     // Step (6): free surface z = v_fs t, reflectivity in 2^32 fixed point:
     // round(W R_q / 2^32). W <= 2^32, and R_q < 2^32 unless R = 1, so the
     // product is one 32 x 32 -> 64-bit multiply-add; W = 2^32 gives R_q.
+    // as ((W - 1) R_q + R_q + 2^31) >> 32: one multiply-add for every W in
+    // [1, 2^32] (W - 1 fits 32 bits), W = 2^32 included
     const unsigned long long Wr =
         (!FAST && sd.R_q >= (1ull << 32))
             ? W
-            : ((W >> 32) ? sd.R_q
-                         : (((unsigned long long)(unsigned)W * (unsigned)sd.R_q + (1ull << 31)) >> 32));
+            : ((unsigned long long)((unsigned)W - 1u) * (unsigned)sd.R_q + (sd.R_q + (1ull << 31))) >> 32;
     st_surf += surf ? 1u : 0u;
     if (DUMP) nsurf += surf ? 1u : 0u;
     const unsigned long long Ws = surf ? Wr : W;   // the weight after the flight's end
