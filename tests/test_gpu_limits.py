@@ -3,7 +3,8 @@ packet by packet (the same bar as tests/test_gpu_parity.py): 4096 snapshot
 times with a finite aperture (one histogram row per time, the aperture
 interval search over 4096 sorted times) and with an unlimited one (one row
 read back for every time), 65536 velocity bins, and one past each limit
-refused."""
+refused. The largest per-packet event limit (2^32 - 1, taken as 2^32 - 2)
+runs and gives the tallies of the default limit, which no walk here reaches."""
 import numpy as np
 import pytest
 
@@ -69,3 +70,16 @@ def test_one_past_each_limit_is_refused(ctx):
             assert e.value.status == pdv.PDV_EINVAL
     finally:
         cloud.close()
+
+
+def test_largest_event_limit(ctx):
+    wl = W.cfg1(n_packets=20000, **WIDE)
+    cloud = pdv.Cloud(ctx, wl)
+    try:
+        outs = [pdv.simulate_spectrum(ctx, cloud, wl.replace(max_events=m), raw=True)
+                for m in (1_000_000, 2**32 - 1)]
+    finally:
+        cloud.close()
+    np.testing.assert_array_equal(outs[0]["raw"], outs[1]["raw"])
+    np.testing.assert_array_equal(outs[0]["counters"], outs[1]["counters"])
+    assert pdv.counters_dict(outs[1]["counters"][0])["truncated"] == 0
