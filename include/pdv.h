@@ -167,7 +167,7 @@ typedef struct {
   uint64_t packet_begin;
   uint64_t seed;
   uint32_t stream_id;
-  uint32_t max_events;             /* per packet; 0 = 1e6, at most 2^32-2 */
+  uint32_t max_events;             /* per packet; 0 = 1e6; 2^32-1 acts as 2^32-2 */
   int n_bins;                      /* 1..65536                           */
   double v_lo, v_hi;               /* m/s, v_hi > v_lo                   */
   int precision;                   /* PDV_PREC_FP32 | PDV_PREC_FP64      */
