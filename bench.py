@@ -645,7 +645,7 @@ def serving_run(ctx, seconds, rate):
     hidden = {"beta": 6.0, "m0": 3.0 * W.MG_CM2, "d_m": 2.0 * W.UM, "tau0": float(g["tau_tot"])}
     out = serving.summary(res, hidden)
     out["oracle_same_packets"] = served_error(res.kept)
-    out["capacity"] = serving_capacity(ctx, probe)
+    out["capacity"] = serving_capacity(ctx, probe, rate)
     return out
 
 
@@ -671,11 +671,12 @@ def served_error(kept, n_each=4):
             "bins_differing": differ, "l1_rel": moved / tot if tot else None, "max_abs_z": zmax}
 
 
-def serving_capacity(ctx, probe, n=64):
+def serving_capacity(ctx, probe, rate, n=64):
     """Spectra/s one GPU sustains on the served request mix (the first n
     arrivals of the stream) when each request runs alone on the FP32 path and
     on the plain FP64 path: both draw the same random numbers, so this is the
     comparison at equal spectrum error."""
+    import numpy as np
     import torch
     from paper_2012_00963_gb300 import pdv
     from paper_2012_00963_gb300 import workloads as W
@@ -686,12 +687,23 @@ def serving_capacity(ctx, probe, n=64):
     for prec in ("fp32", "fp64"):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        lat = []
         for c, w in zip(clouds, wls):
-            pdv.simulate_spectrum(ctx, c, w, precision=prec, raw=False)
+            t1 = time.perf_counter()
+            pdv.simulate_spectrum(ctx, c, w, precision=prec, raw=False)   # blocking
+            lat.append(1e3 * (time.perf_counter() - t1))
         out[prec + "_spectra_per_s"] = n / (time.perf_counter() - t0)
+        # each request's latency when it runs alone (no queue): the path's own
+        # service time, at equal spectrum error
+        out[prec + "_alone_p50_ms"] = float(np.percentile(lat, 50))
+        out[prec + "_alone_p99_ms"] = float(np.percentile(lat, 99))
     for c in clouds:
         c.close()
     out["ratio_fp32_over_fp64"] = out["fp32_spectra_per_s"] / out["fp64_spectra_per_s"]
+    # a path whose capacity is below the stream's offered rate cannot keep its
+    # queue bounded, whatever its latency alone
+    out["offered_rate"] = rate
+    out["fp64_sustains_offered_rate"] = bool(out["fp64_spectra_per_s"] >= rate)
     out["requests"] = n
     out["packets"] = int(sum(w.n_packets for w in wls))
     return out
