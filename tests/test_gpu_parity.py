@@ -189,6 +189,7 @@ BUILDS = {
                                            t_snap=(0.5e-6, 1e-6, 3e-6))),
     "implicit": (True, lambda: W.cfg1(n_packets=100000, implicit_capture=True, **WIDE)),
     "albedo0": (True, lambda: W.cfg1(n_packets=100000, phase=W.Phase(albedo=0.0), **WIDE)),
+    "maxev3": (True, lambda: W.cfg1(n_packets=100000, max_events=3, **WIDE)),
     "R1": (False, lambda: W.cfg1(n_packets=100000, reflectivity=1.0, **WIDE)),
     "coarse_table": (False, lambda: W.cfg1(n_packets=100000, phase=W.Phase(
         kind="table", theta=np.linspace(0.0, np.pi, 181),
